@@ -1,0 +1,386 @@
+"""Throughput of the homomorphic convolution path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config resnet18]
+    python bench.py --impl reference ...    (the CPU oracle, timed on host cores)
+
+A step is one pass of the hot path (forward NTT of the inputs, per-slot
+contraction, inverse NTT, mask addition) over every conv layer of the
+workload for one batch of synthetic encrypted inputs.  The default workload
+is the ResNet-18 CIFAR conv stack, B = 1, N = 8192, L = 3, t = 65537.  Each
+rank runs the full workload on its own GPU (independent images: weak
+scaling, no data-path collective).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2401_16732_gb300 import synth  # noqa: E402
+from paper_2401_16732_gb300.workloads import WORKLOADS  # noqa: E402
+
+T_PLAIN = 65537
+FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 129e6
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def layer_bytes(g, B, L, N, masked=True):
+    """Algorithmic HBM bytes of the fused contraction + INTT + mask kernel for
+    one layer: NTT weights, NTT inputs, output ciphertexts, masks."""
+    w = L * g.Cout * g.G * N * 4
+    cin = B * g.n_in * 2 * L * N * 4
+    out = B * g.n_out * 2 * L * N * 4
+    r = B * g.n_out * N * 4 if masked else 0
+    return w + cin + out + r
+
+
+def ntt_bytes(g, B, L, N):
+    return 2 * B * g.n_in * 2 * L * N * 4
+
+
+def slot_macs(g, B, L, N):
+    return B * g.n_out * g.G * 2 * L * N
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample_step(wl, seed, per_layer):
+    """Run Algorithm 1 (oracle route O2, OpenMP over output channels) on
+    `per_layer` output channels of every layer of one image; return the
+    extrapolated seconds for the whole workload (all channels, all B images)
+    and the seconds actually spent."""
+    import oracle
+    primes = oracle.find_primes(wl.N, wl.L)
+    est, spent = 0.0, 0.0
+    for li, (Cin, Cout, H, W, k, s, p) in enumerate(wl.layers):
+        geo = oracle.geometry(wl.N, Cin, Cout, H, W, k, s, p)
+        w = synth.weights(seed, (Cout, Cin, k, k), li)
+        ct = synth.raw_ciphertexts(seed, primes, (geo.n_in, 2, wl.L, wl.N), li)
+        n = min(per_layer, Cout)
+        t0 = time.perf_counter()
+        oracle.conv_alg1(ct, w, geo, primes, 0, n)
+        dt = time.perf_counter() - t0
+        spent += dt
+        est += dt * (Cout / n) * wl.B
+    return est, spent
+
+
+def cpu_baseline(wl, seed, budget_s=20.0):
+    import oracle
+    threads = oracle.num_threads()
+    per_layer = max(1, threads)
+    est, spent = oracle_sample_step(wl, seed, per_layer)
+    # one more pass with a larger sample when the first was short
+    if spent < budget_s / 4:
+        per_layer = max(1, int(per_layer * min(4.0, budget_s / 2 / max(spent, 1e-3))))
+        est, spent = oracle_sample_step(wl, seed, per_layer)
+    n_layers = len(wl.layers) * wl.B
+    return {"value": n_layers / est, "unit": "layers/s", "cores": threads, "kind": "oracle",
+            "sample": f"Algorithm 1 (oracle O2, OpenMP over output channels) on the first {per_layer} output "
+                      f"channels of each of the {len(wl.layers)} layers of one image ({spent:.1f} s of CPU work), "
+                      f"extrapolated linearly to all channels and B={wl.B}"}
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    threads = oracle.num_threads()
+    per_layer = max(1, threads)
+    for _ in range(args.warmup):
+        oracle_sample_step(wl, args.seed, per_layer)
+    ests, spent = [], 0.0
+    for _ in range(args.steps):
+        est, sp = oracle_sample_step(wl, args.seed, per_layer)
+        ests.append(est)
+        spent += sp
+    n_layers = len(wl.layers) * wl.B
+    est_step = sum(ests) / len(ests)
+    value = n_layers / est_step
+    sample = (f"Algorithm 1 (oracle O2) on {per_layer} output channels per layer of one image per step, "
+              f"extrapolated to all channels and B={wl.B}")
+    print(json.dumps({
+        "impl": "reference", "metric": "encrypted conv layers/s", "value": value, "unit": "layers/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": est_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl.name, "layers": len(wl.layers), "batch": wl.B, "N": wl.N, "L": wl.L,
+                   "t": T_PLAIN},
+        "cpu_baseline": {"value": value, "unit": "layers/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.samples = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                self.samples.append({"sm": float(f[1]), "max": float(f[2]), "util": float(f[4]),
+                                     "hw": f[6], "hwt": f[7], "swt": f[8], "pcap": f[9]})
+            except ValueError:
+                pass
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        load = [s for s in self.samples if s["util"] > 0] or self.samples
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                          ("pcap", "sw_power_cap")):
+            if any(s[key].lower() == "active" for s in load):
+                reasons.append(name)
+        return {"sm_mhz": statistics.median(s["sm"] for s in load), "sm_max_mhz": max(s["max"] for s in load),
+                "reasons": reasons, "samples_under_load": len(load)}
+
+
+def run_gpu(args, wl, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2401_16732_gb300 import flashgpu
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    N, L, B = wl.N, wl.L, wl.B
+    ctx = flashgpu.Context(N, L, T_PLAIN)
+    stream = torch.cuda.Stream(device=dev)
+    seed = args.seed + 1000 * rank
+
+    def to_dev(a, dt=torch.int32):
+        a = np.ascontiguousarray(a)
+        if a.dtype == np.uint32:
+            a = a.view(np.int32)
+        return torch.from_numpy(a).to(dt).to(dev)
+
+    # ---- setup (untimed): weights, fresh encryptions, masks, buffers ----
+    s = synth.secret_key(seed, N)
+    sk = ctx.keygen(to_dev(s, torch.int8))
+    layers = []
+    ws_words = 4
+    for li, shape in enumerate(wl.layers):
+        g = ctx.geom(*shape)
+        w = synth.weights(seed, (g.Cout, g.Cin, g.k, g.k), li)
+        x = synth.activations(seed, (B, g.Cin, g.H, g.W), li)
+        a = synth.uniform_residues(seed, ctx.primes, (B, g.n_in, L, N), li)
+        e = synth.cbd_noise(seed, (B, g.n_in, N), li)
+        r = synth.masks(seed, (B, g.n_out, N), T_PLAIN, li)
+        lay = {"g": g, "w_hat": ctx.encode_weights(g, to_dev(w, torch.int8)),
+               "ct": ctx.encrypt(sk, g, to_dev(x), to_dev(a), to_dev(e)), "r": to_dev(r),
+               "out": torch.empty((B, g.n_out, 2, L, N), dtype=torch.int32, device=dev)}
+        layers.append(lay)
+        ws_words = max(ws_words, ctx.workspace_bytes(g, B) // 4)
+    ws = torch.empty(ws_words, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+
+    def step(events=None):
+        for i, lay in enumerate(layers):
+            if events is not None:
+                events[i][0].record(stream)
+            ctx.he_conv2d_ntt_inputs(lay["g"], lay["ct"], ws, stream=stream)
+            if events is not None:
+                events[i][1].record(stream)
+            ctx.he_conv2d_from_ntt(lay["g"], B, lay["w_hat"], ws, lay["out"], r=lay["r"], stream=stream)
+            if events is not None:
+                events[i][2].record(stream)
+
+    # capture one step in a CUDA graph (40 launches for ResNet-18)
+    with torch.cuda.stream(stream):
+        step()
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step()
+    launches_per_step = 2 * len(layers)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    for _ in range(args.warmup):
+        graph.replay()
+    stream.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    t_end.record(stream)
+    t_end.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # ---- per-kernel durations (eager launches queued behind a GPU sleep so
+    # that event timestamps bracket the kernels, not host launch latency) ----
+    kern = {"ntt": 0.0, "conv": 0.0}
+    nrep = max(1, min(args.steps, 5))
+    for _ in range(nrep):
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in layers]
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(20_000_000)
+        step(evs)
+        stream.synchronize()
+        for e in evs:
+            kern["ntt"] += e[0].elapsed_time(e[1])
+            kern["conv"] += e[1].elapsed_time(e[2])
+    for k in kern:
+        kern[k] /= nrep
+
+    # ---- end to end: pinned host inputs -> device -> path -> host outputs ----
+    e2e = None
+    if not args.skip_e2e:
+        h_in = [lay["ct"].cpu().pin_memory() for lay in layers]
+        h_out = [torch.empty(lay["out"].shape, dtype=torch.int32, pin_memory=True) for lay in layers]
+        h2d = sum(t.numel() * 4 for t in h_in)
+        d2h = sum(t.numel() * 4 for t in h_out)
+        n_e2e = max(1, min(args.steps, 5))
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for lay, h in zip(layers, h_in):
+                    lay["ct"].copy_(h, non_blocking=True)
+            graph.replay()
+            with torch.cuda.stream(stream):
+                for lay, h in zip(layers, h_out):
+                    h.copy_(lay["out"], non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e = {"value": world * B * len(layers) * n_e2e / dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": n_e2e}
+    clocks.stop()
+
+    if rank != 0:
+        return 0
+    geoms = [lay["g"] for lay in layers]
+    conv_bytes = sum(layer_bytes(g, B, L, N) for g in geoms)
+    step_bytes = conv_bytes + sum(ntt_bytes(g, B, L, N) for g in geoms)
+    macs = sum(slot_macs(g, B, L, N) for g in geoms)
+    hbm, peak_kind = peaks()
+    achieved = conv_bytes / (kern["conv"] * 1e-3) / 1e9
+    value = world * B * len(layers) * args.steps / (ms * 1e-3)
+    line = {
+        "metric": "encrypted conv layers/s", "value": value, "unit": "layers/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": wl.name, "layers": len(layers), "batch": B, "N": N, "L": L, "t": T_PLAIN,
+                   "l2": f"no flush: {step_bytes / 1e9:.2f} GB of algorithmic traffic per step > {L2_BYTES / 1e6:.0f} MB L2",
+                   "graph": "one CUDA graph per step"},
+        "slot_mac_per_s": world * macs * args.steps / (ms * 1e-3),
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"kernel": "k_conv_intt (contraction + inverse NTT + mask)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_source": peak_kind, "traffic": None,
+                     "kernel_ms_per_step": kern["conv"], "algorithmic_bytes_per_step": conv_bytes,
+                     "ntt_inputs_ms_per_step": kern["ntt"]},
+        "clocks": clocks.summary(),
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if world == 1 and not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline(wl, args.seed)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="resnet18", choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    wl = WORKLOADS[args.config]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, wl, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        return run_gpu(args, wl, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

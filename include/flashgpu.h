@@ -1,0 +1,190 @@
+/*
+ * flashgpu: GB300 (sm_103a) library for the server-side hot path of the Flash
+ * hybrid private-inference protocol (arXiv 2401.16732): homomorphic
+ * convolution of BFV/RLWE ciphertexts holding direct-encoded activations by
+ * plaintext integer CNN filters, followed by the random-mask addition that
+ * turns each output ciphertext into additive secret shares.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Ring R_q = Z_q[x]/(x^N + 1), N in {2048, 4096, 8192, 16384}; q is held as
+ *   L <= 4 RNS primes q_0 > ... > q_{L-1}, the largest primes below 2^30 with
+ *   q_l = 1 mod 2N (Sec. 2.2, Table 1 use a single q; the RNS split is this
+ *   library's representation of it).  Plaintext modulus t (65537 in the
+ *   workloads), Delta = floor(q / t) (Table 1).
+ * - A ciphertext array is uint32 [n][2][L][N]: ciphertext, component c0/c1,
+ *   limb, coefficient; canonical residues in [0, q_l); coefficient domain.
+ * - Pointers named *_dev are CUDA device pointers on the device that was
+ *   current when the context was created; the caller owns and allocates them.
+ *   Host pointers are named *_host.  `stream` is a cudaStream_t (NULL = the
+ *   legacy default stream); work is enqueued asynchronously on it and the
+ *   call returns before it completes.
+ * - Return value: 0 on success, a negative FL_ERR_* code otherwise; no device
+ *   work is enqueued when an argument check fails.  fl_last_error() gives a
+ *   thread-local message for the last failure on the calling thread.
+ * - Nothing here falls back to the CPU: without a CUDA device every compute
+ *   call fails with FL_ERR_CUDA.
+ *
+ * Layout of one convolution layer (fl_conv_geom) follows Sec. 3.3 and
+ * Algorithm 1: the client zero-pads each H x W channel to Hp x Wp
+ * (Hp = H + 2 pad), direct-encodes it (Eq. 1) and packs c_n = floor(N / P)
+ * padded planes of P = Rin * Wp coefficients per ciphertext, channel j in
+ * ciphertext j / c_n at offset (j mod c_n) * P.  A plane larger than N is cut
+ * into `bands` row bands of Rin padded rows (Rout output rows each); each band
+ * is its own set of G = ceil(Cin / c_n) input ciphertexts (index band*G + g).
+ * The output is one ciphertext per output channel and band (index
+ * i*bands + band, Sec. 3.3: no output packing); output pixel (oy, ox) of band
+ * b sits at coefficient (s * (oy - b*Rout)) * Wp + s * ox.
+ */
+#ifndef FLASHGPU_H
+#define FLASHGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FL_OK 0
+#define FL_ERR_ARG (-1)   /* null pointer, size out of range, short workspace */
+#define FL_ERR_SHAPE (-2) /* geometry that the packing cannot represent */
+#define FL_ERR_CUDA (-3)  /* a CUDA runtime call failed (message has the reason) */
+#define FL_ERR_OOM (-4)   /* the context's own tables could not be allocated */
+#define FL_MAX_LIMBS 4
+
+typedef struct fl_ctx fl_ctx; /* opaque: parameters + device twiddle tables */
+
+typedef struct fl_conv_geom {
+  int32_t N, Cin, Cout, H, W, k, stride, pad;
+  int32_t Hp, Wp, Ho, Wo;   /* padded input and output sizes */
+  int32_t Rin, Rout, bands; /* padded rows per ct, output rows per band */
+  int32_t P, c_n, G;        /* plane size, channels per ct, cts per band */
+  int32_t n_in, n_out;      /* input cts per image (bands*G), output cts (Cout*bands) */
+} fl_conv_geom;
+
+/* Thread-local message describing the last failing call on this thread. */
+const char *fl_last_error(void);
+
+/* Fill *out with the ciphertext layout of a k x k convolution (stride, pad)
+ * from Cin to Cout channels on an H x W input at ring degree N (Sec. 3.3,
+ * Algorithm 1; readings: tap step ky*Wp + kx, channel offset (j mod c_n)*P,
+ * c_n = floor(N/P), row bands when Hp*Wp > N).  Pure host code.
+ * FL_ERR_SHAPE if a padded row band of k rows does not fit in N. */
+int fl_conv_geom_make(int N, int Cin, int Cout, int H, int W, int k, int stride, int pad,
+                      fl_conv_geom *out);
+
+/* Create a context on the current CUDA device: find the L primes, a
+ * primitive 2N-th root of unity per prime, the NTT twiddle tables (allocated
+ * on the device and owned by the context) and the per-limb constants
+ * (Delta mod q_l, N^-1, CRT constants for decryption).  1 <= L <= 4,
+ * 2 <= t < 2^20 odd. */
+int fl_ctx_create(int N, int L, uint32_t t, fl_ctx **out);
+/* Free the context and its device tables (the caller has synchronised). */
+void fl_ctx_destroy(fl_ctx *ctx);
+/* Copy out the primes [L], Delta mod q_l [L] and psi_l [L] (the primitive
+ * 2N-th roots the NTT uses); any output pointer may be NULL. */
+int fl_ctx_params(const fl_ctx *ctx, uint32_t *primes_host, uint32_t *delta_host,
+                  uint32_t *psi_host);
+
+/* ---- Row a1: client side (key, packing, private-key encryption) ---- */
+
+/* Secret key: s_dev int8 [N] ternary (Table 2's s(x)); writes its NTT image
+ * sk_dev uint32 [L][N] (the form every other key argument takes). */
+int fl_keygen(fl_ctx *ctx, const int8_t *s_dev, uint32_t *sk_dev, void *stream);
+
+/* Pack and encrypt B images (Sec. 3.3 packing, Eq. 1, Table 2 private-key
+ * encryption): c0 = [-(a*s + e) + Delta*m]_q, c1 = a, where m is the
+ * direct-encoded zero-padded input.  x_dev int32 [B][Cin][H][W] with values
+ * in [0, t); a_dev uint32 [B][n_in][L][N] uniform residues; e_dev int32
+ * [B][n_in][N] noise (|e| < 2^20); ct_dev uint32 [B][n_in][2][L][N] output. */
+int fl_encrypt(fl_ctx *ctx, const uint32_t *sk_dev, const fl_conv_geom *geom, int B,
+               const int32_t *x_dev, const uint32_t *a_dev, const int32_t *e_dev,
+               uint32_t *ct_dev, void *stream);
+
+/* Algorithm 2 (online encryption): ct = Enc(0) + Delta*m.  enc0_dev holds
+ * pre-computed encryptions of zero [B][n_in][2][L][N]; x_dev as in
+ * fl_encrypt; ct_dev may alias enc0_dev. */
+int fl_encrypt_online(fl_ctx *ctx, const fl_conv_geom *geom, int B, const int32_t *x_dev,
+                      const uint32_t *enc0_dev, uint32_t *ct_dev, void *stream);
+
+/* Decrypt n ciphertexts (Appendix A: Delta*m + v = [c1*s + c0]_q, m =
+ * round(t/q * [c1*s + c0]_q) mod t, exact RNS scale-and-round): ct_dev
+ * [n][2][L][N] -> m_dev uint32 [n][N] in [0, t).  workspace: at least
+ * fl_decrypt_workspace_bytes(ctx, n) device bytes. */
+size_t fl_decrypt_workspace_bytes(const fl_ctx *ctx, int n);
+int fl_decrypt(fl_ctx *ctx, const uint32_t *sk_dev, int n, const uint32_t *ct_dev,
+               uint32_t *m_dev, void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/* Read the convolution outputs out of decrypted output polynomials:
+ * m_dev uint32 [B][n_out][N] -> y_dev int32 [B][Cout][Ho][Wo]. */
+int fl_extract_outputs(const fl_conv_geom *geom, int B, const uint32_t *m_dev,
+                       int32_t *y_dev, void *stream);
+
+/* ---- Row a2: server-side weight encoding (offline) ---- */
+
+/* Size in bytes of the encoded weights of one layer: L*Cout*G*N*4. */
+size_t fl_weights_bytes(const fl_ctx *ctx, const fl_conv_geom *geom);
+
+/* Encode filters w_dev int8 [Cout][Cin][k][k] as the NTT images of the
+ * weight polynomials W_{i,g}(x) = sum_{j in g} sum_{ky,kx} w[i][j][ky][kx] *
+ * x^-(ky*Wp + kx + (j mod c_n)*P) -- Algorithm 1's DRot/CMult sequence for
+ * output channel i folded into one plaintext (Eq. 2: DRot(c, e) = c*x^-e).
+ * w_hat_dev uint32 [L][Cout][G][N] (fl_weights_bytes bytes). */
+int fl_encode_weights(fl_ctx *ctx, const fl_conv_geom *geom, const int8_t *w_dev,
+                      uint32_t *w_hat_dev, void *stream);
+
+/* ---- Rows a3-a6: the hot path ---- */
+
+/* Workspace of fl_he_conv2d / fl_he_conv2d_mask: the NTT images of the input
+ * ciphertexts, B*n_in*2*L*N*4 bytes. */
+size_t fl_he_conv2d_workspace_bytes(const fl_ctx *ctx, const fl_conv_geom *geom, int B);
+
+/* Homomorphic convolution (Algorithm 1, evaluated as y_{i,band} =
+ * sum_g W_{i,g} * ct_{band*G+g} in R_q): forward NTT of the inputs into the
+ * workspace (a3), per-slot contraction mod q_l with lazy 64-bit accumulation
+ * (a4, Sec. 6.1) fused with the inverse NTT of each output (a5).
+ * ct_in_dev [B][n_in][2][L][N]; ct_out_dev [B][n_out][2][L][N].  The result
+ * equals Algorithm 1 coefficient for coefficient. */
+int fl_he_conv2d(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_hat_dev,
+                 const uint32_t *ct_in_dev, uint32_t *ct_out_dev, void *workspace_dev,
+                 size_t workspace_bytes, void *stream);
+
+/* Mask addition (Sec. 5.2: the server adds its random r to the encrypted
+ * result, HAdd(<a>, <r>); here the plaintext add c0 <- c0 + Delta*r, since
+ * the server holds no key).  ct_dev [n][2][L][N] updated in place; r_dev
+ * uint32 [n][N] with values in [0, t) (pre-generated offline, Sec. 6.3).
+ * The client then decrypts a + r; the server's share is (t - r) mod t
+ * (Sec. 2.3). */
+int fl_mask_to_share(fl_ctx *ctx, int n, uint32_t *ct_dev, const uint32_t *r_dev, void *stream);
+
+/* fl_he_conv2d followed by fl_mask_to_share on its outputs, with the mask
+ * fused into the inverse-NTT epilogue (one pass over the outputs).
+ * r_dev uint32 [B][n_out][N]. */
+int fl_he_conv2d_mask(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_hat_dev,
+                      const uint32_t *ct_in_dev, const uint32_t *r_dev, uint32_t *ct_out_dev,
+                      void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/* The two stages of fl_he_conv2d_mask as separate calls (same results):
+ * fl_he_conv2d_ntt_inputs: row a3 only, the forward NTT of ct_in_dev into
+ * the workspace (fl_he_conv2d_workspace_bytes bytes).
+ * fl_he_conv2d_from_ntt: rows a4-a6, contraction + inverse NTT (+ mask when
+ * r_dev is not NULL) from a workspace filled by the first stage. */
+int fl_he_conv2d_ntt_inputs(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *ct_in_dev,
+                            void *workspace_dev, size_t workspace_bytes, void *stream);
+int fl_he_conv2d_from_ntt(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_hat_dev,
+                          const void *workspace_dev, size_t workspace_bytes, const uint32_t *r_dev,
+                          uint32_t *ct_out_dev, void *stream);
+
+/* ---- Building blocks, exposed for tests ---- */
+
+/* In-place negacyclic NTT / inverse NTT of n RNS polynomials data_dev
+ * [n][L][N].  Forward output slot k holds a(psi^(2*brev(k)+1)) with brev the
+ * log2(N)-bit reversal; inverse undoes it (values canonical in [0, q_l)). */
+int fl_ntt_forward(fl_ctx *ctx, int n, uint32_t *data_dev, void *stream);
+int fl_ntt_inverse(fl_ctx *ctx, int n, uint32_t *data_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLASHGPU_H */

@@ -78,20 +78,21 @@ void or_negacyclic_mul(const uint32_t *a, const uint32_t *b, uint32_t N,
 /* ------------------------------------------------------------------ */
 /* DRot (Eq. 2, proof in Appendix A): c'(x) = c(x) * x^{-step} mod       */
 /* x^N + 1, i.e. coefficient i of the result is                          */
-/* (-1)^floor((i+step)/N) * c[(i+step) mod N]   (0 <= step < 2N).        */
+/* (-1)^floor((i+step)/N) * c[(i+step) mod N].  Every step Algorithm 1    */
+/* takes lies in [0, N), so i + step < 2N wraps at most once.             */
 /* ------------------------------------------------------------------ */
 static int64_t drot_coeff(const uint32_t *c, uint32_t N, uint32_t step,
                           uint32_t i)
 {
-    uint64_t idx = (uint64_t)i + step;
-    uint64_t wraps = idx / N;
-    int64_t v = (int64_t)c[idx % N];
-    return (wraps & 1) ? -v : v;
+    uint32_t idx = i + step;
+    if (idx < N) return (int64_t)c[idx];
+    return -(int64_t)c[idx - N];
 }
 
 void or_drot(const uint32_t *c, uint32_t N, uint32_t q, uint32_t step,
              uint32_t *out)
 {
+    if (step >= N) return; /* outside the domain Algorithm 1 uses */
     for (uint32_t i = 0; i < N; ++i) {
         int64_t v = drot_coeff(c, N, step, i);
         out[i] = (uint32_t)(v < 0 ? v + (int64_t)q : v) % q;
@@ -272,9 +273,8 @@ void or_conv_alg1(uint32_t N, int L, const uint32_t *q, int Cin, int k,
                             /* psum += DRot(t, offset_j) */
                             uint32_t off = (uint32_t)((j % c_n) * P);
                             for (uint32_t u = 0; u < N; ++u) {
-                                uint64_t idx = (uint64_t)u + off;
-                                int64_t v = t[idx % N];
-                                psum[u] += ((idx / N) & 1) ? -v : v;
+                                uint32_t idx = u + off;
+                                psum[u] += idx < N ? t[idx] : -t[idx - N];
                             }
                         }
                         /* one reduction per partial sum (lazy reduction) */

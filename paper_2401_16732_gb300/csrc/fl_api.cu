@@ -1,0 +1,491 @@
+// C-ABI of flashgpu (declarations and contracts in include/flashgpu.h).
+//
+// Host side of the library: parameter set-up (primes, roots of unity,
+// twiddle tables, per-limb and CRT constants), argument validation and the
+// sequencing of kernel launches.  All arithmetic on ciphertexts runs in the
+// kernels of fl_kernels.cu; nothing here computes on ciphertext data.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/flashgpu.h"
+#include "fl_launch.h"
+
+using fl::CtxConst;
+using fl::DecConst;
+using fl::GeomDims;
+typedef unsigned __int128 u128;
+
+struct fl_ctx {
+  int N, logN, L, device;
+  uint32_t t;
+  uint32_t psi[FL_MAX_L];
+  CtxConst cc;
+  DecConst dc;
+  uint32_t* tw;  // device [L][4][N]
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(FL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+uint64_t mulmod(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((u128)a * b % m); }
+
+uint64_t powmod(uint64_t b, uint64_t e, uint64_t m) {
+  uint64_t r = 1 % m;
+  b %= m;
+  while (e) {
+    if (e & 1) r = mulmod(r, b, m);
+    b = mulmod(b, b, m);
+    e >>= 1;
+  }
+  return r;
+}
+
+// Deterministic Miller-Rabin for n < 4,759,123,141 with bases 2, 7, 61
+// (Jaeschke, 1993).
+bool is_prime32(uint32_t n) {
+  if (n < 2) return false;
+  for (uint32_t p : {2u, 3u, 5u, 7u, 11u, 13u, 61u})
+    if (n % p == 0) return n == p;
+  uint32_t d = n - 1;
+  int s = 0;
+  while (!(d & 1)) d >>= 1, ++s;
+  for (uint32_t a : {2u, 7u, 61u}) {
+    uint64_t x = powmod(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int r = 1; r < s; ++r) {
+      x = mulmod(x, x, n);
+      if (x == n - 1) { comp = false; break; }
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+
+uint32_t brev(uint32_t x, int bits) {
+  uint32_t r = 0;
+  for (int i = 0; i < bits; ++i) r = (r << 1) | ((x >> i) & 1);
+  return r;
+}
+
+uint32_t shoup(uint32_t w, uint32_t q) { return (uint32_t)(((uint64_t)w << 32) / q); }
+
+GeomDims dims_of(const fl_conv_geom& g) {
+  GeomDims d;
+  d.Cin = g.Cin; d.Cout = g.Cout; d.H = g.H; d.W = g.W; d.k = g.k; d.s = g.stride; d.pad = g.pad;
+  d.Hp = g.Hp; d.Wp = g.Wp; d.Ho = g.Ho; d.Wo = g.Wo; d.Rin = g.Rin; d.Rout = g.Rout;
+  d.bands = g.bands; d.P = g.P; d.c_n = g.c_n; d.G = g.G; d.n_in = g.n_in; d.n_out = g.n_out;
+  return d;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+int check_ctx(const fl_ctx* ctx) {
+  if (!ctx) return fail(FL_ERR_ARG, "null context");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != ctx->device)
+    return fail(FL_ERR_ARG, "current device %d is not the context's device %d", dev, ctx->device);
+  return FL_OK;
+}
+
+int check_geom(const fl_ctx* ctx, const fl_conv_geom* g) {
+  if (!g) return fail(FL_ERR_ARG, "null geometry");
+  fl_conv_geom ref;
+  int rc = fl_conv_geom_make(g->N, g->Cin, g->Cout, g->H, g->W, g->k, g->stride, g->pad, &ref);
+  if (rc) return rc;
+  if (memcmp(&ref, g, sizeof ref) != 0)
+    return fail(FL_ERR_SHAPE, "geometry fields are inconsistent (build it with fl_conv_geom_make)");
+  if (g->N != ctx->N) return fail(FL_ERR_SHAPE, "geometry N=%d but context N=%d", g->N, ctx->N);
+  if (g->Cout > 65535) return fail(FL_ERR_SHAPE, "Cout=%d above 65535", g->Cout);
+  return FL_OK;
+}
+
+int check_ptrs(std::initializer_list<const void*> ps) {
+  for (const void* p : ps) {
+    if (!p) return fail(FL_ERR_ARG, "null device pointer");
+    if (!aligned16(p)) return fail(FL_ERR_ARG, "device pointer %p is not 16-byte aligned", p);
+  }
+  return FL_OK;
+}
+
+int launched(cudaError_t e, const char* what) { return e == cudaSuccess ? FL_OK : cuda_fail(e, what); }
+
+}  // namespace
+
+extern "C" {
+
+const char* fl_last_error(void) { return g_err.c_str(); }
+
+int fl_conv_geom_make(int N, int Cin, int Cout, int H, int W, int k, int stride, int pad,
+                      fl_conv_geom* out) {
+  if (!out) return fail(FL_ERR_ARG, "null output");
+  if (N < 2 || (N & (N - 1)) || N > (1 << 20)) return fail(FL_ERR_SHAPE, "N=%d is not a power of two", N);
+  if (Cin < 1 || Cout < 1 || H < 1 || W < 1 || k < 1 || stride < 1 || pad < 0)
+    return fail(FL_ERR_SHAPE, "non-positive convolution size");
+  if ((long long)Cin * Cout * k * k > (1ll << 31) || H > (1 << 16) || W > (1 << 16) || pad > (1 << 16))
+    return fail(FL_ERR_SHAPE, "convolution too large");
+  fl_conv_geom g;
+  memset(&g, 0, sizeof g);
+  g.N = N; g.Cin = Cin; g.Cout = Cout; g.H = H; g.W = W; g.k = k; g.stride = stride; g.pad = pad;
+  g.Hp = H + 2 * pad;
+  g.Wp = W + 2 * pad;
+  if (k > g.Hp || k > g.Wp) return fail(FL_ERR_SHAPE, "kernel %d larger than padded input", k);
+  g.Ho = (g.Hp - k) / stride + 1;
+  g.Wo = (g.Wp - k) / stride + 1;
+  if ((long long)g.Hp * g.Wp <= N) {
+    g.Rin = g.Hp;
+    g.Rout = g.Ho;
+    g.bands = 1;
+  } else {
+    g.Rin = N / g.Wp;
+    if (g.Rin < k) return fail(FL_ERR_SHAPE, "a band of %d padded rows of width %d exceeds N=%d", k, g.Wp, N);
+    g.Rout = (g.Rin - k) / stride + 1;
+    g.bands = (g.Ho + g.Rout - 1) / g.Rout;
+  }
+  g.P = g.Rin * g.Wp;
+  g.c_n = N / g.P;
+  g.G = (Cin + g.c_n - 1) / g.c_n;
+  g.n_in = g.bands * g.G;
+  g.n_out = Cout * g.bands;
+  *out = g;
+  return FL_OK;
+}
+
+int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
+  if (!out) return fail(FL_ERR_ARG, "null output");
+  *out = nullptr;
+  int logN = 0;
+  while ((1 << logN) < N) ++logN;
+  if ((1 << logN) != N || logN < 11 || logN > 14)
+    return fail(FL_ERR_ARG, "N=%d: supported ring degrees are 2048, 4096, 8192, 16384", N);
+  if (L < 1 || L > FL_MAX_L) return fail(FL_ERR_ARG, "L=%d outside [1, %d]", L, FL_MAX_L);
+  if (t < 3 || t >= (1u << 20) || !(t & 1)) return fail(FL_ERR_ARG, "t=%u must be odd in [3, 2^20)", t);
+  fl_ctx* c = new fl_ctx();
+  c->N = N; c->logN = logN; c->L = L; c->t = t;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDevice"); }
+
+  // primes: largest below 2^30 with q = 1 mod 2N, descending
+  std::vector<uint32_t> qs;
+  const uint64_t step = 2ull * N;
+  for (uint64_t cand = ((1ull << 30) - 2) / step * step + 1; cand > step && (int)qs.size() < L; cand -= step)
+    if (is_prime32((uint32_t)cand)) qs.push_back((uint32_t)cand);
+  if ((int)qs.size() < L) { delete c; return fail(FL_ERR_ARG, "not enough NTT-friendly primes"); }
+
+  u128 Q = 1;
+  for (uint32_t q : qs) Q *= q;
+  const u128 Delta = Q / t;
+  std::vector<uint32_t> host((size_t)L * 4 * N);
+  memset(&c->cc, 0, sizeof c->cc);
+  memset(&c->dc, 0, sizeof c->dc);
+  c->cc.L = L; c->cc.t = t;
+  c->dc.L = L; c->dc.t = t;
+  c->dc.qhi = (uint64_t)(Q >> 64); c->dc.qlo = (uint64_t)Q;
+  for (int l = 0; l < L; ++l) {
+    const uint32_t q = qs[l];
+    // psi: first g^((q-1)/2N), g = 2, 3, ..., with psi^N = -1 (order 2N)
+    uint32_t psi = 0;
+    for (uint64_t g = 2; g < q && !psi; ++g) {
+      uint64_t cand = powmod(g, (q - 1) / step, q);
+      if (powmod(cand, N, q) == q - 1) psi = (uint32_t)cand;
+    }
+    const uint32_t psi_inv = (uint32_t)powmod(psi, q - 2, q);
+    c->psi[l] = psi;
+    uint32_t* T = host.data() + (size_t)l * 4 * N;
+    for (int i = 0; i < N; ++i) {
+      const uint32_t f = (uint32_t)powmod(psi, brev(i, logN), q);
+      const uint32_t v = (uint32_t)powmod(psi_inv, brev(i, logN), q);
+      T[fl::TW_FWD * N + i] = f;
+      T[fl::TW_FWD_SH * N + i] = shoup(f, q);
+      T[fl::TW_INV * N + i] = v;
+      T[fl::TW_INV_SH * N + i] = shoup(v, q);
+    }
+    fl::LimbConst& lc = c->cc.limb[l];
+    lc.q = q;
+    lc.two_q = 2 * q;
+    lc.n_inv = (uint32_t)powmod(N, q - 2, q);
+    lc.n_inv_sh = shoup(lc.n_inv, q);
+    lc.last_w = (uint32_t)mulmod(T[fl::TW_INV * N + 1], lc.n_inv, q);
+    lc.last_w_sh = shoup(lc.last_w, q);
+    lc.delta = (uint32_t)(Delta % q);
+    lc.delta_sh = shoup(lc.delta, q);
+    lc.mu = ~0ull / q;
+    const u128 Ql = Q / q;
+    c->dc.q[l] = q;
+    c->dc.inv[l] = (uint32_t)powmod((uint64_t)(Ql % q), q - 2, q);
+    c->dc.Qhi[l] = (uint64_t)(Ql >> 64);
+    c->dc.Qlo[l] = (uint64_t)Ql;
+  }
+  if ((e = fl::launch_setup(logN)) != cudaSuccess) { delete c; return cuda_fail(e, "kernel set-up"); }
+  if ((e = cudaMalloc(&c->tw, host.size() * 4)) != cudaSuccess) {
+    delete c;
+    return fail(FL_ERR_OOM, "twiddle tables: %s", cudaGetErrorString(e));
+  }
+  if ((e = cudaMemcpy(c->tw, host.data(), host.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(c->tw);
+    delete c;
+    return cuda_fail(e, "twiddle upload");
+  }
+  *out = c;
+  return FL_OK;
+}
+
+void fl_ctx_destroy(fl_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->tw) cudaFree(ctx->tw);
+  delete ctx;
+}
+
+int fl_ctx_params(const fl_ctx* ctx, uint32_t* primes_host, uint32_t* delta_host, uint32_t* psi_host) {
+  if (!ctx) return fail(FL_ERR_ARG, "null context");
+  for (int l = 0; l < ctx->L; ++l) {
+    if (primes_host) primes_host[l] = ctx->cc.limb[l].q;
+    if (delta_host) delta_host[l] = ctx->cc.limb[l].delta;
+    if (psi_host) psi_host[l] = ctx->psi[l];
+  }
+  return FL_OK;
+}
+
+int fl_keygen(fl_ctx* ctx, const int8_t* s_dev, uint32_t* sk_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (!s_dev) return fail(FL_ERR_ARG, "null secret");
+  if ((rc = check_ptrs({sk_dev}))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = launched(fl::launch_sk_expand(s_dev, sk_dev, ctx->N, ctx->cc, st), "sk expand"))) return rc;
+  return launched(fl::launch_ntt_fwd(ctx->logN, ctx->L, sk_dev, ctx->L, ctx->L, sk_dev, ctx->L, ctx->L, 1,
+                                     ctx->tw, ctx->cc, st),
+                  "sk ntt");
+}
+
+int fl_encrypt(fl_ctx* ctx, const uint32_t* sk_dev, const fl_conv_geom* geom, int B, const int32_t* x_dev,
+               const uint32_t* a_dev, const int32_t* e_dev, uint32_t* ct_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_geom(ctx, geom))) return rc;
+  if (B < 0) return fail(FL_ERR_ARG, "B=%d", B);
+  if (B == 0) return FL_OK;
+  if ((rc = check_ptrs({sk_dev, a_dev, ct_dev})) || !x_dev || !e_dev)
+    return rc ? rc : fail(FL_ERR_ARG, "null input");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = B * geom->n_in, L = ctx->L, N = ctx->N;
+  // c1 = a
+  cudaError_t e = cudaMemcpy2DAsync(ct_dev + (size_t)L * N, (size_t)2 * L * N * 4, a_dev, (size_t)L * N * 4,
+                                    (size_t)L * N * 4, n, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "c1 copy");
+  // c0 slot <- NTT(a)
+  if ((rc = launched(fl::launch_ntt_fwd(ctx->logN, n * L, a_dev, n * L, 0, ct_dev, L, 2 * L, 1, ctx->tw,
+                                        ctx->cc, st),
+                     "encrypt ntt")))
+    return rc;
+  // c0 <- Delta*m - INTT(NTT(a) * NTT(s)) - e
+  return launched(fl::launch_pmul_intt(ctx->logN, 1, n, nullptr, ct_dev, sk_dev, x_dev, e_dev, dims_of(*geom),
+                                       ctx->tw, ctx->cc, st),
+                  "encrypt");
+}
+
+int fl_encrypt_online(fl_ctx* ctx, const fl_conv_geom* geom, int B, const int32_t* x_dev,
+                      const uint32_t* enc0_dev, uint32_t* ct_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_geom(ctx, geom))) return rc;
+  if (B < 0) return fail(FL_ERR_ARG, "B=%d", B);
+  if (B == 0) return FL_OK;
+  if ((rc = check_ptrs({enc0_dev, ct_dev})) || !x_dev) return rc ? rc : fail(FL_ERR_ARG, "null input");
+  return launched(fl::launch_enc_online(enc0_dev, ct_dev, x_dev, dims_of(*geom), B * geom->n_in, ctx->N,
+                                        ctx->cc, (cudaStream_t)stream),
+                  "online encrypt");
+}
+
+size_t fl_decrypt_workspace_bytes(const fl_ctx* ctx, int n) {
+  return ctx && n > 0 ? (size_t)n * ctx->L * ctx->N * 4 : 0;
+}
+
+int fl_decrypt(fl_ctx* ctx, const uint32_t* sk_dev, int n, const uint32_t* ct_dev, uint32_t* m_dev,
+               void* workspace_dev, size_t workspace_bytes, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
+  if (n == 0) return FL_OK;
+  if ((rc = check_ptrs({sk_dev, ct_dev, m_dev, workspace_dev}))) return rc;
+  if (workspace_bytes < fl_decrypt_workspace_bytes(ctx, n))
+    return fail(FL_ERR_ARG, "workspace %zu bytes, need %zu", workspace_bytes, fl_decrypt_workspace_bytes(ctx, n));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = ctx->L;
+  uint32_t* ws = (uint32_t*)workspace_dev;
+  // ws <- NTT(c1): source row r is ciphertext r/L, limb r%L of component 1
+  if ((rc = launched(fl::launch_ntt_fwd(ctx->logN, n * L, ct_dev + (size_t)L * ctx->N, L, 2 * L, ws, n * L, 0, 1,
+                                        ctx->tw, ctx->cc, st),
+                     "decrypt ntt")))
+    return rc;
+  GeomDims none;
+  memset(&none, 0, sizeof none);
+  if ((rc = launched(fl::launch_pmul_intt(ctx->logN, 0, n, ws, const_cast<uint32_t*>(ct_dev), sk_dev, nullptr,
+                                          nullptr, none, ctx->tw, ctx->cc, st),
+                     "decrypt phase")))
+    return rc;
+  return launched(fl::launch_dec_round(ws, m_dev, n, ctx->N, ctx->dc, st), "decrypt round");
+}
+
+int fl_extract_outputs(const fl_conv_geom* geom, int B, const uint32_t* m_dev, int32_t* y_dev, void* stream) {
+  if (!geom) return fail(FL_ERR_ARG, "null geometry");
+  fl_conv_geom ref;
+  int rc = fl_conv_geom_make(geom->N, geom->Cin, geom->Cout, geom->H, geom->W, geom->k, geom->stride, geom->pad,
+                             &ref);
+  if (rc) return rc;
+  if (memcmp(&ref, geom, sizeof ref)) return fail(FL_ERR_SHAPE, "geometry fields are inconsistent");
+  if (B < 0) return fail(FL_ERR_ARG, "B=%d", B);
+  if (B == 0) return FL_OK;
+  if (!m_dev || !y_dev) return fail(FL_ERR_ARG, "null pointer");
+  return launched(fl::launch_extract(m_dev, y_dev, dims_of(*geom), B, geom->N, (cudaStream_t)stream), "extract");
+}
+
+size_t fl_weights_bytes(const fl_ctx* ctx, const fl_conv_geom* geom) {
+  return ctx && geom ? (size_t)ctx->L * geom->Cout * geom->G * ctx->N * 4 : 0;
+}
+
+int fl_encode_weights(fl_ctx* ctx, const fl_conv_geom* geom, const int8_t* w_dev, uint32_t* w_hat_dev,
+                      void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_geom(ctx, geom))) return rc;
+  if ((rc = check_ptrs({w_hat_dev})) || !w_dev) return rc ? rc : fail(FL_ERR_ARG, "null filters");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(w_hat_dev, 0, fl_weights_bytes(ctx, geom), st);
+  if (e != cudaSuccess) return cuda_fail(e, "weights memset");
+  if ((rc = launched(fl::launch_w_scatter(w_dev, w_hat_dev, dims_of(*geom), ctx->N, ctx->cc, st), "w scatter")))
+    return rc;
+  const int rows = ctx->L * geom->Cout * geom->G;
+  return launched(fl::launch_ntt_fwd(ctx->logN, rows, w_hat_dev, rows, 0, w_hat_dev, rows, 0, geom->Cout * geom->G,
+                                     ctx->tw, ctx->cc, st),
+                  "weights ntt");
+}
+
+size_t fl_he_conv2d_workspace_bytes(const fl_ctx* ctx, const fl_conv_geom* geom, int B) {
+  return ctx && geom && B > 0 ? (size_t)B * geom->n_in * 2 * ctx->L * ctx->N * 4 : 0;
+}
+
+static int conv_checks(fl_ctx* ctx, const fl_conv_geom* geom, int B, size_t workspace_bytes) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_geom(ctx, geom))) return rc;
+  if (B < 0) return fail(FL_ERR_ARG, "B=%d", B);
+  const size_t need = fl_he_conv2d_workspace_bytes(ctx, geom, B);
+  if (workspace_bytes < need) return fail(FL_ERR_ARG, "workspace %zu bytes, need %zu", workspace_bytes, need);
+  if ((long long)B * geom->bands > 0x7fffffff) return fail(FL_ERR_ARG, "batch too large");
+  return FL_OK;
+}
+
+static int stage_ntt(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* ct_in_dev, void* ws,
+                     cudaStream_t st) {
+  const int rows = B * geom->n_in * 2 * ctx->L;
+  return launched(fl::launch_ntt_fwd(ctx->logN, rows, ct_in_dev, rows, 0, (uint32_t*)ws, rows, 0, 1, ctx->tw,
+                                     ctx->cc, st),
+                  "input ntt");
+}
+
+static int stage_conv(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_hat_dev, const void* ws,
+                      const uint32_t* r_dev, uint32_t* ct_out_dev, cudaStream_t st) {
+  fl::ConvDims cd{geom->Cout, geom->G, geom->n_in, geom->n_out, geom->bands};
+  return launched(fl::launch_conv_intt(ctx->logN, B, cd, w_hat_dev, (const uint32_t*)ws, ct_out_dev, r_dev, ctx->tw,
+                                       ctx->cc, st),
+                  "contraction + intt");
+}
+
+static int he_conv2d_impl(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_hat_dev,
+                          const uint32_t* ct_in_dev, const uint32_t* r_dev, uint32_t* ct_out_dev,
+                          void* workspace_dev, size_t workspace_bytes, void* stream) {
+  int rc;
+  if ((rc = conv_checks(ctx, geom, B, workspace_bytes))) return rc;
+  if (B == 0) return FL_OK;
+  if ((rc = check_ptrs({w_hat_dev, ct_in_dev, ct_out_dev, workspace_dev}))) return rc;
+  if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = stage_ntt(ctx, geom, B, ct_in_dev, workspace_dev, st))) return rc;
+  return stage_conv(ctx, geom, B, w_hat_dev, workspace_dev, r_dev, ct_out_dev, st);
+}
+
+int fl_he_conv2d_ntt_inputs(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* ct_in_dev,
+                            void* workspace_dev, size_t workspace_bytes, void* stream) {
+  int rc;
+  if ((rc = conv_checks(ctx, geom, B, workspace_bytes))) return rc;
+  if (B == 0) return FL_OK;
+  if ((rc = check_ptrs({ct_in_dev, workspace_dev}))) return rc;
+  return stage_ntt(ctx, geom, B, ct_in_dev, workspace_dev, (cudaStream_t)stream);
+}
+
+int fl_he_conv2d_from_ntt(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_hat_dev,
+                          const void* workspace_dev, size_t workspace_bytes, const uint32_t* r_dev,
+                          uint32_t* ct_out_dev, void* stream) {
+  int rc;
+  if ((rc = conv_checks(ctx, geom, B, workspace_bytes))) return rc;
+  if (B == 0) return FL_OK;
+  if ((rc = check_ptrs({w_hat_dev, workspace_dev, ct_out_dev}))) return rc;
+  if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
+  return stage_conv(ctx, geom, B, w_hat_dev, workspace_dev, r_dev, ct_out_dev, (cudaStream_t)stream);
+}
+
+int fl_he_conv2d(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_hat_dev, const uint32_t* ct_in_dev,
+                 uint32_t* ct_out_dev, void* workspace_dev, size_t workspace_bytes, void* stream) {
+  return he_conv2d_impl(ctx, geom, B, w_hat_dev, ct_in_dev, nullptr, ct_out_dev, workspace_dev, workspace_bytes,
+                        stream);
+}
+
+int fl_he_conv2d_mask(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_hat_dev,
+                      const uint32_t* ct_in_dev, const uint32_t* r_dev, uint32_t* ct_out_dev, void* workspace_dev,
+                      size_t workspace_bytes, void* stream) {
+  if (!r_dev) return fail(FL_ERR_ARG, "null mask");
+  return he_conv2d_impl(ctx, geom, B, w_hat_dev, ct_in_dev, r_dev, ct_out_dev, workspace_dev, workspace_bytes,
+                        stream);
+}
+
+int fl_mask_to_share(fl_ctx* ctx, int n, uint32_t* ct_dev, const uint32_t* r_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
+  if (n == 0) return FL_OK;
+  if ((rc = check_ptrs({ct_dev, r_dev}))) return rc;
+  return launched(fl::launch_mask(ct_dev, r_dev, n, ctx->N, ctx->cc, (cudaStream_t)stream), "mask");
+}
+
+int fl_ntt_forward(fl_ctx* ctx, int n, uint32_t* data_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
+  if (n == 0) return FL_OK;
+  if ((rc = check_ptrs({data_dev}))) return rc;
+  const int rows = n * ctx->L;
+  return launched(fl::launch_ntt_fwd(ctx->logN, rows, data_dev, rows, 0, data_dev, rows, 0, 1, ctx->tw, ctx->cc,
+                                     (cudaStream_t)stream),
+                  "ntt");
+}
+
+int fl_ntt_inverse(fl_ctx* ctx, int n, uint32_t* data_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
+  if (n == 0) return FL_OK;
+  if ((rc = check_ptrs({data_dev}))) return rc;
+  return launched(fl::launch_ntt_inv(ctx->logN, n * ctx->L, data_dev, ctx->tw, ctx->cc, (cudaStream_t)stream),
+                  "intt");
+}
+
+}  // extern "C"

@@ -1,0 +1,469 @@
+// CUDA kernels of the HE-convolution path and their launchers.
+//
+//   k_ntt_fwd     forward negacyclic NTT, out of place (row a3; also keygen,
+//                 encryption and weight encoding)
+//   k_ntt_inv     inverse NTT, in place (test entry point)
+//   k_conv_intt   per-slot contraction mod q_l + inverse NTT + optional mask
+//                 epilogue: rows a4, a5, a6 fused, one CTA per output
+//                 (image/band, output channel, limb), both components
+//   k_pmul_intt   NTT-domain product with the secret key + inverse NTT +
+//                 encryption / decryption epilogue (row a1, client side)
+//   k_dec_round   exact RNS scale-and-round for decryption
+//   k_mask        standalone mask addition (row a6)
+//   k_w_scatter   weight polynomial construction (row a2)
+#include <cuda_runtime.h>
+
+#include "fl_device.cuh"
+#include "fl_launch.h"
+
+namespace fl {
+
+// Resident CTAs per SM the register budget is sized for: the fused kernel
+// holds two padded polynomials in shared memory (3 CTAs of 256 threads at
+// N = 8192), the single-polynomial kernels aim at 1024 threads per SM.
+template <int LOGN> constexpr int minb_two_polys() { return (768 >> (LOGN - 5)) > 0 ? (768 >> (LOGN - 5)) : 1; }
+template <int LOGN> constexpr int minb_one_poly() { return 1024 >> (LOGN - 5); }
+
+// --------------------------------------------------------------------------
+// Forward NTT: one CTA per polynomial row.  Row r of the source starts at
+// src + ((r / src_per) * src_stride + r % src_per) * N (same for dst), and
+// uses limb (r / limb_div) % L.
+// --------------------------------------------------------------------------
+template <int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
+    k_ntt_fwd(const uint32_t* __restrict__ src, int src_per, int src_stride, uint32_t* dst,
+              int dst_per, int dst_stride, int limb_div, const uint32_t* __restrict__ tw,
+              CtxConst cc) {
+  constexpr int N = 1 << LOGN, T = N / 32;
+  extern __shared__ uint32_t sm[];
+  const int r = blockIdx.x, tid = threadIdx.x;
+  const int l = (r / limb_div) % cc.L;
+  const LimbConst lc = cc.limb[l];
+  const uint32_t* x = src + ((size_t)(r / src_per) * src_stride + r % src_per) * N;
+  uint32_t* y = dst + ((size_t)(r / dst_per) * dst_stride + r % dst_per) * N;
+  ntt_forward_to_smem<LOGN>(sm, x, tw + (size_t)l * 4 * N, lc, tid);
+  __syncthreads();
+  for (int v = tid; v < N / 4; v += T) {
+    uint4 o;
+    o.x = sm[pad(4 * v + 0)];
+    o.y = sm[pad(4 * v + 1)];
+    o.z = sm[pad(4 * v + 2)];
+    o.w = sm[pad(4 * v + 3)];
+    reinterpret_cast<uint4*>(y)[v] = o;
+  }
+}
+
+// Inverse NTT in place on contiguous rows [n][L][N].
+template <int LOGN>
+__global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
+    k_ntt_inv(uint32_t* data, const uint32_t* __restrict__ tw, CtxConst cc) {
+  constexpr int N = 1 << LOGN, T = N / 32;
+  extern __shared__ uint32_t sm[];
+  const int r = blockIdx.x, tid = threadIdx.x;
+  const int l = r % cc.L;
+  const LimbConst lc = cc.limb[l];
+  uint32_t* x = data + (size_t)r * N;
+  for (int i = tid; i < N; i += T) sm[pad(i)] = x[i];
+  __syncthreads();
+  intt_from_smem<LOGN>(sm, tw + (size_t)l * 4 * N, lc, tid,
+                       [&](uint32_t v, int u) { x[u] = csub(v, lc.q); });
+}
+
+// --------------------------------------------------------------------------
+// Fused contraction + inverse NTT (+ mask).  Grid (B*bands, Cout, L).
+//   Y_c[u] = sum_g W[l][i][g][u] * C[b][band*G+g][c][l][u]  mod q_l
+// accumulated in 64 bits (products < 2^60; a Barrett fold every 16 terms),
+// reduced once, inverse-transformed in shared memory and stored with
+// streaming stores; c0 optionally gets + Delta_l * r[u].
+// --------------------------------------------------------------------------
+template <int LOGN, bool MASK>
+__global__ void __launch_bounds__((1 << LOGN) / 32, minb_two_polys<LOGN>())
+    k_conv_intt(const uint32_t* __restrict__ w_hat, const uint32_t* __restrict__ c_hat,
+                uint32_t* __restrict__ out, const uint32_t* __restrict__ r, ConvDims cd,
+                const uint32_t* __restrict__ tw, CtxConst cc) {
+  constexpr int N = 1 << LOGN, T = N / 32, SW = Geo<LOGN>::SMEM_WORDS;
+  extern __shared__ uint32_t sm[];
+  uint32_t* s0 = sm;
+  uint32_t* s1 = sm + SW;
+  const int tid = threadIdx.x;
+  const int bb = blockIdx.x, i = blockIdx.y, l = blockIdx.z, L = cc.L;
+  const int b = bb / cd.bands, band = bb % cd.bands;
+  const LimbConst lc = cc.limb[l];
+  const size_t ct_words = (size_t)2 * L * N;
+  const uint4* W = reinterpret_cast<const uint4*>(w_hat + ((size_t)l * cd.Cout + i) * cd.G * N);
+  const uint32_t* C = c_hat + ((size_t)b * cd.n_in + (size_t)band * cd.G) * ct_words + (size_t)l * N;
+
+#pragma unroll 1
+  for (int v = tid; v < N / 4; v += T) {
+    uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+#pragma unroll 2
+    for (int g = 0; g < cd.G; ++g) {
+      const uint4 w = __ldg(W + (size_t)g * (N / 4) + v);
+      const uint4 x0 = __ldg(reinterpret_cast<const uint4*>(C + g * ct_words) + v);
+      const uint4 x1 = __ldg(reinterpret_cast<const uint4*>(C + g * ct_words + (size_t)L * N) + v);
+      a0[0] += (uint64_t)w.x * x0.x;
+      a0[1] += (uint64_t)w.y * x0.y;
+      a0[2] += (uint64_t)w.z * x0.z;
+      a0[3] += (uint64_t)w.w * x0.w;
+      a1[0] += (uint64_t)w.x * x1.x;
+      a1[1] += (uint64_t)w.y * x1.y;
+      a1[2] += (uint64_t)w.z * x1.z;
+      a1[3] += (uint64_t)w.w * x1.w;
+      if (((g + 1) & 15) == 0 && g + 1 < cd.G) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          a0[j] = barrett64(a0[j], lc.q, lc.mu);
+          a1[j] = barrett64(a1[j], lc.q, lc.mu);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      s0[pad(4 * v + j)] = barrett64(a0[j], lc.q, lc.mu);
+      s1[pad(4 * v + j)] = barrett64(a1[j], lc.q, lc.mu);
+    }
+  }
+  __syncthreads();
+
+  const size_t oct = (size_t)b * cd.n_out + (size_t)i * cd.bands + band;
+  uint32_t* o0 = out + oct * ct_words + (size_t)l * N;
+  uint32_t* o1 = o0 + (size_t)L * N;
+  const uint32_t* rr = MASK ? r + oct * N : nullptr;
+  const uint32_t* twl = tw + (size_t)l * 4 * N;
+  // One loop body for both components: inlining two transforms lets the
+  // compiler share (and keep live) their twiddle loads, which spills.
+#pragma unroll 1
+  for (int c = 0; c < 2; ++c) {
+    uint32_t* op = c ? o1 : o0;
+    if (c) __syncthreads();
+    intt_from_smem<LOGN>(c ? s1 : s0, twl, lc, tid, [&](uint32_t v, int u) {
+      uint32_t x = v;
+      if (MASK && c == 0) x += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, lc.q);
+      __stcs(op + u, csub(csub(x, lc.two_q), lc.q));
+    });
+  }
+}
+
+// --------------------------------------------------------------------------
+// Client side: NTT-domain product with the secret key + inverse NTT.
+// Grid (n, L).  MODE_DEC: xhat = ws row [n][L][N] (NTT of c1); result
+// [c0 + c1*s] written back to the same ws row.  MODE_ENC: xhat = c0 slot of
+// ct (holds NTT(a)); result c0 = Delta*m - a*s - e written to that slot.
+// --------------------------------------------------------------------------
+enum { MODE_DEC = 0, MODE_ENC = 1 };
+
+__device__ __forceinline__ uint32_t packed_input(const int32_t* __restrict__ x, const GeomDims& g,
+                                                 int b, int ci, int u) {
+  // Coefficient u of input ciphertext ci = band*G + gg of image b: channel
+  // j = gg*c_n + u/P, padded row band*Rout*s + (u%P)/Wp, padded column (u%P)%Wp.
+  const int band = ci / g.G, gg = ci % g.G;
+  const int jj = u / g.P;
+  if (jj >= g.c_n) return 0;
+  const int j = gg * g.c_n + jj;
+  if (j >= g.Cin) return 0;
+  const int rem = u - jj * g.P;
+  const int yy = band * g.Rout * g.s + rem / g.Wp - g.pad;
+  const int xx = rem % g.Wp - g.pad;
+  if (yy < 0 || yy >= g.H || xx < 0 || xx >= g.W) return 0;
+  return (uint32_t)x[(((size_t)b * g.Cin + j) * g.H + yy) * g.W + xx];
+}
+
+template <int LOGN, int MODE>
+__global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
+    k_pmul_intt(uint32_t* __restrict__ ws, uint32_t* __restrict__ ct,
+                const uint32_t* __restrict__ sk, const int32_t* __restrict__ x,
+                const int32_t* __restrict__ e, GeomDims gd, const uint32_t* __restrict__ tw,
+                CtxConst cc) {
+  constexpr int N = 1 << LOGN, T = N / 32;
+  extern __shared__ uint32_t sm[];
+  const int n = blockIdx.x, l = blockIdx.y, L = cc.L, tid = threadIdx.x;
+  const LimbConst lc = cc.limb[l];
+  uint32_t* row = MODE == MODE_DEC ? ws + ((size_t)n * L + l) * N : ct + ((size_t)n * 2 * L + l) * N;
+  const uint32_t* s = sk + (size_t)l * N;
+  for (int i = tid; i < N; i += T) {
+    uint64_t p = (uint64_t)row[i] * __ldg(s + i);
+    sm[pad(i)] = barrett64(p, lc.q, lc.mu);
+  }
+  __syncthreads();
+  if (MODE == MODE_DEC) {
+    const uint32_t* c0 = ct + ((size_t)n * 2 * L + l) * N;
+    intt_from_smem<LOGN>(sm, tw + (size_t)l * 4 * N, lc, tid, [&](uint32_t v, int u) {
+      row[u] = csub(csub(v + __ldg(c0 + u), lc.two_q), lc.q);
+    });
+  } else {
+    const int b = n / gd.n_in, ci = n % gd.n_in;
+    intt_from_smem<LOGN>(sm, tw + (size_t)l * 4 * N, lc, tid, [&](uint32_t v, int u) {
+      // Delta*m - a*s - e  (v = a*s in [0, 2q))
+      uint32_t m = packed_input(x, gd, b, ci, u);
+      uint32_t dm = csub(shoup_mul(m, lc.delta, lc.delta_sh, lc.q), lc.q);  // [0, q)
+      int32_t ev = __ldg(e + (size_t)n * N + u);
+      uint32_t em = ev >= 0 ? (uint32_t)ev : lc.q - (uint32_t)(-ev);  // e mod q, |e| < 2^20
+      uint32_t as = csub(v, lc.q);
+      uint32_t r = dm + lc.two_q - as - em;  // (0, 3q): dm, as, em all in [0, q)
+      row[u] = csub(csub(r, lc.two_q), lc.q);
+    });
+  }
+}
+
+// Exact scale-and-round: x = [c0 + c1 s]_q from its residues x_l.
+// y_l = x_l * (q/q_l)^-1 mod q_l, so t*x/q = sum_l y_l*t/q_l - k*t for an
+// integer k.  With y_l*t = a_l*q_l + b_l: m = (sum a_l + round(S)) mod t,
+// S = sum b_l/q_l = (sum b_l*(q/q_l)) / q, rounded exactly in 128-bit
+// integers (q odd, so S is never a half-integer).
+__global__ void k_dec_round(const uint32_t* __restrict__ ws, uint32_t* __restrict__ m, int n, int N,
+                            DecConst dc) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * N) return;
+  const size_t c = idx / N, u = idx % N;
+  typedef unsigned __int128 u128;
+  u128 num = 0;
+  uint64_t asum = 0;
+  for (int l = 0; l < dc.L; ++l) {
+    const uint32_t q = dc.q[l];
+    uint32_t xl = ws[(c * dc.L + l) * N + u];
+    uint32_t y = (uint32_t)(((uint64_t)xl * dc.inv[l]) % q);
+    uint64_t yt = (uint64_t)y * dc.t;
+    uint64_t a = yt / q;
+    uint64_t bl = yt - a * q;
+    asum += a;
+    num += (u128)bl * (((u128)dc.Qhi[l] << 64) | dc.Qlo[l]);
+  }
+  const u128 Q = ((u128)dc.qhi << 64) | dc.qlo;
+  const u128 two = num << 1;
+  uint32_t rnd = 0;
+  for (int j = 0; j < dc.L; ++j)
+    if (two >= (u128)(2 * j + 1) * Q) ++rnd;
+  m[idx] = (uint32_t)((asum + rnd) % dc.t);
+}
+
+__global__ void k_extract(const uint32_t* __restrict__ m, int32_t* __restrict__ y, GeomDims g, int B,
+                          int N) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t total = (size_t)B * g.Cout * g.Ho * g.Wo;
+  if (idx >= total) return;
+  size_t r = idx;
+  const int ox = r % g.Wo; r /= g.Wo;
+  const int oy = r % g.Ho; r /= g.Ho;
+  const int i = r % g.Cout;
+  const int b = (int)(r / g.Cout);
+  const int band = oy / g.Rout, oyl = oy % g.Rout;
+  const uint32_t* poly = m + ((size_t)b * g.n_out + (size_t)i * g.bands + band) * N;
+  y[idx] = (int32_t)poly[(g.s * oyl) * g.Wp + g.s * ox];
+}
+
+// c0 <- c0 + Delta_l * r  for cts [n][2][L][N]; one thread per 4 coefficients.
+__global__ void k_mask(uint32_t* __restrict__ ct, const uint32_t* __restrict__ r, int n, int N,
+                       CtxConst cc) {
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int L = cc.L;
+  const size_t per_ct = (size_t)L * N / 4;
+  if (v >= (size_t)n * per_ct) return;
+  const size_t c = v / per_ct, rem = v % per_ct;
+  const int l = (int)(rem / (N / 4));
+  const size_t u4 = rem % (N / 4);
+  const LimbConst lc = cc.limb[l];
+  uint4* p = reinterpret_cast<uint4*>(ct + (c * 2 * L + l) * N) + u4;
+  const uint4 rv = __ldg(reinterpret_cast<const uint4*>(r + c * N) + u4);
+  uint4 x = *p;
+  x.x = csub(csub(x.x + shoup_mul(rv.x, lc.delta, lc.delta_sh, lc.q), lc.two_q), lc.q);
+  x.y = csub(csub(x.y + shoup_mul(rv.y, lc.delta, lc.delta_sh, lc.q), lc.two_q), lc.q);
+  x.z = csub(csub(x.z + shoup_mul(rv.z, lc.delta, lc.delta_sh, lc.q), lc.two_q), lc.q);
+  x.w = csub(csub(x.w + shoup_mul(rv.w, lc.delta, lc.delta_sh, lc.q), lc.two_q), lc.q);
+  *p = x;
+}
+
+// Online encryption (Algorithm 2): c0 <- enc0.c0 + Delta*m, c1 <- enc0.c1.
+__global__ void k_enc_online(const uint32_t* __restrict__ enc0, uint32_t* __restrict__ ct,
+                             const int32_t* __restrict__ x, GeomDims gd, int n, int N,
+                             CtxConst cc) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int L = cc.L;
+  if (idx >= (size_t)n * 2 * L * N) return;
+  const int u = idx % N;
+  const int l = (idx / N) % L;
+  const int comp = (idx / ((size_t)L * N)) % 2;
+  const int c = (int)(idx / ((size_t)2 * L * N));
+  uint32_t v = enc0[idx];
+  if (comp == 0) {
+    const LimbConst lc = cc.limb[l];
+    const uint32_t m = packed_input(x, gd, c / gd.n_in, c % gd.n_in, u);
+    v = csub(csub(v + shoup_mul(m, lc.delta, lc.delta_sh, lc.q), lc.two_q), lc.q);
+  }
+  ct[idx] = v;
+}
+
+// Weight polynomial construction: one thread per (l, i, j, ky, kx).  Tap
+// w[i][j][ky][kx] lands on x^-e, e = ky*Wp + kx + (j mod c_n)*P, of W_{i,g},
+// g = j / c_n; x^-e = -x^(N-e) for e > 0.  Exponents within one (i, g) are
+// distinct, so every coefficient is written at most once (buffer pre-zeroed).
+__global__ void k_w_scatter(const int8_t* __restrict__ w, uint32_t* __restrict__ w_hat, GeomDims g,
+                            int N, CtxConst cc) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t per_l = (size_t)g.Cout * g.Cin * g.k * g.k;
+  if (idx >= per_l * cc.L) return;
+  const int l = (int)(idx / per_l);
+  size_t r = idx % per_l;
+  const int kx = r % g.k; r /= g.k;
+  const int ky = r % g.k; r /= g.k;
+  const int j = r % g.Cin;
+  const int i = (int)(r / g.Cin);
+  const int gg = j / g.c_n, jj = j % g.c_n;
+  const int e = ky * g.Wp + kx + jj * g.P;
+  const int wv = w[(((size_t)i * g.Cin + j) * g.k + ky) * g.k + kx];
+  const uint32_t q = cc.limb[l].q;
+  int pos;
+  uint32_t val;
+  if (e == 0) {
+    pos = 0;
+    val = wv >= 0 ? (uint32_t)wv : q - (uint32_t)(-wv);
+  } else {
+    pos = N - e;
+    val = wv > 0 ? q - (uint32_t)wv : (uint32_t)(-wv);
+  }
+  w_hat[(((size_t)l * g.Cout + i) * g.G + gg) * N + pos] = val;
+}
+
+// Secret key expansion: s (ternary int8) -> residues [L][N].
+__global__ void k_sk_expand(const int8_t* __restrict__ s, uint32_t* __restrict__ out, int N,
+                            CtxConst cc) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)cc.L * N) return;
+  const int l = (int)(idx / N);
+  const int sv = s[idx % N];
+  const uint32_t q = cc.limb[l].q;
+  out[idx] = sv >= 0 ? (uint32_t)sv : q - (uint32_t)(-sv);
+}
+
+// --------------------------------------------------------------------------
+// Launchers
+// --------------------------------------------------------------------------
+static inline int blocks_for(size_t n, int t) { return (int)((n + t - 1) / t); }
+
+template <int LOGN>
+static cudaError_t setup_smem() {
+  constexpr int SW = Geo<LOGN>::SMEM_WORDS;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_ntt_fwd<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4))) return e;
+  if ((e = cudaFuncSetAttribute(k_ntt_inv<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4))) return e;
+  if ((e = cudaFuncSetAttribute(k_conv_intt<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SW * 4))) return e;
+  if ((e = cudaFuncSetAttribute(k_conv_intt<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SW * 4))) return e;
+  if ((e = cudaFuncSetAttribute(k_pmul_intt<LOGN, MODE_DEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4))) return e;
+  if ((e = cudaFuncSetAttribute(k_pmul_intt<LOGN, MODE_ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4))) return e;
+  return cudaSuccess;
+}
+
+cudaError_t launch_setup(int logn) {
+  switch (logn) {
+    case 11: return setup_smem<11>();
+    case 12: return setup_smem<12>();
+    case 13: return setup_smem<13>();
+    case 14: return setup_smem<14>();
+  }
+  return cudaErrorInvalidValue;
+}
+
+#define FL_DISPATCH(logn, CALL)            \
+  switch (logn) {                          \
+    case 11: { constexpr int LG = 11; CALL; break; } \
+    case 12: { constexpr int LG = 12; CALL; break; } \
+    case 13: { constexpr int LG = 13; CALL; break; } \
+    case 14: { constexpr int LG = 14; CALL; break; } \
+    default: return cudaErrorInvalidValue;  \
+  }
+
+cudaError_t launch_ntt_fwd(int logn, int rows, const uint32_t* src, int src_per, int src_stride,
+                           uint32_t* dst, int dst_per, int dst_stride, int limb_div,
+                           const uint32_t* tw, const CtxConst& cc, cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  const int N = 1 << logn;
+  const size_t smem = (size_t)(N + N / 32) * 4;
+  FL_DISPATCH(logn, (k_ntt_fwd<LG><<<rows, N / 32, smem, st>>>(src, src_per, src_stride, dst, dst_per,
+                                                                dst_stride, limb_div, tw, cc)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ntt_inv(int logn, int rows, uint32_t* data, const uint32_t* tw, const CtxConst& cc,
+                           cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  const int N = 1 << logn;
+  const size_t smem = (size_t)(N + N / 32) * 4;
+  FL_DISPATCH(logn, (k_ntt_inv<LG><<<rows, N / 32, smem, st>>>(data, tw, cc)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv_intt(int logn, int B, const ConvDims& cd, const uint32_t* w_hat,
+                             const uint32_t* c_hat, uint32_t* out, const uint32_t* r,
+                             const uint32_t* tw, const CtxConst& cc, cudaStream_t st) {
+  const int N = 1 << logn;
+  const size_t smem = (size_t)2 * (N + N / 32) * 4;
+  dim3 grid(B * cd.bands, cd.Cout, cc.L);
+  if (r) {
+    FL_DISPATCH(logn, (k_conv_intt<LG, true><<<grid, N / 32, smem, st>>>(w_hat, c_hat, out, r, cd, tw, cc)));
+  } else {
+    FL_DISPATCH(logn, (k_conv_intt<LG, false><<<grid, N / 32, smem, st>>>(w_hat, c_hat, out, r, cd, tw, cc)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pmul_intt(int logn, int mode, int n, uint32_t* ws, uint32_t* ct, const uint32_t* sk,
+                             const int32_t* x, const int32_t* e, const GeomDims& gd,
+                             const uint32_t* tw, const CtxConst& cc, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int N = 1 << logn;
+  const size_t smem = (size_t)(N + N / 32) * 4;
+  dim3 grid(n, cc.L);
+  if (mode == MODE_DEC) {
+    FL_DISPATCH(logn, (k_pmul_intt<LG, MODE_DEC><<<grid, N / 32, smem, st>>>(ws, ct, sk, x, e, gd, tw, cc)));
+  } else {
+    FL_DISPATCH(logn, (k_pmul_intt<LG, MODE_ENC><<<grid, N / 32, smem, st>>>(ws, ct, sk, x, e, gd, tw, cc)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dec_round(const uint32_t* ws, uint32_t* m, int n, int N, const DecConst& dc,
+                             cudaStream_t st) {
+  const size_t total = (size_t)n * N;
+  if (total == 0) return cudaSuccess;
+  k_dec_round<<<blocks_for(total, 256), 256, 0, st>>>(ws, m, n, N, dc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extract(const uint32_t* m, int32_t* y, const GeomDims& g, int B, int N,
+                           cudaStream_t st) {
+  const size_t total = (size_t)B * g.Cout * g.Ho * g.Wo;
+  if (total == 0) return cudaSuccess;
+  k_extract<<<blocks_for(total, 256), 256, 0, st>>>(m, y, g, B, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask(uint32_t* ct, const uint32_t* r, int n, int N, const CtxConst& cc,
+                        cudaStream_t st) {
+  const size_t total = (size_t)n * cc.L * N / 4;
+  if (total == 0) return cudaSuccess;
+  k_mask<<<blocks_for(total, 256), 256, 0, st>>>(ct, r, n, N, cc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_enc_online(const uint32_t* enc0, uint32_t* ct, const int32_t* x, const GeomDims& gd,
+                              int n, int N, const CtxConst& cc, cudaStream_t st) {
+  const size_t total = (size_t)n * 2 * cc.L * N;
+  if (total == 0) return cudaSuccess;
+  k_enc_online<<<blocks_for(total, 256), 256, 0, st>>>(enc0, ct, x, gd, n, N, cc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_w_scatter(const int8_t* w, uint32_t* w_hat, const GeomDims& g, int N,
+                             const CtxConst& cc, cudaStream_t st) {
+  const size_t total = (size_t)g.Cout * g.Cin * g.k * g.k * cc.L;
+  if (total == 0) return cudaSuccess;
+  k_w_scatter<<<blocks_for(total, 256), 256, 0, st>>>(w, w_hat, g, N, cc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sk_expand(const int8_t* s, uint32_t* out, int N, const CtxConst& cc,
+                             cudaStream_t st) {
+  k_sk_expand<<<blocks_for((size_t)cc.L * N, 256), 256, 0, st>>>(s, out, N, cc);
+  return cudaGetLastError();
+}
+
+}  // namespace fl

@@ -1,0 +1,54 @@
+// Host-side launchers of the kernels in fl_kernels.cu (internal interface
+// between the C-ABI layer and the kernels; not part of the public header).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fl_device.cuh"
+
+namespace fl {
+
+struct ConvDims {  // per-launch shape of the fused contraction + INTT
+  int Cout, G, n_in, n_out, bands;
+};
+
+struct GeomDims {  // geometry fields the packing / extraction kernels read
+  int Cin, Cout, H, W, k, s, pad, Hp, Wp, Ho, Wo, Rin, Rout, bands, P, c_n, G, n_in, n_out;
+};
+
+struct DecConst {  // exact RNS scale-and-round constants
+  uint32_t q[FL_MAX_L];
+  uint32_t inv[FL_MAX_L];  // (q / q_l)^-1 mod q_l
+  uint64_t Qhi[FL_MAX_L], Qlo[FL_MAX_L];  // q / q_l as 128-bit
+  uint64_t qhi, qlo;  // q as 128-bit
+  uint32_t t;
+  int L;
+};
+
+cudaError_t launch_setup(int logn);
+cudaError_t launch_ntt_fwd(int logn, int rows, const uint32_t* src, int src_per, int src_stride,
+                           uint32_t* dst, int dst_per, int dst_stride, int limb_div,
+                           const uint32_t* tw, const CtxConst& cc, cudaStream_t st);
+cudaError_t launch_ntt_inv(int logn, int rows, uint32_t* data, const uint32_t* tw, const CtxConst& cc,
+                           cudaStream_t st);
+cudaError_t launch_conv_intt(int logn, int B, const ConvDims& cd, const uint32_t* w_hat,
+                             const uint32_t* c_hat, uint32_t* out, const uint32_t* r,
+                             const uint32_t* tw, const CtxConst& cc, cudaStream_t st);
+cudaError_t launch_pmul_intt(int logn, int mode, int n, uint32_t* ws, uint32_t* ct, const uint32_t* sk,
+                             const int32_t* x, const int32_t* e, const GeomDims& gd,
+                             const uint32_t* tw, const CtxConst& cc, cudaStream_t st);
+cudaError_t launch_dec_round(const uint32_t* ws, uint32_t* m, int n, int N, const DecConst& dc,
+                             cudaStream_t st);
+cudaError_t launch_extract(const uint32_t* m, int32_t* y, const GeomDims& g, int B, int N,
+                           cudaStream_t st);
+cudaError_t launch_mask(uint32_t* ct, const uint32_t* r, int n, int N, const CtxConst& cc,
+                        cudaStream_t st);
+cudaError_t launch_enc_online(const uint32_t* enc0, uint32_t* ct, const int32_t* x, const GeomDims& gd,
+                              int n, int N, const CtxConst& cc, cudaStream_t st);
+cudaError_t launch_w_scatter(const int8_t* w, uint32_t* w_hat, const GeomDims& g, int N,
+                             const CtxConst& cc, cudaStream_t st);
+cudaError_t launch_sk_expand(const int8_t* s, uint32_t* out, int N, const CtxConst& cc,
+                             cudaStream_t st);
+
+}  // namespace fl

@@ -1,0 +1,228 @@
+"""Thin Python binding of the flashgpu C-ABI (include/flashgpu.h).
+
+Argument marshalling only: every step of the HE convolution runs in the CUDA
+kernels of libflashgpu.so.  Device buffers are torch tensors (ciphertexts as
+int32 tensors holding residues below 2^30, i.e. the same bits as uint32);
+streams are torch CUDA streams.  There is no CPU path: if the shared library
+is missing the import of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libflashgpu.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "flashgpu.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2401_16732_gb300.build` "
+                      "(there is no CPU fallback)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+FL_OK, FL_ERR_ARG, FL_ERR_SHAPE, FL_ERR_CUDA, FL_ERR_OOM = 0, -1, -2, -3, -4
+
+
+class ConvGeom(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "N", "Cin", "Cout", "H", "W", "k", "stride", "pad", "Hp", "Wp", "Ho", "Wo",
+        "Rin", "Rout", "bands", "P", "c_n", "G", "n_in", "n_out")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_vp, _i, _u32, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_size_t
+_gp = ctypes.POINTER(ConvGeom)
+_SIGS = {
+    "fl_last_error": ([], ctypes.c_char_p),
+    "fl_conv_geom_make": ([_i] * 8 + [_gp], _i),
+    "fl_ctx_create": ([_i, _i, _u32, ctypes.POINTER(_vp)], _i),
+    "fl_ctx_destroy": ([_vp], None),
+    "fl_ctx_params": ([_vp, _vp, _vp, _vp], _i),
+    "fl_keygen": ([_vp, _vp, _vp, _vp], _i),
+    "fl_encrypt": ([_vp, _vp, _gp, _i, _vp, _vp, _vp, _vp, _vp], _i),
+    "fl_encrypt_online": ([_vp, _gp, _i, _vp, _vp, _vp, _vp], _i),
+    "fl_decrypt_workspace_bytes": ([_vp, _i], _sz),
+    "fl_decrypt": ([_vp, _vp, _i, _vp, _vp, _vp, _sz, _vp], _i),
+    "fl_extract_outputs": ([_gp, _i, _vp, _vp, _vp], _i),
+    "fl_weights_bytes": ([_vp, _gp], _sz),
+    "fl_encode_weights": ([_vp, _gp, _vp, _vp, _vp], _i),
+    "fl_he_conv2d_workspace_bytes": ([_vp, _gp, _i], _sz),
+    "fl_he_conv2d": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "fl_mask_to_share": ([_vp, _i, _vp, _vp, _vp], _i),
+    "fl_he_conv2d_mask": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "fl_he_conv2d_ntt_inputs": ([_vp, _gp, _i, _vp, _vp, _sz, _vp], _i),
+    "fl_he_conv2d_from_ntt": ([_vp, _gp, _i, _vp, _vp, _sz, _vp, _vp, _vp], _i),
+    "fl_ntt_forward": ([_vp, _i, _vp, _vp], _i),
+    "fl_ntt_inverse": ([_vp, _i, _vp, _vp], _i),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes, _f.restype = _args, _res
+
+
+def header_symbols() -> list[str]:
+    """Every entry point include/flashgpu.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(fl_[a-z0-9_]+)\s*\(", text)))
+
+
+class FlashError(RuntimeError):
+    pass
+
+
+def _check(rc: int):
+    if rc != FL_OK:
+        raise FlashError(f"flashgpu error {rc}: {_lib.fl_last_error().decode()}")
+
+
+def fl_last_error() -> str:
+    return _lib.fl_last_error().decode()
+
+
+def fl_conv_geom_make(N, Cin, Cout, H, W, k, stride=1, pad=0) -> ConvGeom:
+    g = ConvGeom()
+    _check(_lib.fl_conv_geom_make(N, Cin, Cout, H, W, k, stride, pad, ctypes.byref(g)))
+    return g
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_u32(t: torch.Tensor, shape, name):
+    if t.dtype not in (torch.int32, torch.uint32) or not t.is_cuda or not t.is_contiguous():
+        raise FlashError(f"{name}: expected a contiguous 32-bit CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise FlashError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
+    return t
+
+
+class Context:
+    """fl_ctx on the current CUDA device (ring degree N, L limbs, plaintext t)."""
+
+    def __init__(self, N: int, L: int, t: int = 65537):
+        h = ctypes.c_void_p()
+        _check(_lib.fl_ctx_create(N, L, t, ctypes.byref(h)))
+        self.h, self.N, self.L, self.t = h, N, L, t
+        q = (ctypes.c_uint32 * L)()
+        d = (ctypes.c_uint32 * L)()
+        p = (ctypes.c_uint32 * L)()
+        _check(_lib.fl_ctx_params(h, q, d, p))
+        self.primes, self.delta, self.psi = list(q), list(d), list(p)
+        self.device = torch.cuda.current_device()
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.fl_ctx_destroy(self.h)
+            self.h = None
+
+    def geom(self, Cin, Cout, H, W, k, stride=1, pad=0) -> ConvGeom:
+        return fl_conv_geom_make(self.N, Cin, Cout, H, W, k, stride, pad)
+
+    def _new(self, *shape):
+        return torch.empty(shape, dtype=torch.int32, device=f"cuda:{self.device}")
+
+    # -- client side -----------------------------------------------------
+    def keygen(self, s: torch.Tensor, stream=None) -> torch.Tensor:
+        sk = self._new(self.L, self.N)
+        _check(_lib.fl_keygen(self.h, _ptr(s), _ptr(sk), _stream(stream)))
+        return sk
+
+    def encrypt(self, sk, g: ConvGeom, x, a, e, out=None, stream=None) -> torch.Tensor:
+        B = x.shape[0]
+        _dev_u32(a, (B, g.n_in, self.L, self.N), "a")
+        out = self._new(B, g.n_in, 2, self.L, self.N) if out is None else out
+        _check(_lib.fl_encrypt(self.h, _ptr(sk), ctypes.byref(g), B, _ptr(x), _ptr(a), _ptr(e), _ptr(out),
+                               _stream(stream)))
+        return out
+
+    def encrypt_online(self, g: ConvGeom, x, enc0, out=None, stream=None) -> torch.Tensor:
+        B = x.shape[0]
+        _dev_u32(enc0, (B, g.n_in, 2, self.L, self.N), "enc0")
+        out = torch.empty_like(enc0) if out is None else out
+        _check(_lib.fl_encrypt_online(self.h, ctypes.byref(g), B, _ptr(x), _ptr(enc0), _ptr(out), _stream(stream)))
+        return out
+
+    def decrypt(self, sk, ct, stream=None) -> torch.Tensor:
+        """ct [..., 2, L, N] -> m [..., N] (values in [0, t))."""
+        lead = ct.shape[:-3]
+        n = int(torch.tensor(lead).prod()) if len(lead) else 1
+        ws = torch.empty(_lib.fl_decrypt_workspace_bytes(self.h, n) // 4 + 4, dtype=torch.int32, device=ct.device)
+        m = self._new(*lead, self.N)
+        _check(_lib.fl_decrypt(self.h, _ptr(sk), n, _ptr(ct), _ptr(m), _ptr(ws), ws.numel() * 4, _stream(stream)))
+        return m
+
+    def extract_outputs(self, g: ConvGeom, m, stream=None) -> torch.Tensor:
+        B = m.shape[0]
+        y = self._new(B, g.Cout, g.Ho, g.Wo)
+        _check(_lib.fl_extract_outputs(ctypes.byref(g), B, _ptr(m), _ptr(y), _stream(stream)))
+        return y
+
+    # -- server side -----------------------------------------------------
+    def weights_bytes(self, g: ConvGeom) -> int:
+        return _lib.fl_weights_bytes(self.h, ctypes.byref(g))
+
+    def encode_weights(self, g: ConvGeom, w, out=None, stream=None) -> torch.Tensor:
+        out = self._new(self.L, g.Cout, g.G, self.N) if out is None else out
+        _check(_lib.fl_encode_weights(self.h, ctypes.byref(g), _ptr(w), _ptr(out), _stream(stream)))
+        return out
+
+    def workspace_bytes(self, g: ConvGeom, B: int) -> int:
+        return _lib.fl_he_conv2d_workspace_bytes(self.h, ctypes.byref(g), B)
+
+    def workspace(self, g: ConvGeom, B: int) -> torch.Tensor:
+        return torch.empty(max(self.workspace_bytes(g, B), 16) // 4, dtype=torch.int32,
+                           device=f"cuda:{self.device}")
+
+    def he_conv2d(self, g, w_hat, ct_in, out=None, workspace=None, r=None, stream=None) -> torch.Tensor:
+        """Homomorphic convolution of ct_in [B][n_in][2][L][N]; with r
+        ([B][n_out][N]) the mask addition is fused (fl_he_conv2d_mask)."""
+        B = ct_in.shape[0]
+        _dev_u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
+        out = self._new(B, g.n_out, 2, self.L, self.N) if out is None else out
+        ws = self.workspace(g, B) if workspace is None else workspace
+        if r is None:
+            _check(_lib.fl_he_conv2d(self.h, ctypes.byref(g), B, _ptr(w_hat), _ptr(ct_in), _ptr(out), _ptr(ws),
+                                     ws.numel() * ws.element_size(), _stream(stream)))
+        else:
+            _dev_u32(r, (B, g.n_out, self.N), "r")
+            _check(_lib.fl_he_conv2d_mask(self.h, ctypes.byref(g), B, _ptr(w_hat), _ptr(ct_in), _ptr(r), _ptr(out),
+                                          _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+        return out
+
+    def he_conv2d_ntt_inputs(self, g, ct_in, workspace, stream=None):
+        """Stage a3 of he_conv2d: forward NTT of ct_in into the workspace."""
+        _check(_lib.fl_he_conv2d_ntt_inputs(self.h, ctypes.byref(g), ct_in.shape[0], _ptr(ct_in), _ptr(workspace),
+                                            workspace.numel() * workspace.element_size(), _stream(stream)))
+
+    def he_conv2d_from_ntt(self, g, B, w_hat, workspace, out, r=None, stream=None):
+        """Stages a4-a6 of he_conv2d from a workspace filled by he_conv2d_ntt_inputs."""
+        _check(_lib.fl_he_conv2d_from_ntt(self.h, ctypes.byref(g), B, _ptr(w_hat), _ptr(workspace),
+                                          workspace.numel() * workspace.element_size(), _ptr(r), _ptr(out),
+                                          _stream(stream)))
+        return out
+
+    def mask_to_share(self, ct, r, stream=None) -> torch.Tensor:
+        """In place: c0 += Delta*r for ct [..., 2, L, N], r [..., N]."""
+        n = ct.numel() // (2 * self.L * self.N)
+        _check(_lib.fl_mask_to_share(self.h, n, _ptr(ct), _ptr(r), _stream(stream)))
+        return ct
+
+    def ntt_forward(self, data, stream=None):
+        _check(_lib.fl_ntt_forward(self.h, data.numel() // (self.L * self.N), _ptr(data), _stream(stream)))
+        return data
+
+    def ntt_inverse(self, data, stream=None):
+        _check(_lib.fl_ntt_inverse(self.h, data.numel() // (self.L * self.N), _ptr(data), _stream(stream)))
+        return data
