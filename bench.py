@@ -207,7 +207,6 @@ def run_gpu(args, wl, rank, world, local_rank):
     s = synth.secret_key(seed, N)
     sk = ctx.keygen(to_dev(s, torch.int8))
     layers = []
-    ws_words = 4
     for li, shape in enumerate(wl.layers):
         g = ctx.geom(*shape)
         w = synth.weights(seed, (g.Cout, g.Cin, g.k, g.k), li)
@@ -219,20 +218,25 @@ def run_gpu(args, wl, rank, world, local_rank):
                "ct": ctx.encrypt(sk, g, to_dev(x), to_dev(a), to_dev(e)), "r": to_dev(r),
                "out": torch.empty((B, g.n_out, 2, L, N), dtype=torch.int32, device=dev)}
         layers.append(lay)
-        ws_words = max(ws_words, ctx.workspace_bytes(g, B) // 4)
-    ws = torch.empty(ws_words, dtype=torch.int32, device=dev)
+    arr = ctx.stack_layers([{"g": lay["g"], "w_hat": lay["w_hat"], "ct_in": lay["ct"], "r": lay["r"],
+                             "out": lay["out"]} for lay in layers])
+    ws = ctx.stack_workspace(arr)
     torch.cuda.synchronize()
+    from paper_2401_16732_gb300.autotune import tune_stack
+    tuned = tune_stack(ctx, [{"g": lay["g"], "ct_in": lay["ct"], "r": lay["r"]} for lay in layers], arr, ws,
+                       stream=stream, cache=None)
 
     def step(events=None):
-        for i, lay in enumerate(layers):
-            if events is not None:
-                events[i][0].record(stream)
-            ctx.he_conv2d_ntt_inputs(lay["g"], lay["ct"], ws, stream=stream)
-            if events is not None:
-                events[i][1].record(stream)
-            ctx.he_conv2d_from_ntt(lay["g"], B, lay["w_hat"], ws, lay["out"], r=lay["r"], stream=stream)
-            if events is not None:
-                events[i][2].record(stream)
+        # forward NTT of every layer's inputs (one launch), then the
+        # persistent contraction + inverse NTT + mask kernel over all layers
+        if events is not None:
+            events[0].record(stream)
+        ctx.he_conv2d_stack(arr, ws, stream=stream, stage="ntt")
+        if events is not None:
+            events[1].record(stream)
+        ctx.he_conv2d_stack(arr, ws, stream=stream, stage="run")
+        if events is not None:
+            events[2].record(stream)
 
     # capture one step in a CUDA graph (40 launches for ResNet-18)
     with torch.cuda.stream(stream):
@@ -241,16 +245,21 @@ def run_gpu(args, wl, rank, world, local_rank):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         step()
-    launches_per_step = 2 * len(layers)
+    launches_per_step = 2 if tuned["kernel"] == "persistent" else 1 + len(layers)
 
     def barrier():
         if world > 1:
             dist.barrier()
 
+    def replay():
+        # CUDAGraph.replay() launches on the current stream
+        with torch.cuda.stream(stream):
+            graph.replay()
+
     clocks = ClockSampler(local_rank)
     clocks.start()
     for _ in range(args.warmup):
-        graph.replay()
+        replay()
     stream.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -258,7 +267,7 @@ def run_gpu(args, wl, rank, world, local_rank):
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for _ in range(args.steps):
-        graph.replay()
+        replay()
     t_end.record(stream)
     t_end.synchronize()
     torch.cuda.synchronize()
@@ -274,16 +283,16 @@ def run_gpu(args, wl, rank, world, local_rank):
     kern = {"ntt": 0.0, "conv": 0.0}
     nrep = max(1, min(args.steps, 5))
     for _ in range(nrep):
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in layers]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         with torch.cuda.stream(stream):
-            torch.cuda._sleep(20_000_000)
+            torch.cuda._sleep(2_000_000)
         step(evs)
         stream.synchronize()
-        for e in evs:
-            kern["ntt"] += e[0].elapsed_time(e[1])
-            kern["conv"] += e[1].elapsed_time(e[2])
-    for k in kern:
-        kern[k] /= nrep
+        kern["ntt"] += evs[0].elapsed_time(evs[1]) / nrep
+        kern["conv"] += evs[1].elapsed_time(evs[2]) / nrep
+    err_word = ctx.stack_error(ws, stream=stream)
+    if err_word:
+        raise RuntimeError(f"persistent kernel reported a timed-out wait (error word {err_word})")
 
     # ---- end to end: pinned host inputs -> device -> path -> host outputs ----
     e2e = None
@@ -298,7 +307,7 @@ def run_gpu(args, wl, rank, world, local_rank):
             with torch.cuda.stream(stream):
                 for lay, h in zip(layers, h_in):
                     lay["ct"].copy_(h, non_blocking=True)
-            graph.replay()
+            replay()
             with torch.cuda.stream(stream):
                 for lay, h in zip(layers, h_out):
                     h.copy_(lay["out"], non_blocking=True)
@@ -333,10 +342,13 @@ def run_gpu(args, wl, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": wl.name, "layers": len(layers), "batch": B, "N": N, "L": L, "t": T_PLAIN,
                    "l2": f"no flush: {step_bytes / 1e9:.2f} GB of algorithmic traffic per step > {L2_BYTES / 1e6:.0f} MB L2",
-                   "graph": "one CUDA graph per step"},
+                   "graph": "one CUDA graph per step: input NTT of all layers + the contraction/INTT/mask kernel(s)",
+                   "stack_kernel": tuned["kernel"], "autotune_ms": tuned["ms"]},
         "slot_mac_per_s": world * macs * args.steps / (ms * 1e-3),
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"kernel": "k_conv_intt (contraction + inverse NTT + mask)", "bound": "hbm",
+        "roofline": {"kernel": ("k_stack (persistent, all layers)" if tuned["kernel"] == "persistent" else
+                                "k_conv_intt (one launch per layer)") + ": contraction + inverse NTT + mask",
+                     "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": peak_kind, "traffic": None,
                      "kernel_ms_per_step": kern["conv"], "algorithmic_bytes_per_step": conv_bytes,

@@ -176,6 +176,62 @@ int fl_he_conv2d_from_ntt(fl_ctx *ctx, const fl_conv_geom *geom, int B, const ui
                           const void *workspace_dev, size_t workspace_bytes, const uint32_t *r_dev,
                           uint32_t *ct_out_dev, void *stream);
 
+/* ---- Many layers in one launch ---- */
+
+/* One layer of a stack: its geometry (host pointer), batch size, encoded
+ * weights, input ciphertexts [B][n_in][2][L][N], masks [B][n_out][N] (NULL:
+ * no mask) and output ciphertexts [B][n_out][2][L][N]. */
+typedef struct fl_stack_layer {
+  const fl_conv_geom *geom;
+  int32_t B;
+  const uint32_t *w_hat_dev;
+  const uint32_t *ct_in_dev;
+  const uint32_t *r_dev;
+  uint32_t *ct_out_dev;
+} fl_stack_layer;
+
+#define FL_STACK_MAX_LAYERS 64
+
+/* Workspace of fl_he_conv2d_stack: 256 control bytes plus the NTT images of
+ * every layer's inputs. */
+size_t fl_stack_workspace_bytes(const fl_ctx *ctx, const fl_stack_layer *layers, int n_layers);
+
+/* fl_he_conv2d (or fl_he_conv2d_mask where r_dev is set) of up to 64
+ * independent layers in three launches: one forward NTT over every layer's
+ * inputs (a3), then one persistent kernel (a4-a6) whose CTAs pull
+ * (layer, image, output channel, limb) items from a shared queue.  Each
+ * output equals the single-layer call's bit for bit.  The persistent kernel
+ * bounds every internal wait (2 s); if one runs out it stops and records
+ * the failure in the workspace's error word (fl_stack_error). */
+int fl_he_conv2d_stack(fl_ctx *ctx, const fl_stack_layer *layers, int n_layers, void *workspace_dev,
+                       size_t workspace_bytes, void *stream);
+
+/* The two stages of fl_he_conv2d_stack as separate calls (same arguments,
+ * same results): the forward NTT of every layer's inputs into the workspace
+ * (a3), then the persistent contraction + inverse NTT + mask kernel (a4-a6). */
+int fl_he_conv2d_stack_ntt(fl_ctx *ctx, const fl_stack_layer *layers, int n_layers, void *workspace_dev,
+                           size_t workspace_bytes, void *stream);
+int fl_he_conv2d_stack_run(fl_ctx *ctx, const fl_stack_layer *layers, int n_layers, void *workspace_dev,
+                           size_t workspace_bytes, void *stream);
+
+/* Kernel used by the second stage of a stack:
+ * FL_STACK_PER_LAYER: one fused contraction + inverse NTT + mask launch per
+ *   layer (two CTAs of 2*N/32 threads per SM, both components side by side);
+ * FL_STACK_PERSISTENT: one persistent warp-specialised launch over all
+ *   layers (a cp.async-fed contraction team and an inverse-NTT team per SM
+ *   handing items over through shared-memory mbarriers).
+ * Both give identical outputs; which is faster depends on the stack's shapes
+ * (the Python package's autotuner times both and picks).  Default:
+ * FL_STACK_PER_LAYER. */
+#define FL_STACK_PER_LAYER 0
+#define FL_STACK_PERSISTENT 1
+int fl_ctx_set_stack_kernel(fl_ctx *ctx, int kernel);
+int fl_ctx_get_stack_kernel(const fl_ctx *ctx);
+
+/* Synchronise `stream` and read the error word of a workspace last used by
+ * fl_he_conv2d_stack (0: no internal wait ran out). */
+int fl_stack_error(const void *workspace_dev, void *stream, uint64_t *error_host);
+
 /* ---- Building blocks, exposed for tests ---- */
 
 /* In-place negacyclic NTT / inverse NTT of n RNS polynomials data_dev

@@ -1,0 +1,75 @@
+"""Pick the faster stack kernel for a workload by timing both on the device.
+
+The choice depends only on the stack's shapes (ring degree, limbs, layer
+geometries, batch sizes), so it is cached in a JSON file keyed by them.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import torch
+
+from . import flashgpu
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "flashgpu_autotune.json")
+
+
+def _key(ctx, specs) -> str:
+    shapes = [(sp["g"].Cin, sp["g"].Cout, sp["g"].H, sp["g"].W, sp["g"].k, sp["g"].stride, sp["g"].pad,
+               int(sp["ct_in"].shape[0]), sp.get("r") is not None) for sp in specs]
+    dev = torch.cuda.get_device_name(ctx.device)
+    raw = json.dumps([dev, ctx.N, ctx.L, shapes])
+    return hashlib.sha256(raw.encode()).hexdigest()[:24]
+
+
+def _time(ctx, arr, ws, stream, reps):
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.he_conv2d_stack(arr, ws, stream=stream, stage="run")
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return best
+
+
+def tune_stack(ctx: flashgpu.Context, specs, arr, ws, stream=None, reps: int = 3, cache: str | None = DEFAULT_CACHE):
+    """Time both stack kernels on the stack `arr` (inputs already in place),
+    set the faster one on `ctx` and return {"kernel": name, "ms": {...}}."""
+    stream = stream or torch.cuda.current_stream()
+    key = _key(ctx, specs)
+    table = {}
+    if cache and os.path.exists(cache):
+        try:
+            with open(cache) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+    if key in table:
+        ctx.stack_kernel = table[key]["kernel_id"]
+        return {"kernel": table[key]["kernel"], "ms": table[key]["ms"], "cached": True}
+    ctx.he_conv2d_stack(arr, ws, stream=stream, stage="ntt")
+    ms = {}
+    for kid, name in ((flashgpu.FL_STACK_PER_LAYER, "per_layer"), (flashgpu.FL_STACK_PERSISTENT, "persistent")):
+        ctx.stack_kernel = kid
+        ms[name] = _time(ctx, arr, ws, stream, reps)
+        if ctx.stack_error(ws, stream=stream):
+            ms[name] = float("inf")
+    best = min(ms, key=ms.get)
+    kid = flashgpu.FL_STACK_PER_LAYER if best == "per_layer" else flashgpu.FL_STACK_PERSISTENT
+    ctx.stack_kernel = kid
+    table[key] = {"kernel": best, "kernel_id": kid, "ms": ms}
+    if cache:
+        try:
+            os.makedirs(os.path.dirname(cache), exist_ok=True)
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1)
+        except OSError:
+            pass
+    return {"kernel": best, "ms": ms, "cached": False}

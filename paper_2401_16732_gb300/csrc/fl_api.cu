@@ -21,12 +21,13 @@ using fl::GeomDims;
 typedef unsigned __int128 u128;
 
 struct fl_ctx {
-  int N, logN, L, device;
+  int N, logN, L, device, sms;
+  int stack_kernel;  // FL_STACK_PER_LAYER or FL_STACK_PERSISTENT
   uint32_t t;
   uint32_t psi[FL_MAX_L];
   CtxConst cc;
   DecConst dc;
-  uint32_t* tw;  // device [L][4][N]
+  uint32_t* tw;  // device twiddle tables, twiddle_limb_words(logN) words per limb
 };
 
 namespace {
@@ -184,6 +185,7 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
   if (t < 3 || t >= (1u << 20) || !(t & 1)) return fail(FL_ERR_ARG, "t=%u must be odd in [3, 2^20)", t);
   fl_ctx* c = new fl_ctx();
   c->N = N; c->logN = logN; c->L = L; c->t = t;
+  c->stack_kernel = FL_STACK_PER_LAYER;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDevice"); }
 
@@ -197,7 +199,8 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
   u128 Q = 1;
   for (uint32_t q : qs) Q *= q;
   const u128 Delta = Q / t;
-  std::vector<uint32_t> host((size_t)L * 4 * N);
+  const size_t limb_words = fl::twiddle_limb_words(logN);
+  std::vector<uint32_t> host((size_t)L * limb_words);
   memset(&c->cc, 0, sizeof c->cc);
   memset(&c->dc, 0, sizeof c->dc);
   c->cc.L = L; c->cc.t = t;
@@ -213,21 +216,41 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
     }
     const uint32_t psi_inv = (uint32_t)powmod(psi, q - 2, q);
     c->psi[l] = psi;
-    uint32_t* T = host.data() + (size_t)l * 4 * N;
+    uint32_t* Tw = host.data() + (size_t)l * limb_words;
+    uint2* pairs = reinterpret_cast<uint2*>(Tw);
+    std::vector<uint32_t> fw(N), iv(N);
     for (int i = 0; i < N; ++i) {
-      const uint32_t f = (uint32_t)powmod(psi, brev(i, logN), q);
-      const uint32_t v = (uint32_t)powmod(psi_inv, brev(i, logN), q);
-      T[fl::TW_FWD * N + i] = f;
-      T[fl::TW_FWD_SH * N + i] = shoup(f, q);
-      T[fl::TW_INV * N + i] = v;
-      T[fl::TW_INV_SH * N + i] = shoup(v, q);
+      fw[i] = (uint32_t)powmod(psi, brev(i, logN), q);
+      iv[i] = (uint32_t)powmod(psi_inv, brev(i, logN), q);
+      pairs[fl::TW_FWD * N + i] = make_uint2(fw[i], shoup(fw[i], q));
+      pairs[fl::TW_INV * N + i] = make_uint2(iv[i], shoup(iv[i], q));
+    }
+    // thread-major twiddles of the radix-32 pass over stages [logN-5, logN):
+    // thread blk consumes, for stage S0+d (ascending forward, descending
+    // inverse), twiddles (1 << (S0+d)) + blk*2^d + m for m < 2^d.
+    const int Tn = N / 32, S0 = logN - 5;
+    uint32_t* grouped = Tw + 4 * N;
+    for (int dir = 0; dir < 2; ++dir) {
+      const std::vector<uint32_t>& tab = dir == fl::TW_FWD ? fw : iv;
+      for (int blk = 0; blk < Tn; ++blk) {
+        int slot = 0;
+        for (int dd = 0; dd < 5; ++dd) {
+          const int d = dir == fl::TW_INV ? 4 - dd : dd;
+          for (int m = 0; m < (1 << d); ++m, ++slot) {
+            const uint32_t w = tab[(1 << (S0 + d)) + (blk << d) + m];
+            uint32_t* e = grouped + (((size_t)dir * 16 + slot / 2) * Tn + blk) * 4 + (slot & 1) * 2;
+            e[0] = w;
+            e[1] = shoup(w, q);
+          }
+        }
+      }
     }
     fl::LimbConst& lc = c->cc.limb[l];
     lc.q = q;
     lc.two_q = 2 * q;
     lc.n_inv = (uint32_t)powmod(N, q - 2, q);
     lc.n_inv_sh = shoup(lc.n_inv, q);
-    lc.last_w = (uint32_t)mulmod(T[fl::TW_INV * N + 1], lc.n_inv, q);
+    lc.last_w = (uint32_t)mulmod(iv[1], lc.n_inv, q);
     lc.last_w_sh = shoup(lc.last_w, q);
     lc.delta = (uint32_t)(Delta % q);
     lc.delta_sh = shoup(lc.delta, q);
@@ -238,12 +261,20 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
     c->dc.Qhi[l] = (uint64_t)(Ql >> 64);
     c->dc.Qlo[l] = (uint64_t)Ql;
   }
-  if ((e = fl::launch_setup(logN)) != cudaSuccess) { delete c; return cuda_fail(e, "kernel set-up"); }
-  if ((e = cudaMalloc(&c->tw, host.size() * 4)) != cudaSuccess) {
+  if ((e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "SM count");
+  }
+  if ((e = fl::launch_setup(logN)) != cudaSuccess || (e = fl::launch_stack_setup(logN)) != cudaSuccess ||
+      (e = fl::launch_ntt_multi_setup(logN)) != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "kernel set-up");
+  }
+  if ((e = cudaMalloc(&c->tw, host.size() * sizeof(uint32_t))) != cudaSuccess) {
     delete c;
     return fail(FL_ERR_OOM, "twiddle tables: %s", cudaGetErrorString(e));
   }
-  if ((e = cudaMemcpy(c->tw, host.data(), host.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+  if ((e = cudaMemcpy(c->tw, host.data(), host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
     cudaFree(c->tw);
     delete c;
     return cuda_fail(e, "twiddle upload");
@@ -464,6 +495,127 @@ int fl_mask_to_share(fl_ctx* ctx, int n, uint32_t* ct_dev, const uint32_t* r_dev
   if (n == 0) return FL_OK;
   if ((rc = check_ptrs({ct_dev, r_dev}))) return rc;
   return launched(fl::launch_mask(ct_dev, r_dev, n, ctx->N, ctx->cc, (cudaStream_t)stream), "mask");
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+static const size_t kStackCtlBytes = 256;
+
+size_t fl_stack_workspace_bytes(const fl_ctx* ctx, const fl_stack_layer* layers, int n_layers) {
+  if (!ctx || !layers || n_layers < 0) return 0;
+  size_t total = kStackCtlBytes;
+  for (int i = 0; i < n_layers; ++i) {
+    if (!layers[i].geom || layers[i].B < 0) return 0;
+    total += align256((size_t)layers[i].B * layers[i].geom->n_in * 2 * ctx->L * ctx->N * 4);
+  }
+  return total;
+}
+
+// stages: 1 = input NTT, 2 = persistent kernel, 3 = both
+static int stack_impl(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, void* workspace_dev,
+                      size_t workspace_bytes, void* stream, int stages) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (n_layers < 0 || n_layers > FL_STACK_MAX_LAYERS)
+    return fail(FL_ERR_ARG, "n_layers=%d outside [0, %d]", n_layers, FL_STACK_MAX_LAYERS);
+  if (n_layers > 0 && !layers) return fail(FL_ERR_ARG, "null layers");
+  if ((rc = check_ptrs({workspace_dev}))) return rc;
+  const size_t need = fl_stack_workspace_bytes(ctx, layers, n_layers);
+  if (need == 0 || workspace_bytes < need)
+    return fail(FL_ERR_ARG, "workspace %zu bytes, need %zu", workspace_bytes, need);
+  fl::StackArgs a;
+  memset(&a, 0, sizeof a);
+  fl::NttSegs segs;
+  memset(&segs, 0, sizeof segs);
+  char* ws = (char*)workspace_dev + kStackCtlBytes;
+  long long items = 0;
+  int rows = 0;
+  for (int i = 0; i < n_layers; ++i) {
+    const fl_stack_layer& y = layers[i];
+    if ((rc = check_geom(ctx, y.geom))) return fail(rc, "layer %d: %s", i, g_err.c_str());
+    if (y.B == 0) continue;
+    if ((rc = check_ptrs({y.w_hat_dev, y.ct_in_dev, y.ct_out_dev})))
+      return fail(rc, "layer %d: %s", i, g_err.c_str());
+    if (y.r_dev && (rc = check_ptrs({y.r_dev}))) return fail(rc, "layer %d: %s", i, g_err.c_str());
+    const fl_conv_geom& g = *y.geom;
+    const size_t cbytes = (size_t)y.B * g.n_in * 2 * ctx->L * ctx->N * 4;
+    const long long seg_rows = (long long)y.B * g.n_in * 2 * ctx->L;
+    if (rows + seg_rows > 0x7fffffffLL) return fail(FL_ERR_ARG, "too many input rows");
+    const int k = segs.n++;
+    segs.src[k] = y.ct_in_dev;
+    segs.dst[k] = (uint32_t*)ws;
+    segs.row_begin[k] = rows;
+    rows += (int)seg_rows;
+    fl::StackLayer& s = a.layer[a.n_layers++];
+    s.w_hat = y.w_hat_dev;
+    s.c_hat = (const uint32_t*)ws;
+    s.out = y.ct_out_dev;
+    s.r = y.r_dev;
+    s.Cout = g.Cout;
+    s.G = g.G;
+    s.n_in = g.n_in;
+    s.n_out = g.n_out;
+    s.bands = g.bands;
+    s.BB = y.B * g.bands;
+    s.item_begin = items;
+    items += (long long)s.BB * g.Cout * ctx->L;
+    ws += align256(cbytes);
+  }
+  segs.row_begin[segs.n] = rows;
+  a.n_items = items;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* ctl = (unsigned long long*)workspace_dev;
+  if ((stages & 1) && (rc = launched(fl::launch_ntt_multi(ctx->logN, segs, ctx->tw, ctx->cc, st), "stack input ntt")))
+    return rc;
+  if (!(stages & 2)) return FL_OK;
+  if (ctx->stack_kernel == FL_STACK_PERSISTENT)
+    return launched(fl::launch_stack(ctx->logN, a, ctl, ctx->tw, ctx->cc, ctx->sms, st), "stack");
+  // per-layer fused launches; the error word stays 0 (these kernels never wait)
+  cudaError_t e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(e, "control reset");
+  for (int k = 0; k < a.n_layers; ++k) {
+    const fl::StackLayer& y = a.layer[k];
+    fl::ConvDims cd{y.Cout, y.G, y.n_in, y.n_out, y.bands};
+    if ((rc = launched(fl::launch_conv_intt(ctx->logN, y.BB / y.bands, cd, y.w_hat, y.c_hat, y.out, y.r, ctx->tw,
+                                            ctx->cc, st),
+                       "stack layer")))
+      return rc;
+  }
+  return FL_OK;
+}
+
+int fl_ctx_set_stack_kernel(fl_ctx* ctx, int kernel) {
+  if (!ctx) return fail(FL_ERR_ARG, "null context");
+  if (kernel != FL_STACK_PER_LAYER && kernel != FL_STACK_PERSISTENT) return fail(FL_ERR_ARG, "kernel=%d", kernel);
+  ctx->stack_kernel = kernel;
+  return FL_OK;
+}
+
+int fl_ctx_get_stack_kernel(const fl_ctx* ctx) { return ctx ? ctx->stack_kernel : FL_ERR_ARG; }
+
+int fl_he_conv2d_stack(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, void* workspace_dev,
+                       size_t workspace_bytes, void* stream) {
+  return stack_impl(ctx, layers, n_layers, workspace_dev, workspace_bytes, stream, 3);
+}
+
+int fl_he_conv2d_stack_ntt(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, void* workspace_dev,
+                           size_t workspace_bytes, void* stream) {
+  return stack_impl(ctx, layers, n_layers, workspace_dev, workspace_bytes, stream, 1);
+}
+
+int fl_he_conv2d_stack_run(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, void* workspace_dev,
+                           size_t workspace_bytes, void* stream) {
+  return stack_impl(ctx, layers, n_layers, workspace_dev, workspace_bytes, stream, 2);
+}
+
+int fl_stack_error(const void* workspace_dev, void* stream, uint64_t* error_host) {
+  if (!workspace_dev || !error_host) return fail(FL_ERR_ARG, "null pointer");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream sync");
+  unsigned long long v = 0;
+  e = cudaMemcpy(&v, (const unsigned long long*)workspace_dev + 1, sizeof v, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "error word read");
+  *error_host = v;
+  return FL_OK;
 }
 
 int fl_ntt_forward(fl_ctx* ctx, int n, uint32_t* data_dev, void* stream) {

@@ -43,15 +43,29 @@ struct CtxConst {
   uint32_t t;
 };
 
-// Twiddle tables: [L][4][N] words: psi^brev, Shoup(psi^brev),
-// psi^-brev, Shoup(psi^-brev).
-enum { TW_FWD = 0, TW_FWD_SH = 1, TW_INV = 2, TW_INV_SH = 3 };
+// Twiddle tables, per limb (all in one device allocation):
+//  * uint2 [2][N]: (psi^brev(i), Shoup companion) for the forward transform,
+//    then (psi^-brev(i), companion) for the inverse; one 8-byte load fetches a
+//    twiddle with its companion.  Used by the passes whose twiddles are the
+//    same for a whole warp (broadcast loads).
+//  * uint4 [2][16][N/32]: the twiddles of the radix-32 pass on contiguous
+//    groups (forward last pass, inverse first pass), where every thread needs
+//    31 twiddles of its own.  Entry [dir][p][blk] holds the twiddles the
+//    thread of group blk consumes in order 2p and 2p+1, so a warp reads 512
+//    contiguous bytes per load instead of 31 scattered pairs.
+enum { TW_FWD = 0, TW_INV = 1 };
+template <int LOGN> struct TwLayout {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int PAIRS_WORDS = 2 * N * 2;             // uint2 [2][N] in 32-bit words
+  static constexpr int GROUPED_WORDS = 2 * 16 * (N / 32) * 4;  // uint4 [2][16][N/32]
+  static constexpr int LIMB_WORDS = PAIRS_WORDS + GROUPED_WORDS;
+};
 
 __device__ __forceinline__ uint32_t shoup_mul(uint32_t x, uint32_t w, uint32_t wsh, uint32_t q) {
   return x * w - __umulhi(x, wsh) * q;  // [0, 2q)
 }
 
-__device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m) { return x >= m ? x - m : x; }
+__device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m) { return min(x, x - m); }  // x < 2m
 
 __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t q, uint64_t mu) {
   uint64_t qh = __umul64hi(x, mu);
@@ -89,69 +103,75 @@ template <int LOGN> struct Geo {
   static constexpr int SMEM_WORDS = N + N / 32;    // one padded polynomial
 };
 
-// Element k of group gid in the pass over stages [S0, S0+R).
+// Group gid of the pass over stages [S0, S0+R): element k sits at
+// coefficient base + k*TL; in padded shared memory at pb + k*PSTEP.
 template <int LOGN, int S0, int R>
-__device__ __forceinline__ void group_of(int gid, int& blk, int& base) {
-  constexpr int N = 1 << LOGN;
-  constexpr int TL = N >> (S0 + R);
-  static_assert(TL == 1 || TL >= 32, "pass plan keeps passes bank-conflict free");
-  if (TL >= 32) {
-    blk = gid / TL;
-    base = blk * (N >> S0) + gid % TL;
-  } else {
-    blk = gid;
-    base = blk * (N >> S0);
+struct PassGeo {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int TL = N >> (S0 + R);
+  static constexpr int PSTEP = TL >= 32 ? TL + TL / 32 : 1;
+  static_assert(TL == 1 || TL % 32 == 0, "pass plan keeps passes bank-conflict free");
+  static_assert(TL != 1 || R == 5, "contiguous groups are 32 wide");
+  __device__ __forceinline__ static void of(int gid, int& blk, int& base, int& pb) {
+    if (TL >= 32) {
+      blk = gid / TL;
+      base = blk * (N >> S0) + gid % TL;
+      pb = base + (base >> 5);
+    } else {
+      blk = gid;
+      base = blk * 32;
+      pb = blk * 33;
+    }
   }
-}
+};
 
 // Forward pass over stages [S0, S0+R).  SRC_G: read the group from global
-// memory `g` (natural order) instead of shared memory.
-template <int LOGN, int S0, int R, bool SRC_G>
+// memory `g` (natural order) instead of shared memory.  T: threads sharing
+// this polynomial.
+template <int LOGN, int T, int S0, int R, bool SRC_G>
 __device__ __forceinline__ void fwd_pass(uint32_t* __restrict__ s, const uint32_t* __restrict__ g,
-                                         const uint32_t* __restrict__ tw,
-                                         const uint32_t* __restrict__ twsh, uint32_t q,
-                                         uint32_t two_q, int tid) {
-  constexpr int N = 1 << LOGN, T = N / 32, TL = N >> (S0 + R), RAD = 1 << R;
-  constexpr int NG = 32 / RAD;
+                                         const uint2* __restrict__ tw, uint32_t q, uint32_t two_q,
+                                         int tid) {
+  using PG = PassGeo<LOGN, S0, R>;
+  constexpr int RAD = 1 << R, NG = (PG::N / RAD) / T;
 #pragma unroll
   for (int gi = 0; gi < NG; ++gi) {
-    int blk, base;
-    group_of<LOGN, S0, R>(tid + gi * T, blk, base);
+    int blk, base, pb;
+    PG::of(tid + gi * T, blk, base, pb);
     uint32_t v[RAD];
 #pragma unroll
-    for (int k = 0; k < RAD; ++k) v[k] = SRC_G ? __ldg(g + base + k * TL) : s[pad(base + k * TL)];
+    for (int k = 0; k < RAD; ++k) v[k] = SRC_G ? __ldg(g + base + k * PG::TL) : s[pb + k * PG::PSTEP];
 #pragma unroll
     for (int d = 0; d < R; ++d) {
       const int half = RAD >> (d + 1);
 #pragma unroll
       for (int k = 0; k < RAD; ++k) {
         if (k & half) continue;
-        int ti = (1 << (S0 + d)) + (blk << d) + (k >> (R - d));
-        ct_bfly(v[k], v[k + half], __ldg(tw + ti), __ldg(twsh + ti), q, two_q);
+        const uint2 w = __ldg(tw + (1 << (S0 + d)) + (blk << d) + (k >> (R - d)));
+        ct_bfly(v[k], v[k + half], w.x, w.y, q, two_q);
       }
     }
 #pragma unroll
-    for (int k = 0; k < RAD; ++k) s[pad(base + k * TL)] = v[k];
+    for (int k = 0; k < RAD; ++k) s[pb + k * PG::PSTEP] = v[k];
   }
 }
 
 // Inverse pass over stages [S0, S0+R), applied from the highest stage down.
 // LAST: this pass contains stage 0; fold N^-1 into it and hand each final
 // value (in [0, 2q)) with its coefficient index to `epi`, which stores it.
-template <int LOGN, int S0, int R, bool LAST, class Epi>
-__device__ __forceinline__ void inv_pass(uint32_t* __restrict__ s, const uint32_t* __restrict__ tw,
-                                         const uint32_t* __restrict__ twsh, const LimbConst& lc,
-                                         int tid, Epi epi) {
-  constexpr int N = 1 << LOGN, T = N / 32, TL = N >> (S0 + R), RAD = 1 << R;
-  constexpr int NG = 32 / RAD;
+template <int LOGN, int T, int S0, int R, bool LAST, class Epi>
+__device__ __forceinline__ void inv_pass(uint32_t* __restrict__ s, const uint2* __restrict__ tw,
+                                         const LimbConst& lc, int tid, Epi& epi) {
+  using PG = PassGeo<LOGN, S0, R>;
+  constexpr int RAD = 1 << R, NG = (PG::N / RAD) / T;
   const uint32_t q = lc.q, two_q = lc.two_q;
 #pragma unroll
   for (int gi = 0; gi < NG; ++gi) {
-    int blk, base;
-    group_of<LOGN, S0, R>(tid + gi * T, blk, base);
+    int blk, base, pb;
+    PG::of(tid + gi * T, blk, base, pb);
     uint32_t v[RAD];
 #pragma unroll
-    for (int k = 0; k < RAD; ++k) v[k] = s[pad(base + k * TL)];
+    for (int k = 0; k < RAD; ++k) v[k] = s[pb + k * PG::PSTEP];
 #pragma unroll
     for (int d = R - 1; d >= 0; --d) {
       const int half = RAD >> (d + 1);
@@ -163,56 +183,106 @@ __device__ __forceinline__ void inv_pass(uint32_t* __restrict__ s, const uint32_
           v[k] = shoup_mul(X + Y, lc.n_inv, lc.n_inv_sh, q);
           v[k + half] = shoup_mul(X - Y + two_q, lc.last_w, lc.last_w_sh, q);
         } else {
-          int ti = (1 << (S0 + d)) + (blk << d) + (k >> (R - d));
-          gs_bfly(v[k], v[k + half], __ldg(tw + ti), __ldg(twsh + ti), q, two_q);
+          const uint2 w = __ldg(tw + (1 << (S0 + d)) + (blk << d) + (k >> (R - d)));
+          gs_bfly(v[k], v[k + half], w.x, w.y, q, two_q);
         }
       }
     }
     if (LAST) {
 #pragma unroll
-      for (int k = 0; k < RAD; ++k) epi(v[k], base + k * TL);
+      for (int k = 0; k < RAD; ++k) epi(v[k], base + k * PG::TL);
     } else {
 #pragma unroll
-      for (int k = 0; k < RAD; ++k) s[pad(base + k * TL)] = v[k];
+      for (int k = 0; k < RAD; ++k) s[pb + k * PG::PSTEP] = v[k];
     }
   }
 }
 
-// Full forward NTT of one polynomial: global `src` -> shared `s`, result in
-// shared memory reduced to [0, q).  Caller syncs before reading `s`.
+// The radix-32 pass on the contiguous group blk (32 coefficients), forward
+// (stages S0..S0+4 ascending) or inverse (descending), with the thread-major
+// twiddles of that pass: tg[p * T + blk] holds the twiddles of consumption
+// order 2p and 2p+1.  Stage S0+d touches the pairs (k, k + 2^(4-d)) and uses
+// twiddle m = k >> (5-d) of that stage.
+template <bool INV>
+__device__ __forceinline__ void pass32(uint32_t* v, const uint4* __restrict__ tg, int T, int blk,
+                                       uint32_t q, uint32_t two_q) {
+  int slot = 0;
+#pragma unroll
+  for (int dd = 0; dd < 5; ++dd) {
+    const int d = INV ? 4 - dd : dd;
+    const int half = 32 >> (d + 1);
+#pragma unroll
+    for (int m = 0; m < (1 << d); ++m) {
+      const int sl = slot + m;
+      const uint4 t4 = __ldg(tg + (sl >> 1) * T + blk);
+      const uint32_t w = (sl & 1) ? t4.z : t4.x, ws = (sl & 1) ? t4.w : t4.y;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        if ((k & half) || (k >> (5 - d)) != m) continue;
+        if (INV) gs_bfly(v[k], v[k + half], w, ws, q, two_q);
+        else ct_bfly(v[k], v[k + half], w, ws, q, two_q);
+      }
+    }
+    slot += 1 << d;
+  }
+}
+
+// Full forward NTT of one polynomial by T = N/32 threads: global `src` ->
+// shared `s`, result in shared memory reduced to [0, q).  Caller syncs
+// before reading `s`.  tw_l: the limb's tables (TwLayout words).
 template <int LOGN>
 __device__ __forceinline__ void ntt_forward_to_smem(uint32_t* s, const uint32_t* __restrict__ src,
                                                     const uint32_t* __restrict__ tw_l,
                                                     const LimbConst& lc, int tid) {
-  constexpr int N = 1 << LOGN, R1 = Plan<LOGN>::R1, R2 = Plan<LOGN>::R2;
-  const uint32_t* f = tw_l + TW_FWD * N;
-  const uint32_t* fs = tw_l + TW_FWD_SH * N;
-  fwd_pass<LOGN, 0, R1, true>(s, src, f, fs, lc.q, lc.two_q, tid);
+  constexpr int N = 1 << LOGN, T = N / 32, R1 = Plan<LOGN>::R1, R2 = Plan<LOGN>::R2;
+  const uint2* f = reinterpret_cast<const uint2*>(tw_l) + TW_FWD * N;
+  const uint4* tg = reinterpret_cast<const uint4*>(tw_l + TwLayout<LOGN>::PAIRS_WORDS) + TW_FWD * 16 * T;
+  fwd_pass<LOGN, T, 0, R1, true>(s, src, f, lc.q, lc.two_q, tid);
   __syncthreads();
-  fwd_pass<LOGN, R1, R2, false>(s, nullptr, f, fs, lc.q, lc.two_q, tid);
+  fwd_pass<LOGN, T, R1, R2, false>(s, nullptr, f, lc.q, lc.two_q, tid);
   __syncthreads();
-  fwd_pass<LOGN, R1 + R2, 5, false>(s, nullptr, f, fs, lc.q, lc.two_q, tid);
-  __syncthreads();
-  // reduce [0, 4q) -> [0, q)
-  for (int i = tid; i < N; i += N / 32) {
-    uint32_t x = s[pad(i)];
-    s[pad(i)] = csub(csub(x, lc.two_q), lc.q);
+  {
+    uint32_t v[32];
+    const int pb = tid * 33;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = s[pb + k];
+    pass32<false>(v, tg, T, tid, lc.q, lc.two_q);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) s[pb + k] = csub(csub(v[k], lc.two_q), lc.q);  // [0, 4q) -> [0, q)
   }
 }
 
-// Full inverse NTT of the polynomial in shared memory `s` (values in
-// [0, 2q)); every output coefficient goes through `epi(value_in_[0,2q), u)`.
+// Full inverse NTT by T = N/32 threads of the polynomial in shared memory
+// `s` (values in [0, 2q)); every output coefficient goes through
+// `epi(value_in_[0,2q), u)`.  `bar()` synchronises every thread that takes
+// part (several polynomials may be transformed side by side by disjoint
+// thread groups sharing one barrier).
+template <int LOGN, class Epi, class Bar>
+__device__ __forceinline__ void intt_from_smem_bar(uint32_t* s, const uint32_t* __restrict__ tw_l,
+                                                   const LimbConst& lc, int tid, Epi epi, Bar bar) {
+  constexpr int N = 1 << LOGN, T = N / 32, R1 = Plan<LOGN>::R1, R2 = Plan<LOGN>::R2;
+  const uint2* f = reinterpret_cast<const uint2*>(tw_l) + TW_INV * N;
+  const uint4* tg = reinterpret_cast<const uint4*>(tw_l + TwLayout<LOGN>::PAIRS_WORDS) + TW_INV * 16 * T;
+  {
+    uint32_t v[32];
+    const int pb = tid * 33;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = s[pb + k];
+    pass32<true>(v, tg, T, tid, lc.q, lc.two_q);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) s[pb + k] = v[k];
+  }
+  bar();
+  inv_pass<LOGN, T, R1, R2, false>(s, f, lc, tid, epi);
+  bar();
+  inv_pass<LOGN, T, 0, R1, true>(s, f, lc, tid, epi);
+}
+
+// As above with block-wide barriers.
 template <int LOGN, class Epi>
 __device__ __forceinline__ void intt_from_smem(uint32_t* s, const uint32_t* __restrict__ tw_l,
                                                const LimbConst& lc, int tid, Epi epi) {
-  constexpr int N = 1 << LOGN, R1 = Plan<LOGN>::R1, R2 = Plan<LOGN>::R2;
-  const uint32_t* f = tw_l + TW_INV * N;
-  const uint32_t* fs = tw_l + TW_INV_SH * N;
-  inv_pass<LOGN, R1 + R2, 5, false>(s, f, fs, lc, tid, epi);
-  __syncthreads();
-  inv_pass<LOGN, R1, R2, false>(s, f, fs, lc, tid, epi);
-  __syncthreads();
-  inv_pass<LOGN, 0, R1, true>(s, f, fs, lc, tid, epi);
+  intt_from_smem_bar<LOGN>(s, tw_l, lc, tid, epi, [] { __syncthreads(); });
 }
 
 }  // namespace fl

@@ -18,10 +18,11 @@
 
 namespace fl {
 
-// Resident CTAs per SM the register budget is sized for: the fused kernel
-// holds two padded polynomials in shared memory (3 CTAs of 256 threads at
-// N = 8192), the single-polynomial kernels aim at 1024 threads per SM.
-template <int LOGN> constexpr int minb_two_polys() { return (768 >> (LOGN - 5)) > 0 ? (768 >> (LOGN - 5)) : 1; }
+// Resident CTAs per SM the register budget (64 per thread) is sized for:
+// 1024 threads per SM.  The fused kernel runs 2 * N/32 threads (one group per
+// output component) on two padded polynomials of shared memory, so at
+// N = 8192 two CTAs fit with about 90 KiB of L1 left for the twiddles.
+template <int LOGN> constexpr int minb_two_polys() { return (512 >> (LOGN - 5)) > 0 ? (512 >> (LOGN - 5)) : 1; }
 template <int LOGN> constexpr int minb_one_poly() { return 1024 >> (LOGN - 5); }
 
 // --------------------------------------------------------------------------
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
   const LimbConst lc = cc.limb[l];
   const uint32_t* x = src + ((size_t)(r / src_per) * src_stride + r % src_per) * N;
   uint32_t* y = dst + ((size_t)(r / dst_per) * dst_stride + r % dst_per) * N;
-  ntt_forward_to_smem<LOGN>(sm, x, tw + (size_t)l * 4 * N, lc, tid);
+  ntt_forward_to_smem<LOGN>(sm, x, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, tid);
   __syncthreads();
   for (int v = tid; v < N / 4; v += T) {
     uint4 o;
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
   uint32_t* x = data + (size_t)r * N;
   for (int i = tid; i < N; i += T) sm[pad(i)] = x[i];
   __syncthreads();
-  intt_from_smem<LOGN>(sm, tw + (size_t)l * 4 * N, lc, tid,
+  intt_from_smem<LOGN>(sm, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, tid,
                        [&](uint32_t v, int u) { x[u] = csub(v, lc.q); });
 }
 
@@ -77,11 +78,11 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
 // streaming stores; c0 optionally gets + Delta_l * r[u].
 // --------------------------------------------------------------------------
 template <int LOGN, bool MASK>
-__global__ void __launch_bounds__((1 << LOGN) / 32, minb_two_polys<LOGN>())
+__global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>())
     k_conv_intt(const uint32_t* __restrict__ w_hat, const uint32_t* __restrict__ c_hat,
                 uint32_t* __restrict__ out, const uint32_t* __restrict__ r, ConvDims cd,
                 const uint32_t* __restrict__ tw, CtxConst cc) {
-  constexpr int N = 1 << LOGN, T = N / 32, SW = Geo<LOGN>::SMEM_WORDS;
+  constexpr int N = 1 << LOGN, T = N / 32, T2 = 2 * T, SW = Geo<LOGN>::SMEM_WORDS;
   extern __shared__ uint32_t sm[];
   uint32_t* s0 = sm;
   uint32_t* s1 = sm + SW;
@@ -93,8 +94,10 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_two_polys<LOGN>())
   const uint4* W = reinterpret_cast<const uint4*>(w_hat + ((size_t)l * cd.Cout + i) * cd.G * N);
   const uint32_t* C = c_hat + ((size_t)b * cd.n_in + (size_t)band * cd.G) * ct_words + (size_t)l * N;
 
+  // contraction: each thread owns 4 consecutive slots of both components, so
+  // every weight word is loaded once and used twice
 #pragma unroll 1
-  for (int v = tid; v < N / 4; v += T) {
+  for (int v = tid; v < N / 4; v += T2) {
     uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
 #pragma unroll 2
     for (int g = 0; g < cd.G; ++g) {
@@ -117,31 +120,25 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_two_polys<LOGN>())
         }
       }
     }
+    const int pu = pad(4 * v);  // the 4 slots share one 32-word row
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      s0[pad(4 * v + j)] = barrett64(a0[j], lc.q, lc.mu);
-      s1[pad(4 * v + j)] = barrett64(a1[j], lc.q, lc.mu);
+      s0[pu + j] = barrett64(a0[j], lc.q, lc.mu);
+      s1[pu + j] = barrett64(a1[j], lc.q, lc.mu);
     }
   }
   __syncthreads();
 
+  // inverse NTTs: threads [0, T) transform c0, [T, 2T) transform c1
+  const int h = tid >= T, lt = tid - h * T;
   const size_t oct = (size_t)b * cd.n_out + (size_t)i * cd.bands + band;
-  uint32_t* o0 = out + oct * ct_words + (size_t)l * N;
-  uint32_t* o1 = o0 + (size_t)L * N;
-  const uint32_t* rr = MASK ? r + oct * N : nullptr;
-  const uint32_t* twl = tw + (size_t)l * 4 * N;
-  // One loop body for both components: inlining two transforms lets the
-  // compiler share (and keep live) their twiddle loads, which spills.
-#pragma unroll 1
-  for (int c = 0; c < 2; ++c) {
-    uint32_t* op = c ? o1 : o0;
-    if (c) __syncthreads();
-    intt_from_smem<LOGN>(c ? s1 : s0, twl, lc, tid, [&](uint32_t v, int u) {
-      uint32_t x = v;
-      if (MASK && c == 0) x += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, lc.q);
-      __stcs(op + u, csub(csub(x, lc.two_q), lc.q));
-    });
-  }
+  uint32_t* op = out + oct * ct_words + (size_t)h * L * N + (size_t)l * N;
+  const uint32_t* rr = (MASK && h == 0) ? r + oct * N : nullptr;
+  intt_from_smem<LOGN>(h ? s1 : s0, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, lt, [&](uint32_t v, int u) {
+    uint32_t x = v;
+    if (MASK && rr) x += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, lc.q);
+    __stcs(op + u, csub(csub(x, lc.two_q), lc.q));
+  });
 }
 
 // --------------------------------------------------------------------------
@@ -187,12 +184,12 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
   __syncthreads();
   if (MODE == MODE_DEC) {
     const uint32_t* c0 = ct + ((size_t)n * 2 * L + l) * N;
-    intt_from_smem<LOGN>(sm, tw + (size_t)l * 4 * N, lc, tid, [&](uint32_t v, int u) {
+    intt_from_smem<LOGN>(sm, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, tid, [&](uint32_t v, int u) {
       row[u] = csub(csub(v + __ldg(c0 + u), lc.two_q), lc.q);
     });
   } else {
     const int b = n / gd.n_in, ci = n % gd.n_in;
-    intt_from_smem<LOGN>(sm, tw + (size_t)l * 4 * N, lc, tid, [&](uint32_t v, int u) {
+    intt_from_smem<LOGN>(sm, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, tid, [&](uint32_t v, int u) {
       // Delta*m - a*s - e  (v = a*s in [0, 2q))
       uint32_t m = packed_input(x, gd, b, ci, u);
       uint32_t dm = csub(shoup_mul(m, lc.delta, lc.delta_sh, lc.q), lc.q);  // [0, q)
@@ -349,8 +346,16 @@ static cudaError_t setup_smem() {
   if ((e = cudaFuncSetAttribute(k_conv_intt<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SW * 4))) return e;
   if ((e = cudaFuncSetAttribute(k_pmul_intt<LOGN, MODE_DEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4))) return e;
   if ((e = cudaFuncSetAttribute(k_pmul_intt<LOGN, MODE_ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4))) return e;
+  // every kernel here is sized for ~135 KiB of shared memory per SM; the
+  // rest of the unified L1 is left to the twiddle tables
+  const int carve = 60;
+  if ((e = cudaFuncSetAttribute(k_conv_intt<LOGN, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+  if ((e = cudaFuncSetAttribute(k_conv_intt<LOGN, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+  if ((e = cudaFuncSetAttribute(k_ntt_fwd<LOGN>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
   return cudaSuccess;
 }
+
+size_t twiddle_limb_words(int logn) { return (size_t)TwLayout<11>::LIMB_WORDS << (logn - 11); }
 
 cudaError_t launch_setup(int logn) {
   switch (logn) {
@@ -398,9 +403,9 @@ cudaError_t launch_conv_intt(int logn, int B, const ConvDims& cd, const uint32_t
   const size_t smem = (size_t)2 * (N + N / 32) * 4;
   dim3 grid(B * cd.bands, cd.Cout, cc.L);
   if (r) {
-    FL_DISPATCH(logn, (k_conv_intt<LG, true><<<grid, N / 32, smem, st>>>(w_hat, c_hat, out, r, cd, tw, cc)));
+    FL_DISPATCH(logn, (k_conv_intt<LG, true><<<grid, N / 16, smem, st>>>(w_hat, c_hat, out, r, cd, tw, cc)));
   } else {
-    FL_DISPATCH(logn, (k_conv_intt<LG, false><<<grid, N / 32, smem, st>>>(w_hat, c_hat, out, r, cd, tw, cc)));
+    FL_DISPATCH(logn, (k_conv_intt<LG, false><<<grid, N / 16, smem, st>>>(w_hat, c_hat, out, r, cd, tw, cc)));
   }
   return cudaGetLastError();
 }

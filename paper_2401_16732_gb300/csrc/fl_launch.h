@@ -26,7 +26,39 @@ struct DecConst {  // exact RNS scale-and-round constants
   int L;
 };
 
+#define FL_STACK_MAX 64
+
+struct StackLayer {  // one layer of a persistent stack launch
+  const uint32_t* w_hat;  // [L][Cout][G][N] NTT-domain weights
+  const uint32_t* c_hat;  // [B][n_in][2][L][N] NTT-domain inputs
+  uint32_t* out;          // [B][n_out][2][L][N]
+  const uint32_t* r;      // [B][n_out][N] masks or nullptr
+  int Cout, G, n_in, n_out, bands, BB;  // BB = B * bands
+  long long item_begin;   // first item of this layer in the queue
+};
+
+struct StackArgs {
+  StackLayer layer[FL_STACK_MAX];
+  int n_layers;
+  long long n_items;
+};
+
+struct NttSegs {  // forward NTT of several contiguous row ranges in one launch
+  const uint32_t* src[FL_STACK_MAX];
+  uint32_t* dst[FL_STACK_MAX];
+  int row_begin[FL_STACK_MAX + 1];
+  int n;
+};
+
 cudaError_t launch_setup(int logn);
+cudaError_t launch_stack_setup(int logn);
+cudaError_t launch_ntt_multi_setup(int logn);
+int stack_ctas_per_sm(int logn);
+cudaError_t launch_stack(int logn, const StackArgs& a, unsigned long long* ctl, const uint32_t* tw,
+                         const CtxConst& cc, int sms, cudaStream_t st);
+cudaError_t launch_ntt_multi(int logn, const NttSegs& segs, const uint32_t* tw, const CtxConst& cc,
+                             cudaStream_t st);
+size_t twiddle_limb_words(int logn);
 cudaError_t launch_ntt_fwd(int logn, int rows, const uint32_t* src, int src_per, int src_stride,
                            uint32_t* dst, int dst_per, int dst_stride, int limb_div,
                            const uint32_t* tw, const CtxConst& cc, cudaStream_t st);

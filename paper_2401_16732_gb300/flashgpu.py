@@ -24,6 +24,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 FL_OK, FL_ERR_ARG, FL_ERR_SHAPE, FL_ERR_CUDA, FL_ERR_OOM = 0, -1, -2, -3, -4
+FL_STACK_PER_LAYER, FL_STACK_PERSISTENT = 0, 1
 
 
 class ConvGeom(ctypes.Structure):
@@ -33,6 +34,11 @@ class ConvGeom(ctypes.Structure):
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class StackLayer(ctypes.Structure):
+    _fields_ = [("geom", ctypes.POINTER(ConvGeom)), ("B", ctypes.c_int32), ("w_hat_dev", ctypes.c_void_p),
+                ("ct_in_dev", ctypes.c_void_p), ("r_dev", ctypes.c_void_p), ("ct_out_dev", ctypes.c_void_p)]
 
 
 _vp, _i, _u32, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_size_t
@@ -57,6 +63,13 @@ _SIGS = {
     "fl_he_conv2d_mask": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_he_conv2d_ntt_inputs": ([_vp, _gp, _i, _vp, _vp, _sz, _vp], _i),
     "fl_he_conv2d_from_ntt": ([_vp, _gp, _i, _vp, _vp, _sz, _vp, _vp, _vp], _i),
+    "fl_stack_workspace_bytes": ([_vp, ctypes.POINTER(StackLayer), _i], _sz),
+    "fl_he_conv2d_stack": ([_vp, ctypes.POINTER(StackLayer), _i, _vp, _sz, _vp], _i),
+    "fl_he_conv2d_stack_ntt": ([_vp, ctypes.POINTER(StackLayer), _i, _vp, _sz, _vp], _i),
+    "fl_he_conv2d_stack_run": ([_vp, ctypes.POINTER(StackLayer), _i, _vp, _sz, _vp], _i),
+    "fl_stack_error": ([_vp, _vp, ctypes.POINTER(ctypes.c_uint64)], _i),
+    "fl_ctx_set_stack_kernel": ([_vp, _i], _i),
+    "fl_ctx_get_stack_kernel": ([_vp], _i),
     "fl_ntt_forward": ([_vp, _i, _vp, _vp], _i),
     "fl_ntt_inverse": ([_vp, _i, _vp, _vp], _i),
 }
@@ -212,6 +225,48 @@ class Context:
                                           workspace.numel() * workspace.element_size(), _ptr(r), _ptr(out),
                                           _stream(stream)))
         return out
+
+    # -- many layers in one launch ------------------------------------------
+    def stack_layers(self, specs):
+        """specs: list of dicts with keys g, w_hat, ct_in, out and optional r.
+        Returns the ctypes array fl_he_conv2d_stack takes (keeps the geometry
+        objects alive through the returned array's `_keep`)."""
+        arr = (StackLayer * len(specs))()
+        keep = []
+        for k, sp in enumerate(specs):
+            g = sp["g"]
+            keep.append(g)
+            arr[k].geom = ctypes.pointer(g)
+            arr[k].B = sp["ct_in"].shape[0]
+            arr[k].w_hat_dev = sp["w_hat"].data_ptr()
+            arr[k].ct_in_dev = sp["ct_in"].data_ptr()
+            arr[k].r_dev = sp["r"].data_ptr() if sp.get("r") is not None else None
+            arr[k].ct_out_dev = sp["out"].data_ptr()
+        arr._keep = keep
+        return arr
+
+    def stack_workspace(self, arr) -> torch.Tensor:
+        nbytes = _lib.fl_stack_workspace_bytes(self.h, arr, len(arr))
+        return torch.empty(max(nbytes, 256) // 4, dtype=torch.int32, device=f"cuda:{self.device}")
+
+    def he_conv2d_stack(self, arr, workspace, stream=None, stage="all"):
+        fn = {"all": _lib.fl_he_conv2d_stack, "ntt": _lib.fl_he_conv2d_stack_ntt,
+              "run": _lib.fl_he_conv2d_stack_run}[stage]
+        _check(fn(self.h, arr, len(arr), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                  _stream(stream)))
+
+    @property
+    def stack_kernel(self) -> int:
+        return _lib.fl_ctx_get_stack_kernel(self.h)
+
+    @stack_kernel.setter
+    def stack_kernel(self, k: int):
+        _check(_lib.fl_ctx_set_stack_kernel(self.h, k))
+
+    def stack_error(self, workspace, stream=None) -> int:
+        v = ctypes.c_uint64()
+        _check(_lib.fl_stack_error(_ptr(workspace), _stream(stream), ctypes.byref(v)))
+        return v.value
 
     def mask_to_share(self, ct, r, stream=None) -> torch.Tensor:
         """In place: c0 += Delta*r for ct [..., 2, L, N], r [..., N]."""

@@ -317,3 +317,68 @@ def test_maximum_residues(fg, oracle):
     wh = c.encode_weights(g, dev(w, torch.int8))
     y = u32(c.he_conv2d(g, wh, dev(ct)))
     assert (y[0] == oracle.conv_alg1(ct[0], w, geo, c.primes)).all()
+
+
+# ------------------------------------------------------------------ many layers in one launch
+STACKS = [
+    (2048, 2, [((7, 5, 9, 9, 3, 2, 1), 2, True), ((160, 3, 14, 14, 3, 1, 1), 1, False),
+               ((3, 4, 40, 40, 7, 2, 3), 2, True), ((9, 6, 12, 12, 1, 2, 0), 0, True)]),
+    (4096, 2, [((16, 16, 16, 16, 3, 1, 1), 1, True), ((16, 16, 16, 16, 3, 1, 1), 3, True),
+               ((40, 7, 8, 8, 1, 1, 0), 2, False)]),
+    (8192, 3, [((3, 8, 32, 32, 3, 1, 1), 1, True), ((64, 12, 32, 32, 3, 2, 1), 2, True),
+               ((128, 9, 16, 16, 1, 2, 0), 1, False), ((512, 5, 4, 4, 3, 1, 1), 1, True)]),
+    (16384, 4, [((5, 3, 30, 30, 3, 1, 1), 1, True), ((3, 6, 224, 224, 7, 2, 3), 1, True)]),
+]
+
+
+@pytest.mark.parametrize("kernel", ["per_layer", "persistent"])
+@pytest.mark.parametrize("N,L,layers", STACKS)
+def test_stack_equals_single_layer_and_oracle(fg, oracle, N, L, layers, kernel):
+    c = ctx(fg, N, L)
+    c.stack_kernel = fg.FL_STACK_PERSISTENT if kernel == "persistent" else fg.FL_STACK_PER_LAYER
+    specs, ref = [], []
+    for li, (shape, B, masked) in enumerate(layers):
+        g = c.geom(*shape)
+        w = synth.weights(40 + li, (g.Cout, g.Cin, g.k, g.k))
+        ct = synth.raw_ciphertexts(40 + li, c.primes, (B, g.n_in, 2, L, N))
+        r = synth.masks(40 + li, (B, g.n_out, N), T) if masked else None
+        wh = c.encode_weights(g, dev(w, torch.int8))
+        sp = {"g": g, "w_hat": wh, "ct_in": dev(ct), "r": dev(r) if masked else None,
+              "out": torch.full((B, g.n_out, 2, L, N), -1, dtype=torch.int32, device="cuda"),
+              "w": w, "ct": ct, "rr": r, "shape": shape}
+        specs.append(sp)
+    arr = c.stack_layers(specs)
+    ws = c.stack_workspace(arr)
+    c.he_conv2d_stack(arr, ws)
+    assert c.stack_error(ws) == 0
+    for sp in specs:
+        B = sp["ct_in"].shape[0]
+        if B == 0:
+            continue
+        single = u32(c.he_conv2d(sp["g"], sp["w_hat"], sp["ct_in"], r=sp["r"]))
+        got = u32(sp["out"])
+        assert (got == single).all(), sp["shape"]
+        geo = oracle.geometry(N, *sp["shape"])
+        i_hi = min(sp["g"].Cout, 2)
+        want = oracle.conv_alg1(sp["ct"][B - 1], sp["w"], geo, c.primes, 0, i_hi)
+        if sp["rr"] is not None:
+            want = oracle.mask(want, sp["rr"][B - 1, :i_hi * geo.bands], c.primes)
+        assert (got[B - 1, :i_hi * geo.bands] == want).all(), sp["shape"]
+    # a second run through the split stages gives the same outputs
+    outs = [sp["out"].clone() for sp in specs]
+    for sp in specs:
+        sp["out"].fill_(-1)
+    c.he_conv2d_stack(arr, ws, stage="ntt")
+    c.he_conv2d_stack(arr, ws, stage="run")
+    assert c.stack_error(ws) == 0
+    for sp, o in zip(specs, outs):
+        assert torch.equal(sp["out"], o)
+    c.stack_kernel = fg.FL_STACK_PER_LAYER
+
+
+def test_stack_empty(fg):
+    c = ctx(fg, 4096, 2)
+    arr = c.stack_layers([])
+    ws = torch.empty(64, dtype=torch.int32, device="cuda")
+    c.he_conv2d_stack(arr, ws)
+    assert c.stack_error(ws) == 0
