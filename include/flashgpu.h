@@ -232,6 +232,35 @@ int fl_ctx_get_stack_kernel(const fl_ctx *ctx);
  * fl_he_conv2d_stack (0: no internal wait ran out). */
 int fl_stack_error(const void *workspace_dev, void *stream, uint64_t *error_host);
 
+/* ---- For callers that may not allocate device memory ---- */
+
+/* fl_he_conv2d_mask_noalloc: the same computation and arguments as
+ * fl_he_conv2d_mask, minus the workspace.  It is meant for callers that are
+ * not allowed to allocate device memory -- e.g. a plugin whose host
+ * framework owns all device memory and only passes it input and output
+ * buffers, or a latency-critical request loop that must not allocate (an
+ * allocation can synchronise the device) on the request path.  It has no
+ * counterpart in the paper; it only changes where the scratch lives.
+ *
+ * - Scratch: a fixed array of FL_NOALLOC_SCRATCH_BYTES inside the library,
+ *   one per device, held by every device that loads the library until the
+ *   process exits.  The call needs B*n_in*2*L*N*4 bytes of it
+ *   (fl_he_conv2d_workspace_bytes); a larger call is rejected with
+ *   FL_ERR_ARG and a message, before any work is queued.
+ * - The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture begins.
+ * - Calls share the array: two calls whose work overlaps on the GPU (other
+ *   streams, or other threads) race on it and give undefined results;
+ *   order them (one stream, or events).  The array keeps the last call's
+ *   contents; no part of it has to start at zero, because the first stage
+ *   overwrites every word the second stage reads.
+ * - Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+#define FL_NOALLOC_SCRATCH_BYTES (16u << 20)
+int fl_he_conv2d_mask_noalloc(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_hat_dev,
+                              const uint32_t *ct_in_dev, const uint32_t *r_dev, uint32_t *ct_out_dev,
+                              void *stream);
+
 /* ---- Building blocks, exposed for tests ---- */
 
 /* In-place negacyclic NTT / inverse NTT of n RNS polynomials data_dev

@@ -135,6 +135,28 @@ int launched(cudaError_t e, const char* what) { return e == cudaSuccess ? FL_OK 
 
 }  // namespace
 
+namespace fl {
+int ctx_internals(const fl_ctx* ctx, int* logN, int* L, int* device, const uint32_t** tw, const CtxConst** cc) {
+  if (!ctx) return fail(FL_ERR_ARG, "null context");
+  *logN = ctx->logN;
+  *L = ctx->L;
+  *device = ctx->device;
+  *tw = ctx->tw;
+  *cc = &ctx->cc;
+  return FL_OK;
+}
+
+int fail_msg(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+}  // namespace fl
+
 extern "C" {
 
 const char* fl_last_error(void) { return g_err.c_str(); }

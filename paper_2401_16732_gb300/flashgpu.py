@@ -25,6 +25,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 FL_OK, FL_ERR_ARG, FL_ERR_SHAPE, FL_ERR_CUDA, FL_ERR_OOM = 0, -1, -2, -3, -4
 FL_STACK_PER_LAYER, FL_STACK_PERSISTENT = 0, 1
+FL_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class ConvGeom(ctypes.Structure):
@@ -68,6 +69,7 @@ _SIGS = {
     "fl_he_conv2d_stack_ntt": ([_vp, ctypes.POINTER(StackLayer), _i, _vp, _sz, _vp], _i),
     "fl_he_conv2d_stack_run": ([_vp, ctypes.POINTER(StackLayer), _i, _vp, _sz, _vp], _i),
     "fl_stack_error": ([_vp, _vp, ctypes.POINTER(ctypes.c_uint64)], _i),
+    "fl_he_conv2d_mask_noalloc": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "fl_ctx_set_stack_kernel": ([_vp, _i], _i),
     "fl_ctx_get_stack_kernel": ([_vp], _i),
     "fl_ntt_forward": ([_vp, _i, _vp, _vp], _i),
@@ -267,6 +269,15 @@ class Context:
         v = ctypes.c_uint64()
         _check(_lib.fl_stack_error(_ptr(workspace), _stream(stream), ctypes.byref(v)))
         return v.value
+
+    def he_conv2d_mask_noalloc(self, g, w_hat, ct_in, r, out, stream=None) -> torch.Tensor:
+        """fl_he_conv2d_mask without a workspace: the library's fixed scratch
+        array is used instead (FL_NOALLOC_SCRATCH_BYTES; calls must not
+        overlap on the GPU).  Allocates nothing on the device; `out` is the
+        caller's [B][n_out][2][L][N] buffer."""
+        _check(_lib.fl_he_conv2d_mask_noalloc(self.h, ctypes.byref(g), ct_in.shape[0], _ptr(w_hat), _ptr(ct_in),
+                                              _ptr(r), _ptr(out), _stream(stream)))
+        return out
 
     def mask_to_share(self, ct, r, stream=None) -> torch.Tensor:
         """In place: c0 += Delta*r for ct [..., 2, L, N], r [..., N]."""
