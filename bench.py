@@ -64,41 +64,55 @@ def slot_macs(g, B, L, N):
 # ---------------------------------------------------------------------------
 # CPU oracle leg (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample_step(wl, seed, per_layer):
-    """Run Algorithm 1 (oracle route O2, OpenMP over output channels) on
-    `per_layer` output channels of every layer of one image; return the
-    extrapolated seconds for the whole workload (all channels, all B images)
-    and the seconds actually spent."""
+def o2_macs(wl, shape):
+    """Multiply-adds Algorithm 1 (route O2) spends on one image of a layer:
+    Cout * Cin * k^2 taps over 2 components, L limbs, N coefficients, bands."""
+    import oracle
+    geo = oracle.geometry(wl.N, *shape)
+    Cin, Cout, k = shape[0], shape[1], shape[4]
+    return Cout * Cin * k * k * 2 * wl.L * wl.N * geo.bands
+
+
+def oracle_sample(wl, seed, budget_s):
+    """Time Algorithm 1 (oracle route O2, OpenMP over output channels) on a
+    bounded sample of (layer, output channel) jobs of one image, walking the
+    layers in order with min(cores, Cout) channels each until `budget_s` is
+    spent; the inner loop is the same for every multiply-add, so the whole
+    workload's time follows from the measured multiply-add rate.  Returns
+    (extrapolated seconds per step, seconds spent, sample description)."""
     import oracle
     primes = oracle.find_primes(wl.N, wl.L)
-    est, spent = 0.0, 0.0
-    for li, (Cin, Cout, H, W, k, s, p) in enumerate(wl.layers):
-        geo = oracle.geometry(wl.N, Cin, Cout, H, W, k, s, p)
+    threads = oracle.num_threads()
+    spent, done, layers_done, chans = 0.0, 0, 0, 0
+    for li, shape in enumerate(wl.layers):
+        Cin, Cout, H, W, k, s, p = shape
+        n = min(threads, Cout)
+        job = o2_macs(wl, shape) * n // Cout
+        if layers_done and done and spent + job / (done / spent) > budget_s:
+            continue
+        geo = oracle.geometry(wl.N, *shape)
         w = synth.weights(seed, (Cout, Cin, k, k), li)
         ct = synth.raw_ciphertexts(seed, primes, (geo.n_in, 2, wl.L, wl.N), li)
-        n = min(per_layer, Cout)
         t0 = time.perf_counter()
         oracle.conv_alg1(ct, w, geo, primes, 0, n)
-        dt = time.perf_counter() - t0
-        spent += dt
-        est += dt * (Cout / n) * wl.B
-    return est, spent
+        spent += time.perf_counter() - t0
+        done += job
+        layers_done += 1
+        chans += n
+    rate = done / spent
+    total = sum(o2_macs(wl, sh) for sh in wl.layers) * wl.B
+    desc = (f"Algorithm 1 (oracle O2, OpenMP over output channels, {threads} threads) on {chans} output channels "
+            f"from {layers_done} of {len(wl.layers)} layers of one image ({spent:.1f} s, {rate / 1e9:.2f} G "
+            f"multiply-adds/s), extrapolated by multiply-add count to all channels, layers and B={wl.B}")
+    return total / rate, spent, desc
 
 
-def cpu_baseline(wl, seed, budget_s=20.0):
+def cpu_baseline(wl, seed, budget_s=15.0):
     import oracle
-    threads = oracle.num_threads()
-    per_layer = max(1, threads)
-    est, spent = oracle_sample_step(wl, seed, per_layer)
-    # one more pass with a larger sample when the first was short
-    if spent < budget_s / 4:
-        per_layer = max(1, int(per_layer * min(4.0, budget_s / 2 / max(spent, 1e-3))))
-        est, spent = oracle_sample_step(wl, seed, per_layer)
+    est, spent, desc = oracle_sample(wl, seed, budget_s)
     n_layers = len(wl.layers) * wl.B
-    return {"value": n_layers / est, "unit": "layers/s", "cores": threads, "kind": "oracle",
-            "sample": f"Algorithm 1 (oracle O2, OpenMP over output channels) on the first {per_layer} output "
-                      f"channels of each of the {len(wl.layers)} layers of one image ({spent:.1f} s of CPU work), "
-                      f"extrapolated linearly to all channels and B={wl.B}"}
+    return {"value": n_layers / est, "unit": "layers/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": desc}
 
 
 def run_reference(args, wl, rank, world):
@@ -106,26 +120,24 @@ def run_reference(args, wl, rank, world):
         return 0
     import oracle
     threads = oracle.num_threads()
-    per_layer = max(1, threads)
+    budget = 8.0
     for _ in range(args.warmup):
-        oracle_sample_step(wl, args.seed, per_layer)
-    ests, spent = [], 0.0
+        oracle_sample(wl, args.seed, budget / 4)
+    ests, desc = [], ""
     for _ in range(args.steps):
-        est, sp = oracle_sample_step(wl, args.seed, per_layer)
+        est, sp, desc = oracle_sample(wl, args.seed, budget)
         ests.append(est)
-        spent += sp
     n_layers = len(wl.layers) * wl.B
     est_step = sum(ests) / len(ests)
     value = n_layers / est_step
-    sample = (f"Algorithm 1 (oracle O2) on {per_layer} output channels per layer of one image per step, "
-              f"extrapolated to all channels and B={wl.B}")
     print(json.dumps({
         "impl": "reference", "metric": "encrypted conv layers/s", "value": value, "unit": "layers/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": est_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": wl.name, "layers": len(wl.layers), "batch": wl.B, "N": wl.N, "L": wl.L,
                    "t": T_PLAIN},
-        "cpu_baseline": {"value": value, "unit": "layers/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "layers/s", "cores": threads, "kind": "oracle",
+                         "sample": "each step: " + desc},
         "e2e": {"value": value, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
     return 0
@@ -189,6 +201,7 @@ def run_gpu(args, wl, rank, world, local_rank):
     import torch.distributed as dist
 
     from paper_2401_16732_gb300 import flashgpu
+    from paper_2401_16732_gb300.dist import max_over_ranks, whole_job_rate
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -211,20 +224,26 @@ def run_gpu(args, wl, rank, world, local_rank):
         g = ctx.geom(*shape)
         w = synth.weights(seed, (g.Cout, g.Cin, g.k, g.k), li)
         x = synth.activations(seed, (B, g.Cin, g.H, g.W), li)
-        a = synth.uniform_residues(seed, ctx.primes, (B, g.n_in, L, N), li)
-        e = synth.cbd_noise(seed, (B, g.n_in, N), li)
-        r = synth.masks(seed, (B, g.n_out, N), T_PLAIN, li)
+        a = synth.device_uniform_residues(seed, ctx.primes, (B, g.n_in, L, N), li, device=dev)
+        e = synth.device_cbd_noise(seed, (B, g.n_in, N), li, device=dev)
         lay = {"g": g, "w_hat": ctx.encode_weights(g, to_dev(w, torch.int8)),
-               "ct": ctx.encrypt(sk, g, to_dev(x), to_dev(a), to_dev(e)), "r": to_dev(r),
+               "ct": ctx.encrypt(sk, g, to_dev(x), a, e),
+               "r": synth.device_masks(seed, (B, g.n_out, N), T_PLAIN, li, device=dev),
                "out": torch.empty((B, g.n_out, 2, L, N), dtype=torch.int32, device=dev)}
+        del a, e
         layers.append(lay)
     arr = ctx.stack_layers([{"g": lay["g"], "w_hat": lay["w_hat"], "ct_in": lay["ct"], "r": lay["r"],
                              "out": lay["out"]} for lay in layers])
     ws = ctx.stack_workspace(arr)
     torch.cuda.synchronize()
-    from paper_2401_16732_gb300.autotune import tune_stack
-    tuned = tune_stack(ctx, [{"g": lay["g"], "ct_in": lay["ct"], "r": lay["r"]} for lay in layers], arr, ws,
-                       stream=stream, cache=None)
+    if args.stack_kernel == "auto":
+        from paper_2401_16732_gb300.autotune import tune_stack
+        tuned = tune_stack(ctx, [{"g": lay["g"], "ct_in": lay["ct"], "r": lay["r"]} for lay in layers], arr, ws,
+                           stream=stream, cache=None)
+    else:
+        ctx.stack_kernel = (flashgpu.FL_STACK_PERSISTENT if args.stack_kernel == "persistent"
+                            else flashgpu.FL_STACK_PER_LAYER)
+        tuned = {"kernel": args.stack_kernel, "ms": None}
 
     def step(events=None):
         # forward NTT of every layer's inputs (one launch), then the
@@ -272,11 +291,7 @@ def run_gpu(args, wl, rank, world, local_rank):
     t_end.synchronize()
     torch.cuda.synchronize()
     barrier()
-    ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_end), dev)
 
     # ---- per-kernel durations (eager launches queued behind a GPU sleep so
     # that event timestamps bracket the kernels, not host launch latency) ----
@@ -297,20 +312,26 @@ def run_gpu(args, wl, rank, world, local_rank):
     # ---- end to end: pinned host inputs -> device -> path -> host outputs ----
     e2e = None
     if not args.skip_e2e:
-        h_in = [lay["ct"].cpu().pin_memory() for lay in layers]
-        h_out = [torch.empty(lay["out"].shape, dtype=torch.int32, pin_memory=True) for lay in layers]
-        h2d = sum(t.numel() * 4 for t in h_in)
-        d2h = sum(t.numel() * 4 for t in h_out)
-        n_e2e = max(1, min(args.steps, 5))
+        # every layer's inputs come from, and every layer's output ciphertexts
+        # go to, pinned host memory (one reused buffer per direction, sized for
+        # the largest layer)
+        in_words = max(lay["ct"].numel() for lay in layers)
+        out_words = max(lay["out"].numel() for lay in layers)
+        h_in = torch.empty(in_words, dtype=torch.int32, pin_memory=True)
+        h_out = torch.empty(out_words, dtype=torch.int32, pin_memory=True)
+        h_in.copy_(max(layers, key=lambda lay: lay["ct"].numel())["ct"].view(-1).cpu())
+        h2d = sum(lay["ct"].numel() * 4 for lay in layers)
+        d2h = sum(lay["out"].numel() * 4 for lay in layers)
+        n_e2e = max(1, min(args.steps, 5 if d2h < 8e9 else 2))
 
         def e2e_step():
             with torch.cuda.stream(stream):
-                for lay, h in zip(layers, h_in):
-                    lay["ct"].copy_(h, non_blocking=True)
+                for lay in layers:
+                    lay["ct"].view(-1).copy_(h_in[:lay["ct"].numel()], non_blocking=True)
             replay()
             with torch.cuda.stream(stream):
-                for lay, h in zip(layers, h_out):
-                    h.copy_(lay["out"], non_blocking=True)
+                for lay in layers:
+                    h_out[:lay["out"].numel()].copy_(lay["out"].view(-1), non_blocking=True)
             stream.synchronize()
 
         e2e_step()
@@ -318,12 +339,8 @@ def run_gpu(args, wl, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             e2e_step()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
-        e2e = {"value": world * B * len(layers) * n_e2e / dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
+        e2e_rate, _ = whole_job_rate(B * len(layers) * n_e2e, time.perf_counter() - t0, dev)
+        e2e = {"value": e2e_rate, "unit": "layers/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": n_e2e}
     clocks.stop()
 
@@ -373,6 +390,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--stack-kernel", default="auto", choices=["auto", "per_layer", "persistent"],
+                    help="kernel for the contraction/INTT/mask stage (auto: time both, keep the faster)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.config]

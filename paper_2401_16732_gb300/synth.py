@@ -69,3 +69,40 @@ def raw_ciphertexts(seed: int, primes, shape, *index) -> np.ndarray:
     for l, ql in enumerate(primes):
         out[..., l, :] = g.integers(0, ql, size=shape[:-2] + shape[-1:], dtype=np.int64)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Device-side draws for large benchmark inputs (same distributions; a seeded
+# torch generator on the device instead of numpy on the host).
+# ---------------------------------------------------------------------------
+def _torch_gen(seed: int, purpose: int, *index: int, device="cuda"):
+    import torch
+    ss = np.random.SeedSequence([seed, purpose, *index]).generate_state(2, np.uint32)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(ss[0]) << 32 | int(ss[1]))
+    return g
+
+
+def device_uniform_residues(seed: int, primes, shape, *index, device="cuda"):
+    """int32 tensor [..., L, N] on `device`, limb l uniform in [0, primes[l])."""
+    import torch
+    g = _torch_gen(seed, UNIFORM_A, *index, device=device)
+    out = torch.empty(shape, dtype=torch.int32, device=device)
+    for l, ql in enumerate(primes):
+        out[..., l, :] = torch.randint(0, int(ql), shape[:-2] + shape[-1:], generator=g, device=device,
+                                       dtype=torch.int64).to(torch.int32)
+    return out
+
+
+def device_masks(seed: int, shape, t: int, *index, device="cuda"):
+    import torch
+    g = _torch_gen(seed, MASK, *index, device=device)
+    return torch.randint(0, t, shape, generator=g, device=device, dtype=torch.int32)
+
+
+def device_cbd_noise(seed: int, shape, *index, eta: int = 21, device="cuda"):
+    import torch
+    g = _torch_gen(seed, NOISE, *index, device=device)
+    n = torch.full(shape, float(eta), device=device)
+    p = torch.full(shape, 0.5, device=device)
+    return (torch.binomial(n, p, generator=g) - torch.binomial(n, p, generator=g)).to(torch.int32)
