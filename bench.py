@@ -31,6 +31,14 @@ from paper_2401_16732_gb300.workloads import WORKLOADS  # noqa: E402
 T_PLAIN = 65537
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129e6
+# Integer-ALU roofline of the inverse NTT: a lazy Gentleman-Sande butterfly
+# with Shoup multiplication needs 4 ALU-pipe operations (sum, conditional
+# subtract as add + min, difference) and 3 multiplies; the ALU pipe retires 16
+# lanes per clock per SM sub-partition.  152 SMs x 4 x 16 x 2.07 GHz / 4.
+ALU_BFLY_PEAK = 152 * 4 * 16 * 2.07e9 / 4
+# DRAM bytes (read + write) of one step's launches of the dominant kernel, from
+# one ncu capture of the same command (profiles/); a kernel change voids them.
+TRAFFIC = {("resnet18", "per_layer"): 2.660e9}
 
 
 def peaks():
@@ -51,6 +59,11 @@ def layer_bytes(g, B, L, N, masked=True):
     out = B * g.n_out * 2 * L * N * 4
     r = B * g.n_out * N * 4 if masked else 0
     return w + cin + out + r
+
+
+def intt_butterflies(g, B, L, N):
+    """Butterflies of the inverse NTTs the fused kernel runs for one layer."""
+    return B * g.n_out * 2 * L * (N // 2) * (N.bit_length() - 1)
 
 
 def ntt_bytes(g, B, L, N):
@@ -351,8 +364,26 @@ def run_gpu(args, wl, rank, world, local_rank):
     step_bytes = conv_bytes + sum(ntt_bytes(g, B, L, N) for g in geoms)
     macs = sum(slot_macs(g, B, L, N) for g in geoms)
     hbm, peak_kind = peaks()
-    achieved = conv_bytes / (kern["conv"] * 1e-3) / 1e9
+    bfly = sum(intt_butterflies(g, B, L, N) for g in geoms)
+    kern_s = kern["conv"] * 1e-3
+    achieved = conv_bytes / kern_s / 1e9
+    achieved_bfly = bfly / kern_s
+    hbm_floor, alu_floor = conv_bytes / (hbm * 1e9), bfly / ALU_BFLY_PEAK
     value = world * B * len(layers) * args.steps / (ms * 1e-3)
+    kname = ("k_stack (persistent, all layers)" if tuned["kernel"] == "persistent" else
+             "k_conv_intt (one launch per layer)") + ": contraction + inverse NTT + mask"
+    traffic = TRAFFIC.get((args.config, tuned["kernel"]))
+    hbm_line = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": peak_kind, "traffic": traffic}
+    alu_line = {"bound": "alu", "achieved": achieved_bfly / 1e12, "peak": ALU_BFLY_PEAK / 1e12,
+                "unit": "T butterflies/s", "frac": achieved_bfly / ALU_BFLY_PEAK,
+                "peak_source": "derived: 152 SMs x 4 x 16 ALU lanes x 2.07 GHz / 4 ALU ops per butterfly"}
+    main, other = (hbm_line, alu_line) if hbm_floor >= alu_floor else (alu_line, hbm_line)
+    roof = dict(main)
+    roof.update({"kernel": kname, "kernel_ms_per_step": kern["conv"], "algorithmic_bytes_per_step": conv_bytes,
+                 "algorithmic_butterflies_per_step": bfly, "hbm_floor_ms": hbm_floor * 1e3,
+                 "alu_floor_ms": alu_floor * 1e3, "other_roofline": other,
+                 "ntt_inputs_ms_per_step": kern["ntt"]})
     line = {
         "metric": "encrypted conv layers/s", "value": value, "unit": "layers/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -363,13 +394,7 @@ def run_gpu(args, wl, rank, world, local_rank):
                    "stack_kernel": tuned["kernel"], "autotune_ms": tuned["ms"]},
         "slot_mac_per_s": world * macs * args.steps / (ms * 1e-3),
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"kernel": ("k_stack (persistent, all layers)" if tuned["kernel"] == "persistent" else
-                                "k_conv_intt (one launch per layer)") + ": contraction + inverse NTT + mask",
-                     "bound": "hbm",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "peak_source": peak_kind, "traffic": None,
-                     "kernel_ms_per_step": kern["conv"], "algorithmic_bytes_per_step": conv_bytes,
-                     "ntt_inputs_ms_per_step": kern["ntt"]},
+        "roofline": roof,
         "clocks": clocks.summary(),
     }
     if e2e is not None:
@@ -380,13 +405,56 @@ def run_gpu(args, wl, rank, world, local_rank):
     return 0
 
 
+def run_serve(args, rank, world, local_rank):
+    """Serving loop (continuous batching) on ResNet-18 (N=8192) and ResNet-50
+    (N=16384) requests: Poisson arrivals at 200 requests/s, 70% / 30%, batch
+    size uniform in 1..8.  Reports served layers/s and per-request p50/p99."""
+    import torch
+
+    from paper_2401_16732_gb300 import serve
+    from paper_2401_16732_gb300.workloads import resnet18_cifar, resnet50_imagenet
+    torch.cuda.set_device(local_rank)
+    models = {"resnet18": serve.ModelSpec("resnet18", 8192, 3, resnet18_cifar()),
+              "resnet50": serve.ModelSpec("resnet50", 16384, 4, resnet50_imagenet())}
+    srv = serve.Server(models)
+    mix = {"resnet18": 0.7, "resnet50": 0.3}
+    warm = serve.poisson_requests(max(args.warmup, 3), 200.0, mix, seed=args.seed + 100)
+    srv.run(warm, realtime=False)
+    n = 12 * args.steps
+    reqs = serve.poisson_requests(n, 200.0, mix, seed=args.seed)
+    keep = {(q.rid, 0) for q in reqs[:4]}
+    srv.keep = keep
+    srv.layer_images = 0
+    torch.cuda.synchronize()
+    finished, wall = srv.run(reqs, realtime=True)
+    if rank != 0:
+        return 0
+    stats = serve.latency_stats(finished)
+    li = sum(q.B * len(models[q.model].layers) for q in finished)
+    offered = sum(q.B * len(models[q.model].layers) for q in reqs) / reqs[-1].arrival
+    print(json.dumps({
+        "metric": "served encrypted conv layers/s", "value": li / wall, "unit": "layers/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "serving: Poisson 200 req/s, 70% ResNet-18 CIFAR (N=8192, L=3), 30% ResNet-50 "
+                               "ImageNet (N=16384, L=4), batch U{1..8}, continuous batching by layer rounds",
+                   "requests": n, "admission": "peak live bytes of the request's largest layer",
+                   "weights_resident_gib": sum(r.weight_bytes for r in srv.res.values()) / 2 ** 30,
+                   "stack_kernel": "per_layer"},
+        "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "mean_ms": stats.get("mean_ms"),
+        "wall_s": wall, "rounds": srv.rounds, "peak_active_requests": srv.peak_active,
+        "offered_layers_per_s": offered, "offered_over_served": offered / (li / wall),
+    }), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="resnet18", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="resnet18", choices=sorted(WORKLOADS) + ["serve"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
@@ -394,6 +462,9 @@ def main():
                     help="kernel for the contraction/INTT/mask stage (auto: time both, keep the faster)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.config == "serve":
+        return run_serve(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+                         int(os.environ.get("LOCAL_RANK", "0")))
     wl = WORKLOADS[args.config]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
