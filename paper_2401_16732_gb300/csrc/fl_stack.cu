@@ -6,19 +6,24 @@
 // output channel, limb), both components.  Two thread teams share the CTA:
 //
 //   producer team (PT threads): per-slot contraction mod q_l of the item's
-//     weights with its NTT-domain inputs, 64-bit lazy accumulation, written
-//     to one of BUFS shared-memory buffers (two polynomials each);
-//   consumer team (2 * N/32 threads): inverse NTT of both components side by
-//     side, mask epilogue, streaming stores of the output ciphertext limb.
+//     weights with its NTT-domain inputs, 64-bit lazy accumulation.  Its
+//     loads stream through a private cp.async ring, DEPTH stages deep per
+//     thread, so that enough bytes are in flight to cover L2/HBM latency.  It
+//     writes the reduced NTT-domain result straight into the item's place in
+//     the output ciphertext (the lines stay in L2).
+//   consumer team (PAR * N/32 threads): loads that result back into shared
+//     memory, runs the inverse NTT of both components, adds the mask and
+//     overwrites the output with the final coefficient-domain limb.
 //
-// With two buffers the producer computes item k+1 while the consumer
-// transforms item k, so the HBM-bound contraction overlaps the ALU-bound
-// transform.  Hand-off uses shared-memory mbarriers; every wait is bounded
-// by a wall-clock limit after which the team sets an error word and leaves
-// the loop (both teams then drain out: no thread is ever left in a hardware
-// barrier).  Team-internal synchronisation uses named barriers whose thread
-// counts are fixed, and each team's leader alone waits on an mbarrier and
-// broadcasts the outcome, so all threads of a team take the same path.
+// The producer runs up to QD items ahead of the consumer, so the HBM- and
+// L2-bound contraction overlaps the ALU-bound transform.  Hand-off uses
+// shared-memory mbarriers (release/acquire at CTA scope, which orders the
+// producer's global writes before the consumer's reads); every wait is
+// bounded by a wall-clock limit after which the team sets an error word and
+// leaves the loop (both teams then drain out: no thread is ever left in a
+// hardware barrier).  Team-internal synchronisation uses named barriers whose
+// thread counts are fixed, and each team's leader alone waits on an mbarrier
+// and broadcasts the outcome, so all threads of a team take the same path.
 #include <cuda_runtime.h>
 
 #include "fl_device.cuh"
@@ -106,25 +111,30 @@ __device__ __forceinline__ Item decode(const StackArgs& a, long long it) {
 // components side by side; PAR = 1: N/32 threads, one component after the
 // other (N = 16384, where twice as many threads would leave too few
 // registers).  MINB: resident CTAs per SM.
-constexpr int DEPTH = 3;  // stages in flight per producer thread
-constexpr int GS = 2;     // weight rows per stage
+constexpr int QD = 4;  // items the producer may run ahead of the consumer
 
-template <int LOGN, int BUFS>
-__host__ __device__ constexpr int ring_word_offset() {
-  // polys, then 2*BUFS mbarriers, BUFS+1 item words and two flags (rounded to 16 bytes)
-  return BUFS * 2 * Geo<LOGN>::SMEM_WORDS + ((2 * BUFS * 8 + (BUFS + 1) * 8 + 8 + 15) / 16) * 4;
+// Shared memory: consumer polys [2][SW] | mbarriers full[QD], empty[QD] |
+// item ids [QD] | producer broadcast | two abort flags | producer ring.
+template <int LOGN>
+__host__ __device__ constexpr int ring_word_offset() {  // same for every GS
+  return 2 * Geo<LOGN>::SMEM_WORDS + ((2 * QD * 8 + QD * 8 + 8 + 8 + 15) / 16) * 4;
 }
 
-template <int LOGN, int BUFS, int PT, int PAR, int MINB>
+// PAR = 2: the consumer team has 2 * N/32 threads and transforms both
+// components side by side; PAR = 1: N/32 threads, one component after the
+// other (N = 16384, where twice as many threads would leave too few
+// registers).  DEPTH: producer stages in flight per thread, GS weight rows
+// each.  MINB: resident CTAs per SM.
+template <int LOGN, int PT, int PAR, int DEPTH, int GS, int MINB>
 __global__ void __launch_bounds__(PT + PAR * ((1 << LOGN) / 32), MINB)
     k_stack(StackArgs a, unsigned long long* __restrict__ ctl, const uint32_t* __restrict__ tw, CtxConst cc) {
   constexpr int N = 1 << LOGN, T = N / 32, CTN = PAR * T, SW = Geo<LOGN>::SMEM_WORDS;
   extern __shared__ __align__(16) uint32_t sm[];
-  uint32_t* polys = sm;  // [BUFS][2][SW]
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + BUFS * 2 * SW);
-  uint64_t* empty = full + BUFS;
-  volatile long long* slot_item = reinterpret_cast<volatile long long*>(empty + BUFS);  // [BUFS]
-  volatile long long* bcast = slot_item + BUFS;                                         // producer broadcast
+  uint32_t* polys = sm;  // [2][SW]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + 2 * SW);
+  uint64_t* empty = full + QD;
+  volatile long long* slot_item = reinterpret_cast<volatile long long*>(empty + QD);  // [QD]
+  volatile long long* bcast = slot_item + QD;
   volatile int* abort_p = reinterpret_cast<volatile int*>(bcast + 1);
   volatile int* abort_c = abort_p + 1;
   unsigned long long* counter = ctl;
@@ -132,7 +142,7 @@ __global__ void __launch_bounds__(PT + PAR * ((1 << LOGN) / 32), MINB)
 
   const int tid = threadIdx.x;
   if (tid == 0) {
-    for (int b = 0; b < BUFS; ++b) {
+    for (int b = 0; b < QD; ++b) {
       mbar_init(&full[b], 1);
       mbar_init(&empty[b], 1);
     }
@@ -141,6 +151,9 @@ __global__ void __launch_bounds__(PT + PAR * ((1 << LOGN) / 32), MINB)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+
+  const int L = cc.L;
+  const size_t ct_words = (size_t)2 * L * N;
 
   if (tid < PT) {
     // ---------------- producer: contraction ----------------
@@ -151,84 +164,86 @@ __global__ void __launch_bounds__(PT + PAR * ((1 << LOGN) / 32), MINB)
     // continuing into the next item, and accumulates from shared memory.
     const int pt = tid;
     constexpr int CS = 4 * PT;
-    uint4* ring = reinterpret_cast<uint4*>(sm + ring_word_offset<LOGN, BUFS>());  // [DEPTH][3][GS][PT]
-    const int L = cc.L;
-    const size_t ct_words = (size_t)2 * L * N;
+    uint4* ring = reinterpret_cast<uint4*>(sm + ring_word_offset<LOGN>());  // [DEPTH][3][GS][PT]
 
-    // current / next item (the leader fetches one item ahead)
     long long cur, nxt;
     if (pt == 0) *bcast = (long long)atomicAdd(counter, 1ull);
     named_sync(BAR_PRODUCER, PT);
     cur = *bcast;
     named_sync(BAR_PRODUCER, PT);
 
-    // Stage stream cursor for issuing copies: item iss.it, stage iss_s.  It
-    // runs at most DEPTH stages ahead of consumption, and every item has at
-    // least 8 stages, so it never passes the item after `cur`.
+    // Stage stream cursor for issuing copies: item iss.it, slot range
+    // iss_r, row chunk iss_g.  It runs at most DEPTH stages ahead of
+    // consumption, and every item has at least N/CS >= 8 stages, so it never
+    // passes the item after `cur`.  Counters advance incrementally (no
+    // division) to keep the per-stage instruction count low.
+    constexpr int NR = N / CS;
     struct Src {
       const uint32_t* W;  // weight rows of the item (row g at W + g*N)
       const uint32_t* C;  // component-0 input row g at C + g*ct_words, component 1 at + L*N
-      int G, ngc, ns;     // rows, row chunks, stages
+      uint32_t* out;      // component-0 output limb (component 1 at + L*N)
+      int G, ngc;         // rows, row chunks
       long long it;
+      bool live;
     };
     auto src_of = [&](long long it, Src& o) {
       o.it = it;
-      if (it < 0 || it >= a.n_items) {
-        o.ns = 0;
-        return;
-      }
+      o.live = it >= 0 && it < a.n_items;
+      if (!o.live) return;
       const Item x = decode(a, it);
       const StackLayer& y = a.layer[x.li];
       const int bimg = x.bb / y.bands, band = x.bb % y.bands;
       o.W = y.w_hat + ((size_t)x.l * y.Cout + x.i) * y.G * N;
       o.C = y.c_hat + ((size_t)bimg * y.n_in + (size_t)band * y.G) * ct_words + (size_t)x.l * N;
+      o.out = y.out + ((size_t)bimg * y.n_out + (size_t)x.i * y.bands + band) * ct_words + (size_t)x.l * N;
       o.G = y.G;
       o.ngc = (y.G + GS - 1) / GS;
-      o.ns = (N / CS) * o.ngc;
     };
     Src iss, cons;
     src_of(cur, iss);
     cons = iss;
-    int iss_s = 0;     // next stage of `iss` to issue
-    long long issued = 0, consumed = 0;
+    int iss_r = 0, iss_g = 0, iss_slot = 0, inflight = 0;
     bool nxt_known = false;
     nxt = -1;
+    const uint32_t ln = (uint32_t)L * N;
 
-    // issue the copies of one stage into ring slot (issued % DEPTH)
     auto issue = [&]() {
-      const int slot = (int)(issued % DEPTH);
-      const int r = iss_s / iss.ngc, g0 = (iss_s % iss.ngc) * GS;
-      const int u = r * CS + 4 * pt;
+      const int u = iss_r * CS + 4 * pt;
+      const int g0 = iss_g * GS;
+      uint4* dst = ring + (iss_slot * 3 * GS) * PT + pt;
+      const uint32_t* wsrc = iss.W + (size_t)g0 * N + u;
+      const uint32_t* csrc = iss.C + (size_t)g0 * ct_words + u;
 #pragma unroll
       for (int gs = 0; gs < GS; ++gs) {
-        const int g = g0 + gs;
-        if (g < iss.G) {
-          const uint32_t* wsrc = iss.W + (size_t)g * N + u;
-          const uint32_t* c0 = iss.C + (size_t)g * ct_words + u;
-          cp_async16(ring + ((slot * 3 + 0) * GS + gs) * PT + pt, wsrc);
-          cp_async16(ring + ((slot * 3 + 1) * GS + gs) * PT + pt, c0);
-          cp_async16(ring + ((slot * 3 + 2) * GS + gs) * PT + pt, c0 + (size_t)L * N);
+        if (g0 + gs < iss.G) {
+          cp_async16(dst + (0 * GS + gs) * PT, wsrc + (size_t)gs * N);
+          cp_async16(dst + (1 * GS + gs) * PT, csrc + (size_t)gs * ct_words);
+          cp_async16(dst + (2 * GS + gs) * PT, csrc + (size_t)gs * ct_words + ln);
         }
       }
       cp_async_commit();
-      ++issued;
-      if (++iss_s == iss.ns) {  // move the issue cursor to the next item
-        iss_s = 0;
-        Src n;
-        src_of(nxt_known ? nxt : -1, n);
-        iss = n;
+      ++inflight;
+      iss_slot = iss_slot + 1 == DEPTH ? 0 : iss_slot + 1;
+      if (++iss_g == iss.ngc) {
+        iss_g = 0;
+        if (++iss_r == NR) {
+          iss_r = 0;
+          Src n;
+          src_of(nxt_known ? nxt : -1, n);
+          iss = n;
+        }
       }
     };
-    auto can_issue = [&]() { return iss.ns > 0 && (nxt_known || iss.it == cur); };
+    auto can_issue = [&]() { return iss.live && (nxt_known || iss.it == cur); };
+    int cons_slot = 0;
 
     for (int j = 0;; ++j) {
-      const int b = j % BUFS;
-      // leader: fetch the item after `cur`, and wait until buffer b is free
+      const int b = j % QD;
       if (pt == 0) {
         bool ok = true;
         if (cur < a.n_items) {
           *bcast = (long long)atomicAdd(counter, 1ull);
-          if (j >= BUFS) ok = mbar_wait(&empty[b], (unsigned)((j / BUFS - 1) & 1));
+          if (j >= QD) ok = mbar_wait(&empty[b], (unsigned)((j / QD - 1) & 1));
         } else {
           *bcast = a.n_items;
         }
@@ -249,72 +264,74 @@ __global__ void __launch_bounds__(PT + PAR * ((1 << LOGN) / 32), MINB)
         }
         break;
       }
-      // keep DEPTH stages in flight
-      while (issued - consumed < DEPTH && can_issue()) issue();
+      while (inflight < DEPTH && can_issue()) issue();
 
       const Item x = decode(a, cur);
       const LimbConst lc = cc.limb[x.l];
-      uint32_t* s0 = polys + (size_t)(2 * b) * SW;
-      uint32_t* s1 = s0 + SW;
-      uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
-      int folded = 0;
 #pragma unroll 1
-      for (int st = 0; st < cons.ns; ++st) {
-        // stage `consumed` is the oldest in flight: wait for this thread's copies
-        const long long ahead = issued - consumed - 1;
-        if (ahead >= 2) cp_async_wait<2>();
-        else if (ahead == 1) cp_async_wait<1>();
-        else cp_async_wait<0>();
-        const int slot = (int)(consumed % DEPTH);
-        const int r = st / cons.ngc, g0 = (st % cons.ngc) * GS;
+      for (int r = 0; r < NR; ++r) {
+        uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+        int folded = 0;
+#pragma unroll 1
+        for (int gc = 0; gc < cons.ngc; ++gc) {
+          // wait for this thread's copies of the oldest stage in flight
+          if (inflight >= 3) cp_async_wait<2>();
+          else if (inflight == 2) cp_async_wait<1>();
+          else cp_async_wait<0>();
+          const uint4* src = ring + (cons_slot * 3 * GS) * PT + pt;
+          const int rows = min(GS, cons.G - gc * GS);
 #pragma unroll
-        for (int gs = 0; gs < GS; ++gs) {
-          if (g0 + gs < cons.G) {
-            const uint4 w = ring[((slot * 3 + 0) * GS + gs) * PT + pt];
-            const uint4 x0 = ring[((slot * 3 + 1) * GS + gs) * PT + pt];
-            const uint4 x1 = ring[((slot * 3 + 2) * GS + gs) * PT + pt];
-            a0[0] += (uint64_t)w.x * x0.x;
-            a0[1] += (uint64_t)w.y * x0.y;
-            a0[2] += (uint64_t)w.z * x0.z;
-            a0[3] += (uint64_t)w.w * x0.w;
-            a1[0] += (uint64_t)w.x * x1.x;
-            a1[1] += (uint64_t)w.y * x1.y;
-            a1[2] += (uint64_t)w.z * x1.z;
-            a1[3] += (uint64_t)w.w * x1.w;
-            if (++folded == 16) {  // 16 products < 2^64: fold before the next
-              folded = 0;
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                a0[q] = barrett64(a0[q], lc.q, lc.mu);
-                a1[q] = barrett64(a1[q], lc.q, lc.mu);
-              }
+          for (int gs = 0; gs < GS; ++gs) {
+            if (gs < rows) {
+              const uint4 w = src[(0 * GS + gs) * PT];
+              const uint4 x0 = src[(1 * GS + gs) * PT];
+              const uint4 x1 = src[(2 * GS + gs) * PT];
+              a0[0] += (uint64_t)w.x * x0.x;
+              a0[1] += (uint64_t)w.y * x0.y;
+              a0[2] += (uint64_t)w.z * x0.z;
+              a0[3] += (uint64_t)w.w * x0.w;
+              a1[0] += (uint64_t)w.x * x1.x;
+              a1[1] += (uint64_t)w.y * x1.y;
+              a1[2] += (uint64_t)w.z * x1.z;
+              a1[3] += (uint64_t)w.w * x1.w;
             }
           }
-        }
-        // The refill below overwrites the slot just read: make the
-        // accumulations (which consume the shared-memory loads) complete in
-        // program order before the copy is issued.
-        asm volatile("" ::"l"(a0[0]), "l"(a0[1]), "l"(a0[2]), "l"(a0[3]), "l"(a1[0]), "l"(a1[1]), "l"(a1[2]),
-                     "l"(a1[3]));
-        ++consumed;
-        // refill the slot just freed (the ring slot is private to this thread)
-        if (can_issue()) issue();
-        if (st % cons.ngc == cons.ngc - 1) {  // slot range r complete
-          const int pu = pad(r * CS + 4 * pt);
+          folded += rows;
+          if (folded > 16 - GS && gc + 1 < cons.ngc) {  // the next chunk could pass 16 products: fold
+            folded = 0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            s0[pu + q] = barrett64(a0[q], lc.q, lc.mu);
-            s1[pu + q] = barrett64(a1[q], lc.q, lc.mu);
-            a0[q] = 0;
-            a1[q] = 0;
+            for (int q = 0; q < 4; ++q) {
+              a0[q] = barrett64(a0[q], lc.q, lc.mu);
+              a1[q] = barrett64(a1[q], lc.q, lc.mu);
+            }
           }
-          folded = 0;
+          // The refill below overwrites the slot just read: make the
+          // accumulations (which consume the shared-memory loads) complete
+          // in program order before the copy is issued.
+          asm volatile("" ::"l"(a0[0]), "l"(a0[1]), "l"(a0[2]), "l"(a0[3]), "l"(a1[0]), "l"(a1[1]), "l"(a1[2]),
+                       "l"(a1[3]));
+          --inflight;
+          cons_slot = cons_slot + 1 == DEPTH ? 0 : cons_slot + 1;
+          if (can_issue()) issue();
         }
+        // slot range r complete: its NTT-domain result goes to the output
+        const int u = r * CS + 4 * pt;
+        uint4 y0, y1;
+        y0.x = barrett64(a0[0], lc.q, lc.mu);
+        y0.y = barrett64(a0[1], lc.q, lc.mu);
+        y0.z = barrett64(a0[2], lc.q, lc.mu);
+        y0.w = barrett64(a0[3], lc.q, lc.mu);
+        y1.x = barrett64(a1[0], lc.q, lc.mu);
+        y1.y = barrett64(a1[1], lc.q, lc.mu);
+        y1.z = barrett64(a1[2], lc.q, lc.mu);
+        y1.w = barrett64(a1[3], lc.q, lc.mu);
+        *reinterpret_cast<uint4*>(cons.out + u) = y0;
+        *reinterpret_cast<uint4*>(cons.out + ln + u) = y1;
       }
-      named_sync(BAR_PRODUCER, PT);  // all slots of the item written
+      named_sync(BAR_PRODUCER, PT);  // every result word of the item is written
       if (pt == 0) {
         slot_item[b] = cur;
-        mbar_arrive(&full[b]);
+        mbar_arrive(&full[b]);  // release at CTA scope: the writes above precede the consumer's reads
       }
       cur = nxt;
       Src nc;
@@ -326,9 +343,9 @@ __global__ void __launch_bounds__(PT + PAR * ((1 << LOGN) / 32), MINB)
     // ---------------- consumer: inverse NTTs + mask ----------------
     const int ct = tid - PT;
     for (int k = 0;; ++k) {
-      const int b = k % BUFS;
+      const int b = k % QD;
       if (ct == 0) {
-        if (!mbar_wait(&full[b], (unsigned)((k / BUFS) & 1))) {
+        if (!mbar_wait(&full[b], (unsigned)((k / QD) & 1))) {
           atomicOr(err, 2ull);
           *abort_c = 1;
         }
@@ -339,19 +356,29 @@ __global__ void __launch_bounds__(PT + PAR * ((1 << LOGN) / 32), MINB)
       if (it < 0) break;
       const Item x = decode(a, it);
       const StackLayer& s = a.layer[x.li];
-      const int L = cc.L;
       const LimbConst lc = cc.limb[x.l];
       const int bimg = x.bb / s.bands, band = x.bb % s.bands;
-      const size_t ct_words = (size_t)2 * L * N;
       const size_t oct = (size_t)bimg * s.n_out + (size_t)x.i * s.bands + band;
+      uint32_t* o0 = s.out + oct * ct_words + (size_t)x.l * N;
+      // the NTT-domain result of both components into shared memory
+      for (int v = ct; v < N / 2; v += CTN) {
+        const int h = v >= N / 4, vq = v - h * (N / 4);
+        const uint4 y = __ldcg(reinterpret_cast<const uint4*>(o0 + (size_t)h * L * N) + vq);
+        uint32_t* sp = polys + (size_t)h * SW + pad(4 * vq);
+        sp[0] = y.x;
+        sp[1] = y.y;
+        sp[2] = y.z;
+        sp[3] = y.w;
+      }
+      named_sync(BAR_CONSUMER, CTN);
       const uint32_t* twl = tw + (size_t)x.l * TwLayout<LOGN>::LIMB_WORDS;
 #pragma unroll 1
       for (int hs = 0; hs < 3 - PAR; ++hs) {
         const int h = PAR == 2 ? (ct >= T) : hs;
         const int lt = PAR == 2 ? ct - h * T : ct;
-        uint32_t* op = s.out + oct * ct_words + (size_t)h * L * N + (size_t)x.l * N;
+        uint32_t* op = o0 + (size_t)h * L * N;
         const uint32_t* rr = (s.r && h == 0) ? s.r + oct * N : nullptr;
-        uint32_t* sp = polys + (size_t)(2 * b + h) * SW;
+        uint32_t* sp = polys + (size_t)h * SW;
         if (hs) named_sync(BAR_CONSUMER, CTN);
         intt_from_smem_bar<LOGN>(sp, twl, lc, lt,
                                  [&](uint32_t v, int u) {
@@ -361,28 +388,26 @@ __global__ void __launch_bounds__(PT + PAR * ((1 << LOGN) / 32), MINB)
                                  },
                                  [] { named_sync(BAR_CONSUMER, CTN); });
       }
-      named_sync(BAR_CONSUMER, CTN);  // every consumer thread is done with buffer b
+      named_sync(BAR_CONSUMER, CTN);  // every consumer thread is done with the item
       if (ct == 0) mbar_arrive(&empty[b]);
     }
   }
 }
 
-template <int LOGN, int BUFS, int PT>
-static size_t stack_smem() {
-  return (size_t)ring_word_offset<LOGN, BUFS>() * 4 + (size_t)DEPTH * 3 * GS * PT * 16;
-}
-
-// N <= 8192: two buffers (the producer runs one item ahead); N = 16384: the
-// four padded polynomials of two buffers do not fit, so one buffer and a
-// consumer team that transforms one component after the other.  Resident
-// CTAs per SM follow from shared memory (about 135 KiB per SM).
 template <int LOGN> struct StackCfg {
-  static constexpr int BUFS = LOGN <= 13 ? 2 : 1;
   static constexpr int PT = LOGN == 11 ? 64 : LOGN == 12 ? 128 : 256;
   static constexpr int PAR = LOGN <= 13 ? 2 : 1;
+  static constexpr int DEPTH = 3;
+  static constexpr int GS = LOGN <= 13 ? 4 : 2;
   static constexpr int MINB = LOGN == 11 ? 4 : LOGN == 12 ? 2 : 1;
   static constexpr int THREADS = PT + PAR * ((1 << LOGN) / 32);
 };
+
+template <int LOGN>
+static size_t stack_smem() {
+  using C = StackCfg<LOGN>;
+  return (size_t)ring_word_offset<LOGN>() * 4 + (size_t)C::DEPTH * 3 * C::GS * C::PT * 16;
+}
 
 int stack_ctas_per_sm(int logn) {
   switch (logn) {
@@ -397,8 +422,8 @@ int stack_ctas_per_sm(int logn) {
 template <int LOGN>
 static cudaError_t stack_setup() {
   using C = StackCfg<LOGN>;
-  return cudaFuncSetAttribute(k_stack<LOGN, C::BUFS, C::PT, C::PAR, C::MINB>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stack_smem<LOGN, C::BUFS, C::PT>());
+  return cudaFuncSetAttribute(k_stack<LOGN, C::PT, C::PAR, C::DEPTH, C::GS, C::MINB>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stack_smem<LOGN>());
 }
 
 cudaError_t launch_stack_setup(int logn) {
@@ -415,8 +440,7 @@ template <int LOGN>
 static cudaError_t stack_launch(const StackArgs& a, unsigned long long* ctl, const uint32_t* tw, const CtxConst& cc,
                                 int grid, cudaStream_t st) {
   using C = StackCfg<LOGN>;
-  k_stack<LOGN, C::BUFS, C::PT, C::PAR, C::MINB>
-      <<<grid, C::THREADS, stack_smem<LOGN, C::BUFS, C::PT>(), st>>>(a, ctl, tw, cc);
+  k_stack<LOGN, C::PT, C::PAR, C::DEPTH, C::GS, C::MINB><<<grid, C::THREADS, stack_smem<LOGN>(), st>>>(a, ctl, tw, cc);
   return cudaGetLastError();
 }
 

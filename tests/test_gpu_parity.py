@@ -171,6 +171,8 @@ CONV_CASES = [
     (2048, 2, (3, 4, 40, 40, 7, 2, 3), 2),       # 7x7/2 stem with row bands
     (8192, 3, (3, 8, 32, 32, 3, 1, 1), 1),       # ResNet-18 stem shape, N = 8192
     (16384, 4, (5, 3, 30, 30, 3, 1, 1), 1),      # N = 16384, L = 4
+    (2048, 3, (8, 101, 6, 6, 3, 1, 1), 2),       # odd Cout, grid beyond two waves
+    (8192, 3, (40, 150, 8, 8, 3, 1, 1), 1),      # 450 CTAs at N = 8192
 ]
 
 
