@@ -216,7 +216,10 @@ int fl_he_conv2d_stack_run(fl_ctx *ctx, const fl_stack_layer *layers, int n_laye
 
 /* Kernel used by the second stage of a stack:
  * FL_STACK_PER_LAYER: one fused contraction + inverse NTT + mask launch per
- *   layer (two CTAs of 2*N/32 threads per SM, both components side by side);
+ *   layer (two CTAs of 2*N/32 threads per SM, both components side by side),
+ *   the layers spread over three streams of the context that fork from and
+ *   join back into `stream` (so one context should not run two stacks at
+ *   once from different host threads);
  * FL_STACK_PERSISTENT: one persistent warp-specialised launch over all
  *   layers (a cp.async-fed contraction team and an inverse-NTT team per SM
  *   handing items over through shared-memory mbarriers).

@@ -20,9 +20,14 @@ using fl::DecConst;
 using fl::GeomDims;
 typedef unsigned __int128 u128;
 
+constexpr int kAuxStreams = 3;
+
 struct fl_ctx {
   int N, logN, L, device, sms;
   int stack_kernel;  // FL_STACK_PER_LAYER or FL_STACK_PERSISTENT
+  // per-layer stack launches fan out over these (fork/join through events)
+  cudaStream_t aux[kAuxStreams];
+  cudaEvent_t fork_ev, join_ev[kAuxStreams];
   uint32_t t;
   uint32_t psi[FL_MAX_L];
   CtxConst cc;
@@ -292,6 +297,14 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
     delete c;
     return cuda_fail(e, "kernel set-up");
   }
+  bool ok = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < kAuxStreams && ok; ++k)
+    ok = cudaStreamCreateWithFlags(&c->aux[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    delete c;
+    return fail(FL_ERR_OOM, "auxiliary streams / events");
+  }
   if ((e = cudaMalloc(&c->tw, host.size() * sizeof(uint32_t))) != cudaSuccess) {
     delete c;
     return fail(FL_ERR_OOM, "twiddle tables: %s", cudaGetErrorString(e));
@@ -307,6 +320,11 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
 
 void fl_ctx_destroy(fl_ctx* ctx) {
   if (!ctx) return;
+  for (int k = 0; k < kAuxStreams; ++k) {
+    if (ctx->aux[k]) cudaStreamDestroy(ctx->aux[k]);
+    if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   if (ctx->tw) cudaFree(ctx->tw);
   delete ctx;
 }
@@ -591,16 +609,31 @@ static int stack_impl(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, v
   if (!(stages & 2)) return FL_OK;
   if (ctx->stack_kernel == FL_STACK_PERSISTENT)
     return launched(fl::launch_stack(ctx->logN, a, ctl, ctx->tw, ctx->cc, ctx->sms, st), "stack");
-  // per-layer fused launches; the error word stays 0 (these kernels never wait)
+  // per-layer fused launches; the error word stays 0 (these kernels never
+  // wait).  The layers are independent, so they fan out over the context's
+  // auxiliary streams and join back into `st`.
   cudaError_t e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return cuda_fail(e, "control reset");
+  const int fan = a.n_layers < kAuxStreams ? a.n_layers : kAuxStreams;
+  if (fan > 1) {
+    if ((e = cudaEventRecord(ctx->fork_ev, st)) != cudaSuccess) return cuda_fail(e, "fork");
+    for (int k = 0; k < fan; ++k)
+      if ((e = cudaStreamWaitEvent(ctx->aux[k], ctx->fork_ev, 0)) != cudaSuccess) return cuda_fail(e, "fork");
+  }
   for (int k = 0; k < a.n_layers; ++k) {
     const fl::StackLayer& y = a.layer[k];
     fl::ConvDims cd{y.Cout, y.G, y.n_in, y.n_out, y.bands};
+    cudaStream_t sk = fan > 1 ? ctx->aux[k % fan] : st;
     if ((rc = launched(fl::launch_conv_intt(ctx->logN, y.BB / y.bands, cd, y.w_hat, y.c_hat, y.out, y.r, ctx->tw,
-                                            ctx->cc, st),
+                                            ctx->cc, sk),
                        "stack layer")))
       return rc;
+  }
+  if (fan > 1) {
+    for (int k = 0; k < fan; ++k) {
+      if ((e = cudaEventRecord(ctx->join_ev[k], ctx->aux[k])) != cudaSuccess) return cuda_fail(e, "join");
+      if ((e = cudaStreamWaitEvent(st, ctx->join_ev[k], 0)) != cudaSuccess) return cuda_fail(e, "join");
+    }
   }
   return FL_OK;
 }
