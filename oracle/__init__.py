@@ -70,6 +70,8 @@ def lib():
         L.or_conv_alg1.argtypes = conv
         L.or_mask.argtypes = [u32, i32, u32p, u32p, u32p, u32p]
         L.or_num_threads.restype = ctypes.c_int
+        L.or_batch_encode.argtypes = [u32, u32, u32, u32p, u32p]
+        L.or_batch_decode.argtypes = [u32, u32, u32, u32p, u32p]
         _lib = L
     return _lib
 
@@ -376,6 +378,87 @@ def noise_bound(w: np.ndarray, primes, t=T_DEFAULT, x_max=255, e_max=21,
     S = int(np.abs(w.astype(np.int64)).reshape(w.shape[0], -1).sum(1).max())
     b = r_t * (-(-x_max * S // t) + 1) + e_max * S
     return b + (r_t if masked else 0)
+
+
+# ---------------------------------------------------------------------------
+# Batch encoding and the server side of the x^2 + x protocol (Sec. 5.2)
+# ---------------------------------------------------------------------------
+def plain_root(N: int, t: int = T_DEFAULT) -> int:
+    """Reading: psi_t is the first g^((t-1)/2N), g = 2, 3, ..., with
+    psi_t^N = -1 mod t (a primitive 2N-th root of unity; t = 1 mod 2N)."""
+    assert (t - 1) % (2 * N) == 0
+    for g in range(2, t):
+        psi = pow(g, (t - 1) // (2 * N), t)
+        if pow(psi, N, t) == t - 1:
+            return psi
+    raise ValueError("no root")
+
+
+def batch_encode(slots, N, t=T_DEFAULT) -> np.ndarray:
+    s = _u32(np.asarray(slots) % t)
+    out = np.zeros(N, np.uint32)
+    lib().or_batch_encode(N, t, plain_root(N, t), _p(s, ctypes.c_uint32), _p(out, ctypes.c_uint32))
+    return out
+
+
+def batch_decode(m, N, t=T_DEFAULT) -> np.ndarray:
+    m = _u32(np.asarray(m) % t)
+    out = np.zeros(N, np.uint32)
+    lib().or_batch_decode(N, t, plain_root(N, t), _p(m, ctypes.c_uint32), _p(out, ctypes.c_uint32))
+    return out
+
+
+def lift_centered(m, q: int, t: int = T_DEFAULT) -> np.ndarray:
+    """Plaintext coefficients in [0, t) as integers in (-t/2, t/2], mod q."""
+    m = np.asarray(m).astype(np.int64)
+    c = np.where(m > t // 2, m - t, m)
+    return (c % q).astype(np.uint32)
+
+
+def pmult(ct, m, primes, t=T_DEFAULT) -> np.ndarray:
+    """PMult (Sec. 2.2): both components times the plaintext polynomial m
+    (coefficients lifted to (-t/2, t/2]) in R_q.  ct [n][2][L][N], m [n][N]."""
+    ct = _u32(ct)
+    out = np.zeros_like(ct)
+    for c in range(ct.shape[0]):
+        for l, ql in enumerate(primes):
+            mm = lift_centered(m[c], ql, t)
+            for j in range(2):
+                out[c, j, l] = negacyclic_mul(mm, ct[c, j, l], ql)
+    return out
+
+
+def add_plain(ct, m, primes, t=T_DEFAULT) -> np.ndarray:
+    """HAdd with a plaintext: c0 <- c0 + Delta*m (m in [0, t))."""
+    return mask(ct, np.asarray(m, dtype=np.uint32), primes, t)
+
+
+def sub_ct(a, b, primes) -> np.ndarray:
+    """HAdd of a and the negation of b, limb by limb."""
+    a, b = _u32(a), _u32(b)
+    out = np.empty_like(a)
+    for l, ql in enumerate(primes):
+        out[..., l, :] = ((a[..., l, :].astype(np.int64) - b[..., l, :]) % ql).astype(np.uint32)
+    return out
+
+
+def x2x_server_round1(ct_batch, r, v, primes, t=T_DEFAULT) -> np.ndarray:
+    """Server step of Sec. 5.2 on <a+r> (batch encoded): PMult by the batch
+    encoding of 2r, then add v (batch encoded): <2ar + 2r^2 + v>.
+    ct_batch [n][2][L][N]; r, v [n][N] slot vectors mod t."""
+    N = ct_batch.shape[-1]
+    pm = np.stack([batch_encode((2 * np.asarray(r[c], np.int64)) % t, N, t) for c in range(ct_batch.shape[0])])
+    pv = np.stack([batch_encode(v[c], N, t) for c in range(ct_batch.shape[0])])
+    return add_plain(pmult(ct_batch, pm, primes, t), pv, primes, t)
+
+
+def x2x_server_round2(ct_x, ct_y, r, v, primes, t=T_DEFAULT) -> np.ndarray:
+    """Final server step of Sec. 5.2: with <X> = <a^2 + 2ar + r^2 + a + r> and
+    <Y> = <2ar + 2r^2 + v> (both direct encoded), <a^2 + a> = <X> - <Y> +
+    (r^2 - r + v) (direct encoded plaintext)."""
+    r = np.asarray(r, np.int64)
+    c = (r * r - r + np.asarray(v, np.int64)) % t
+    return add_plain(sub_ct(ct_x, ct_y, primes), c, primes, t)
 
 
 def num_threads() -> int:

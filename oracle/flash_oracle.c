@@ -316,3 +316,50 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Batch (SIMD) encoding over Z_t[x]/(x^N+1) (Sec. 2.2; used by the x^2+x */
+/* protocol of Sec. 5.2).  Slot k of a plaintext m is its value at the    */
+/* root psi_t^(2k+1), psi_t a primitive 2N-th root of unity mod t.         */
+/*   decode: s_k = m(psi_t^(2k+1)) mod t                                   */
+/*   encode: m_j = N^-1 * sum_k s_k * psi_t^(-(2k+1) j) mod t              */
+/* (the interpolation formula: the N roots are distinct and x^N+1 splits). */
+/* ------------------------------------------------------------------ */
+static uint64_t or_powmod(uint64_t b, uint64_t e, uint64_t m)
+{
+    uint64_t r = 1 % m;
+    b %= m;
+    while (e) {
+        if (e & 1) r = r * b % m;
+        b = b * b % m;
+        e >>= 1;
+    }
+    return r;
+}
+
+void or_batch_decode(uint32_t N, uint32_t t, uint32_t psi, const uint32_t *m, uint32_t *s)
+{
+    for (uint32_t k = 0; k < N; ++k) {
+        uint64_t z = or_powmod(psi, 2ull * k + 1, t), zp = 1, acc = 0;
+        for (uint32_t j = 0; j < N; ++j) {
+            acc = (acc + (uint64_t)m[j] * zp) % t;
+            zp = zp * z % t;
+        }
+        s[k] = (uint32_t)acc;
+    }
+}
+
+void or_batch_encode(uint32_t N, uint32_t t, uint32_t psi, const uint32_t *s, uint32_t *m)
+{
+    uint64_t psi_inv = or_powmod(psi, t - 2, t);
+    uint64_t n_inv = or_powmod(N, t - 2, t);
+    for (uint32_t j = 0; j < N; ++j) {
+        /* sum_k s_k * (psi^-(2k+1))^j = psi^-j * sum_k s_k * (psi^-2j)^k */
+        uint64_t step = or_powmod(psi_inv, 2ull * j, t), zp = or_powmod(psi_inv, j, t), acc = 0;
+        for (uint32_t k = 0; k < N; ++k) {
+            acc = (acc + (uint64_t)s[k] * zp) % t;
+            zp = zp * step % t;
+        }
+        m[j] = (uint32_t)(acc * n_inv % t);
+    }
+}

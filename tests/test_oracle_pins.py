@@ -360,3 +360,46 @@ def test_planted_mistakes_are_caught(oracle):
         W[1:] = (ql - W[1:]) % ql
         return W
     assert not (conv_with(unsigned) == want).all()
+
+
+# ----------------------------------------------------------------- batch encoding and x^2 + x
+@pytest.mark.parametrize("N", [8, 16, 64])
+def test_batch_encoding_is_slotwise(oracle, N):
+    """decode(encode(s)) = s, and the negacyclic product of two encodings
+    decodes to the slot-wise product (the defining property of SIMD slots)."""
+    g = np.random.default_rng(N)
+    s1, s2 = g.integers(0, T, N), g.integers(0, T, N)
+    m1, m2 = oracle.batch_encode(s1, N), oracle.batch_encode(s2, N)
+    assert (oracle.batch_decode(m1, N) == s1).all()
+    prod = oracle.negacyclic_mul(m1, m2, T)
+    assert (oracle.batch_decode(prod, N) == (s1 * s2) % T).all()
+    # direct check of decode against the definition on one slot
+    psi = oracle.plain_root(N)
+    k = 3 % N
+    z = pow(psi, 2 * k + 1, T)
+    assert int(oracle.batch_decode(m1, N)[k]) == sum(int(m1[j]) * pow(z, j, T) for j in range(N)) % T
+
+
+def test_x2x_protocol_end_to_end(oracle):
+    """Sec. 5.2: starting from <a> (direct), mask with r, let the client square,
+    run both server rounds, and the result decrypts to a^2 + a mod t."""
+    N, L = 256, 3
+    primes = oracle.find_primes(N, L)
+    s = synth.secret_key(51, N)
+    a = synth.masks(51, (1, N), T)
+    r = synth.masks(52, (1, N), T)
+    v = synth.masks(53, (1, N), T)
+    enc = lambda m, k: oracle.encrypt(s, synth.uniform_residues(60 + k, primes, (1, L, N)),
+                                      synth.cbd_noise(60 + k, (1, N)), np.asarray(m, np.uint32), primes)
+    ct_a = enc(a, 0)
+    z = oracle.decrypt(s, oracle.mask(ct_a, r, primes), primes)          # client: a + r
+    assert (z == (a + r) % T).all()
+    X = (z * z + z) % T                                                  # client: x^2 + x
+    ct_x = enc(X, 1)                                                     # direct encoding
+    ct_zb = enc(oracle.batch_encode(z[0], N)[None], 2)                   # batch encoding
+    ct_y_b = oracle.x2x_server_round1(ct_zb, r, v, primes)              # server round 1
+    Yb = oracle.batch_decode(oracle.decrypt(s, ct_y_b, primes)[0], N)    # client decrypts slots
+    assert (Yb == (2 * r[0] * z[0] + v[0]) % T).all()
+    ct_y = enc(Yb[None], 3)                                              # re-encrypt, direct
+    out = oracle.x2x_server_round2(ct_x, ct_y, r, v, primes)             # server round 2
+    assert (oracle.decrypt(s, out, primes) == (a * a + a) % T).all()
