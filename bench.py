@@ -128,9 +128,47 @@ def cpu_baseline(wl, seed, budget_s=15.0):
             "sample": desc}
 
 
+# ---------------------------------------------------------------------------
+# x^2 + x activation protocol, server side (Sec. 5.2)
+# ---------------------------------------------------------------------------
+X2X_B = 16
+
+
+def x2x_shapes():
+    """The activation layers of ResNet-18 CIFAR: every conv input but the
+    stem's (the image) is an x^2 + x output, one activation ciphertext per
+    packed input ciphertext of that conv."""
+    wl = WORKLOADS["resnet18"]
+    return wl, wl.layers[1:]
+
+
+def x2x_sample(seed, budget_s):
+    """Oracle server rounds 1 and 2 (Sec. 5.2) on single ciphertexts at N=8192,
+    L=3 until `budget_s` is spent.  Returns (seconds per ciphertext, sample)."""
+    import oracle
+    wl, _ = x2x_shapes()
+    N, L = wl.N, wl.L
+    primes = oracle.find_primes(N, L)
+    spent, done = 0.0, 0
+    while spent < budget_s or done == 0:
+        ct = synth.raw_ciphertexts(seed, primes, (1, 2, L, N), done, 1)
+        cy = synth.raw_ciphertexts(seed, primes, (1, 2, L, N), done, 2)
+        r, v = synth.masks(seed, (1, N), T_PLAIN, done, 1), synth.masks(seed, (1, N), T_PLAIN, done, 2)
+        t0 = time.perf_counter()
+        oracle.x2x_server_round1(ct, r, v, primes)
+        oracle.x2x_server_round2(ct, cy, r, v, primes)
+        spent += time.perf_counter() - t0
+        done += 1
+    desc = (f"oracle rounds 1 and 2 (schoolbook PMult, O(N^2) batch encoding) on {done} activation ciphertexts "
+            f"at N={N}, L={L} ({spent:.1f} s), scaled by ciphertext count")
+    return spent / done, desc
+
+
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return 0
+    if args.config == "x2x":
+        return run_reference_x2x(args)
     import oracle
     threads = oracle.num_threads()
     budget = 8.0
@@ -152,6 +190,34 @@ def run_reference(args, wl, rank, world):
         "cpu_baseline": {"value": value, "unit": "layers/s", "cores": threads, "kind": "oracle",
                          "sample": "each step: " + desc},
         "e2e": {"value": value, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def run_reference_x2x(args):
+    import oracle
+    wl, shapes = x2x_shapes()
+    geos = [oracle.geometry(wl.N, *sh) for sh in shapes]
+    n = X2X_B * sum(g.n_in for g in geos)
+    acts = X2X_B * sum(sh[0] * sh[2] * sh[3] for sh in shapes)
+    for _ in range(args.warmup):
+        x2x_sample(args.seed, 0.0)
+    per_ct, desc = [], ""
+    for _ in range(args.steps):
+        sec, desc = x2x_sample(args.seed, 6.0)
+        per_ct.append(sec)
+    step_s = n * sum(per_ct) / len(per_ct)
+    value = acts / step_s
+    print(json.dumps({
+        "impl": "reference", "metric": "x^2+x activations/s (server rounds 1+2)", "value": value,
+        "unit": "activations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"x^2+x layers of ResNet-18 CIFAR, B={X2X_B}", "ciphertexts": n, "activations": acts,
+                   "N": wl.N, "L": wl.L, "t": T_PLAIN},
+        "cpu_baseline": {"value": value, "unit": "activations/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: " + desc},
+        "e2e": {"value": value, "unit": "activations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
     return 0
 
@@ -405,6 +471,134 @@ def run_gpu(args, wl, rank, world, local_rank):
     return 0
 
 
+def run_x2x(args, rank, world, local_rank):
+    """Server rounds 1 and 2 of the x^2 + x protocol over every activation
+    ciphertext of ResNet-18 CIFAR, B=16 (N=8192, L=3).  The offline step (r, v
+    and their encodings) is untimed, as in Sec. 6.2."""
+    import torch
+
+    from paper_2401_16732_gb300 import flashgpu
+    from paper_2401_16732_gb300.dist import max_over_ranks, whole_job_rate
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl, shapes = x2x_shapes()
+    N, L, B = wl.N, wl.L, X2X_B
+    ctx = flashgpu.Context(N, L, T_PLAIN)
+    geoms = [ctx.geom(*sh) for sh in shapes]
+    n = B * sum(g.n_in for g in geoms)
+    acts = B * sum(sh[0] * sh[2] * sh[3] for sh in shapes)
+    seed = args.seed + 1000 * rank
+    stream = torch.cuda.Stream(device=dev)
+    prep = ctx.x2x_prepare(synth.device_masks(seed, (n, N), T_PLAIN, 1, device=dev),
+                           synth.device_masks(seed, (n, N), T_PLAIN, 2, device=dev))
+    ct_z, ct_x, ct_y = (synth.device_uniform_residues(seed, ctx.primes, (n, 2, L, N), k, device=dev)
+                        for k in (3, 4, 5))
+    out1, out2 = torch.empty_like(ct_z), torch.empty_like(ct_z)
+    torch.cuda.synchronize()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        ctx.x2x_round1(prep, ct_z, out1, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        ctx.x2x_round2(prep, ct_x, ct_y, out2, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    t1.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = max_over_ranks(t0.elapsed_time(t1), dev)
+    k1 = k2 = 0.0
+    nrep = max(1, min(args.steps, 5))
+    for _ in range(nrep):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(2_000_000)
+        step(evs)
+        stream.synchronize()
+        k1 += evs[0].elapsed_time(evs[1]) / nrep
+        k2 += evs[1].elapsed_time(evs[2]) / nrep
+
+    e2e = None
+    if not args.skip_e2e:
+        # client -> server: <z> (batch), <X>, <Y>; server -> client: round 1's <2rz + v>
+        h_in = [torch.empty(ct_z.numel(), dtype=torch.int32, pin_memory=True) for _ in range(3)]
+        for h, d in zip(h_in, (ct_z, ct_x, ct_y)):
+            h.copy_(d.view(-1).cpu())
+        h_out = torch.empty(ct_z.numel(), dtype=torch.int32, pin_memory=True)
+        n_e2e = max(1, min(args.steps, 5))
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for h, d in zip(h_in, (ct_z, ct_x, ct_y)):
+                    d.view(-1).copy_(h, non_blocking=True)
+            step()
+            with torch.cuda.stream(stream):
+                h_out.copy_(out1.view(-1), non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        ts = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        rate, _ = whole_job_rate(acts * n_e2e, time.perf_counter() - ts, dev)
+        e2e = {"value": rate, "unit": "activations/s", "h2d_bytes_per_step": 3 * ct_z.numel() * 4,
+               "d2h_bytes_per_step": out1.numel() * 4, "steps": n_e2e}
+    clocks.stop()
+    if rank != 0:
+        return 0
+    hbm, peak_kind = peaks()
+    logn = N.bit_length() - 1
+    bfly1 = n * L * 4 * (N // 2) * logn  # two forward and two inverse NTTs per (ciphertext, limb)
+    bytes1 = n * (5 * L + 1) * N * 4     # <z>, NTT(2r), encode(v) in; result out
+    bytes2 = n * (6 * L + 1) * N * 4     # <X>, <Y>, r^2 - r + v in; result out
+    alu1 = bfly1 / (k1 * 1e-3)
+    hbm1, hbm2 = bytes1 / (k1 * 1e-3) / 1e9, bytes2 / (k2 * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": alu1 / 1e12, "peak": ALU_BFLY_PEAK / 1e12, "unit": "T butterflies/s",
+            "frac": alu1 / ALU_BFLY_PEAK,
+            "peak_source": "derived: 152 SMs x 4 x 16 ALU lanes x 2.07 GHz / 4 ALU ops per butterfly",
+            "traffic": None, "kernel": "k_x2x_round1: forward NTT x2, NTT-domain PMult, inverse NTT x2, + encode(v)",
+            "kernel_ms_per_step": k1, "algorithmic_butterflies_per_step": bfly1,
+            "hbm_view": {"achieved": hbm1, "peak": hbm, "frac": hbm1 / hbm, "algorithmic_bytes_per_step": bytes1},
+            "other_kernels": [{"kernel": "k_x2x_round2: <X> - <Y> + Delta*(r^2 - r + v)", "bound": "hbm",
+                               "kernel_ms_per_step": k2, "achieved": hbm2, "peak": hbm, "unit": "GB/s",
+                               "frac": hbm2 / hbm, "peak_source": peak_kind, "algorithmic_bytes_per_step": bytes2}]}
+    line = {
+        "metric": "x^2+x activations/s (server rounds 1+2)", "value": world * acts * args.steps / (ms * 1e-3),
+        "unit": "activations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"x^2+x layers of ResNet-18 CIFAR, B={B}", "ciphertexts": n, "activations": acts,
+                   "N": N, "L": L, "t": T_PLAIN,
+                   "l2": f"no flush: {(bytes1 + bytes2) / 1e9:.2f} GB per step > {L2_BYTES / 1e6:.0f} MB L2"},
+        "gpu_launches": 2 * args.steps, "roofline": roof, "clocks": clocks.summary(),
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if world == 1 and not args.skip_cpu:
+        sec, desc = x2x_sample(args.seed, 10.0)
+        line["cpu_baseline"] = {"value": acts / (n * sec), "unit": "activations/s", "cores": 1, "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args, rank, world, local_rank):
     """Serving loop (continuous batching) on ResNet-18 (N=8192) and ResNet-50
     (N=16384) requests: Poisson arrivals at 200 requests/s, 70% / 30%, batch
@@ -454,7 +648,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="resnet18", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--config", default="resnet18", choices=sorted(WORKLOADS) + ["serve", "x2x"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
@@ -465,7 +659,7 @@ def main():
     if args.config == "serve":
         return run_serve(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
                          int(os.environ.get("LOCAL_RANK", "0")))
-    wl = WORKLOADS[args.config]
+    wl = WORKLOADS[args.config] if args.config != "x2x" else None
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -477,6 +671,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
+        if args.config == "x2x":
+            return run_x2x(args, rank, world, local_rank)
         return run_gpu(args, wl, rank, world, local_rank)
     finally:
         if world > 1:

@@ -264,6 +264,65 @@ int fl_he_conv2d_mask_noalloc(fl_ctx *ctx, const fl_conv_geom *geom, int B, cons
                               const uint32_t *ct_in_dev, const uint32_t *r_dev, uint32_t *ct_out_dev,
                               void *stream);
 
+/* ---- The x^2 + x activation protocol, server side (Sec. 5.2) ---- */
+
+/* After a convolution and its mask r (fl_he_conv2d_mask), the client holds
+ * z = a + r.  It returns <X> with X = z^2 + z under direct encoding and <z>
+ * under batch encoding.  Server round 1 computes <Y> = <2rz + v> (batch
+ * encoded) with a fresh mask v.  The client decrypts and decodes Y and
+ * returns it under direct encoding.  Server round 2 computes
+ * <a^2 + a> = <X> - <Y> + (r^2 - r + v), the next convolution's input.
+ *
+ * Every call here works on n ciphertexts [n][2][L][N] whose plaintexts are
+ * vectors of N values mod t.  One value sits at each coefficient (direct) or
+ * slot (batch).  r and v are vectors [n][N] in that same layout:
+ * fl_repack_outputs brings a convolution's mask into the next layer's input
+ * layout.  All of it needs t prime with t = 1 mod 2N (t = 65537 serves every
+ * supported N).  With another t each call returns FL_ERR_ARG.  Pointers are
+ * device pointers, 16-byte aligned.  Work is queued on `stream` and nothing
+ * is allocated. */
+
+/* Batch (SIMD) encoding over Z_t[x]/(x^N+1) (Sec. 2.2).  Slot k of a
+ * plaintext m holds m(psi_t^(2k+1)) mod t.  psi_t is the first
+ * g^((t-1)/2N), g = 2, 3, ..., of multiplicative order 2N.  encode:
+ * slots_dev [n][N] (each reduced mod t) -> m_dev [n][N] in [0, t).
+ * decode: m_dev [n][N] with values in [0, t) -> slots_dev [n][N]. */
+int fl_batch_encode(fl_ctx *ctx, int n, const uint32_t *slots_dev, uint32_t *m_dev, void *stream);
+int fl_batch_decode(fl_ctx *ctx, int n, const uint32_t *m_dev, uint32_t *slots_dev, void *stream);
+
+/* Offline step: r_dev, v_dev [n][N] (reduced mod t) -> prep_dev, which
+ * holds fl_x2x_prep_bytes(ctx, n) bytes laid out [n][L+2][N].  Rows
+ * [0, L) hold NTT_l of the batch encoding of 2r, lifted to (-t/2, t/2] mod
+ * q_l.  Row L holds the batch encoding of v in [0, t).  Row L+1 holds
+ * r^2 - r + v mod t (direct encoding).  Sec. 6.2 pre-generates r, v and
+ * r^2. */
+size_t fl_x2x_prep_bytes(const fl_ctx *ctx, int n);
+int fl_x2x_prepare(fl_ctx *ctx, int n, const uint32_t *r_dev, const uint32_t *v_dev, uint32_t *prep_dev,
+                   void *stream);
+
+/* Round 1: ct_out = PMult(ct_z, encode(2r)) + encode(v), both batch
+ * encoded.  PMult is defined in Sec. 2.2.  ct_z_dev is the client's <z>
+ * [n][2][L][N].  ct_out_dev may equal ct_z_dev (in place) and must not
+ * overlap prep_dev. */
+int fl_x2x_round1(fl_ctx *ctx, int n, const uint32_t *prep_dev, const uint32_t *ct_z_dev, uint32_t *ct_out_dev,
+                  void *stream);
+
+/* Round 2: ct_out = ct_x - ct_y + Delta*(r^2 - r + v) in R_q.  These are the
+ * direct-encoded <X> and <Y> [n][2][L][N].  ct_out_dev may equal either
+ * input and must not overlap prep_dev. */
+int fl_x2x_round2(fl_ctx *ctx, int n, const uint32_t *prep_dev, const uint32_t *ct_x_dev, const uint32_t *ct_y_dev,
+                  uint32_t *ct_out_dev, void *stream);
+
+/* Plain-vector re-layout (server side, for its own masks).  src_dev
+ * [B][prev->n_out][N] is laid out as prev's outputs: output (j, y, x) of
+ * image b sits at coefficient (s*(y % Rout))*Wp + s*x of polynomial
+ * j*bands + y/Rout.  dst_dev [B][next->n_in][N] gets the same values as
+ * next's zero-padded packed inputs (fl_encrypt's packing), with 0 at padding
+ * and unused coefficients.  prev->Cout, Ho, Wo and N must equal next->Cin,
+ * H, W and N (FL_ERR_SHAPE otherwise).  The buffers must not overlap. */
+int fl_repack_outputs(const fl_conv_geom *prev, const fl_conv_geom *next, int B, const uint32_t *src_dev,
+                      uint32_t *dst_dev, void *stream);
+
 /* ---- Building blocks, exposed for tests ---- */
 
 /* In-place negacyclic NTT / inverse NTT of n RNS polynomials data_dev

@@ -33,6 +33,11 @@ struct fl_ctx {
   CtxConst cc;
   DecConst dc;
   uint32_t* tw;  // device twiddle tables, twiddle_limb_words(logN) words per limb
+  // batch encoding over Z_t[x]/(x^N+1), present when t is prime and t = 1 mod 2N:
+  // the tables of t follow the L limbs' tables in `tw`
+  int batch;
+  uint32_t psi_t;
+  fl::LimbConst tc;
 };
 
 namespace {
@@ -95,6 +100,57 @@ uint32_t brev(uint32_t x, int bits) {
 }
 
 uint32_t shoup(uint32_t w, uint32_t q) { return (uint32_t)(((uint64_t)w << 32) / q); }
+
+// Twiddle tables (fl::TwLayout) and constants of one NTT modulus q, prime
+// with q = 1 mod 2N: an RNS limb of the ciphertext modulus, or the plaintext
+// modulus t for batch encoding.  Delta fields are left to the caller.
+void build_tables(uint32_t q, int N, int logN, uint32_t* Tw, fl::LimbConst& lc, uint32_t* psi_out) {
+  const uint64_t step = 2ull * N;
+  // psi: first g^((q-1)/2N), g = 2, 3, ..., with psi^N = -1 (order 2N)
+  uint32_t psi = 0;
+  for (uint64_t g = 2; g < q && !psi; ++g) {
+    uint64_t cand = powmod(g, (q - 1) / step, q);
+    if (powmod(cand, N, q) == q - 1) psi = (uint32_t)cand;
+  }
+  const uint32_t psi_inv = (uint32_t)powmod(psi, q - 2, q);
+  *psi_out = psi;
+  uint2* pairs = reinterpret_cast<uint2*>(Tw);
+  std::vector<uint32_t> fw(N), iv(N);
+  for (int i = 0; i < N; ++i) {
+    fw[i] = (uint32_t)powmod(psi, brev(i, logN), q);
+    iv[i] = (uint32_t)powmod(psi_inv, brev(i, logN), q);
+    pairs[fl::TW_FWD * N + i] = make_uint2(fw[i], shoup(fw[i], q));
+    pairs[fl::TW_INV * N + i] = make_uint2(iv[i], shoup(iv[i], q));
+  }
+  // thread-major twiddles of the radix-32 pass over stages [logN-5, logN):
+  // thread blk consumes, for stage S0+d (ascending forward, descending
+  // inverse), twiddles (1 << (S0+d)) + blk*2^d + m for m < 2^d.
+  const int Tn = N / 32, S0 = logN - 5;
+  uint32_t* grouped = Tw + 4 * N;
+  for (int dir = 0; dir < 2; ++dir) {
+    const std::vector<uint32_t>& tab = dir == fl::TW_FWD ? fw : iv;
+    for (int blk = 0; blk < Tn; ++blk) {
+      int slot = 0;
+      for (int dd = 0; dd < 5; ++dd) {
+        const int d = dir == fl::TW_INV ? 4 - dd : dd;
+        for (int m = 0; m < (1 << d); ++m, ++slot) {
+          const uint32_t w = tab[(1 << (S0 + d)) + (blk << d) + m];
+          uint32_t* e = grouped + (((size_t)dir * 16 + slot / 2) * Tn + blk) * 4 + (slot & 1) * 2;
+          e[0] = w;
+          e[1] = shoup(w, q);
+        }
+      }
+    }
+  }
+  memset(&lc, 0, sizeof lc);
+  lc.q = q;
+  lc.two_q = 2 * q;
+  lc.n_inv = (uint32_t)powmod(N, q - 2, q);
+  lc.n_inv_sh = shoup(lc.n_inv, q);
+  lc.last_w = (uint32_t)mulmod(iv[1], lc.n_inv, q);
+  lc.last_w_sh = shoup(lc.last_w, q);
+  lc.mu = ~0ull / q;
+}
 
 GeomDims dims_of(const fl_conv_geom& g) {
   GeomDims d;
@@ -227,7 +283,8 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
   for (uint32_t q : qs) Q *= q;
   const u128 Delta = Q / t;
   const size_t limb_words = fl::twiddle_limb_words(logN);
-  std::vector<uint32_t> host((size_t)L * limb_words);
+  const bool batch = is_prime32(t) && (t - 1) % (2ull * N) == 0;
+  std::vector<uint32_t> host((size_t)(L + (batch ? 1 : 0)) * limb_words);
   memset(&c->cc, 0, sizeof c->cc);
   memset(&c->dc, 0, sizeof c->dc);
   c->cc.L = L; c->cc.t = t;
@@ -235,65 +292,26 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
   c->dc.qhi = (uint64_t)(Q >> 64); c->dc.qlo = (uint64_t)Q;
   for (int l = 0; l < L; ++l) {
     const uint32_t q = qs[l];
-    // psi: first g^((q-1)/2N), g = 2, 3, ..., with psi^N = -1 (order 2N)
-    uint32_t psi = 0;
-    for (uint64_t g = 2; g < q && !psi; ++g) {
-      uint64_t cand = powmod(g, (q - 1) / step, q);
-      if (powmod(cand, N, q) == q - 1) psi = (uint32_t)cand;
-    }
-    const uint32_t psi_inv = (uint32_t)powmod(psi, q - 2, q);
-    c->psi[l] = psi;
-    uint32_t* Tw = host.data() + (size_t)l * limb_words;
-    uint2* pairs = reinterpret_cast<uint2*>(Tw);
-    std::vector<uint32_t> fw(N), iv(N);
-    for (int i = 0; i < N; ++i) {
-      fw[i] = (uint32_t)powmod(psi, brev(i, logN), q);
-      iv[i] = (uint32_t)powmod(psi_inv, brev(i, logN), q);
-      pairs[fl::TW_FWD * N + i] = make_uint2(fw[i], shoup(fw[i], q));
-      pairs[fl::TW_INV * N + i] = make_uint2(iv[i], shoup(iv[i], q));
-    }
-    // thread-major twiddles of the radix-32 pass over stages [logN-5, logN):
-    // thread blk consumes, for stage S0+d (ascending forward, descending
-    // inverse), twiddles (1 << (S0+d)) + blk*2^d + m for m < 2^d.
-    const int Tn = N / 32, S0 = logN - 5;
-    uint32_t* grouped = Tw + 4 * N;
-    for (int dir = 0; dir < 2; ++dir) {
-      const std::vector<uint32_t>& tab = dir == fl::TW_FWD ? fw : iv;
-      for (int blk = 0; blk < Tn; ++blk) {
-        int slot = 0;
-        for (int dd = 0; dd < 5; ++dd) {
-          const int d = dir == fl::TW_INV ? 4 - dd : dd;
-          for (int m = 0; m < (1 << d); ++m, ++slot) {
-            const uint32_t w = tab[(1 << (S0 + d)) + (blk << d) + m];
-            uint32_t* e = grouped + (((size_t)dir * 16 + slot / 2) * Tn + blk) * 4 + (slot & 1) * 2;
-            e[0] = w;
-            e[1] = shoup(w, q);
-          }
-        }
-      }
-    }
+    build_tables(q, N, logN, host.data() + (size_t)l * limb_words, c->cc.limb[l], &c->psi[l]);
     fl::LimbConst& lc = c->cc.limb[l];
-    lc.q = q;
-    lc.two_q = 2 * q;
-    lc.n_inv = (uint32_t)powmod(N, q - 2, q);
-    lc.n_inv_sh = shoup(lc.n_inv, q);
-    lc.last_w = (uint32_t)mulmod(iv[1], lc.n_inv, q);
-    lc.last_w_sh = shoup(lc.last_w, q);
     lc.delta = (uint32_t)(Delta % q);
     lc.delta_sh = shoup(lc.delta, q);
-    lc.mu = ~0ull / q;
     const u128 Ql = Q / q;
     c->dc.q[l] = q;
     c->dc.inv[l] = (uint32_t)powmod((uint64_t)(Ql % q), q - 2, q);
     c->dc.Qhi[l] = (uint64_t)(Ql >> 64);
     c->dc.Qlo[l] = (uint64_t)Ql;
   }
+  if (batch) {
+    build_tables(t, N, logN, host.data() + (size_t)L * limb_words, c->tc, &c->psi_t);
+    c->batch = 1;
+  }
   if ((e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess) {
     delete c;
     return cuda_fail(e, "SM count");
   }
   if ((e = fl::launch_setup(logN)) != cudaSuccess || (e = fl::launch_stack_setup(logN)) != cudaSuccess ||
-      (e = fl::launch_ntt_multi_setup(logN)) != cudaSuccess) {
+      (e = fl::launch_ntt_multi_setup(logN)) != cudaSuccess || (e = fl::launch_act_setup(logN)) != cudaSuccess) {
     delete c;
     return cuda_fail(e, "kernel set-up");
   }
@@ -693,6 +711,119 @@ int fl_ntt_inverse(fl_ctx* ctx, int n, uint32_t* data_dev, void* stream) {
   if ((rc = check_ptrs({data_dev}))) return rc;
   return launched(fl::launch_ntt_inv(ctx->logN, n * ctx->L, data_dev, ctx->tw, ctx->cc, (cudaStream_t)stream),
                   "intt");
+}
+
+// ---------------------------------------------------------------------------
+// Batch encoding and the x^2 + x protocol, server side (Sec. 5.2)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+int check_batch(const fl_ctx* ctx) {
+  if (!ctx->batch)
+    return fail(FL_ERR_ARG, "batch encoding needs t prime with t = 1 mod 2N (t=%u, N=%d)", ctx->t, ctx->N);
+  return FL_OK;
+}
+const uint32_t* tw_t(const fl_ctx* ctx) { return ctx->tw + (size_t)ctx->L * fl::twiddle_limb_words(ctx->logN); }
+}  // namespace
+
+extern "C" {
+
+int fl_batch_encode(fl_ctx* ctx, int n, const uint32_t* slots_dev, uint32_t* m_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_batch(ctx))) return rc;
+  if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
+  if (n == 0) return FL_OK;
+  if ((rc = check_ptrs({slots_dev, m_dev}))) return rc;
+  return launched(fl::launch_batch_encode(ctx->logN, n, slots_dev, 1, m_dev, ctx->N, 0, tw_t(ctx), ctx->tc, ctx->cc,
+                                          (cudaStream_t)stream),
+                  "batch encode");
+}
+
+int fl_batch_decode(fl_ctx* ctx, int n, const uint32_t* m_dev, uint32_t* slots_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_batch(ctx))) return rc;
+  if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
+  if (n == 0) return FL_OK;
+  if ((rc = check_ptrs({slots_dev, m_dev}))) return rc;
+  return launched(fl::launch_batch_decode(ctx->logN, n, m_dev, slots_dev, tw_t(ctx), ctx->tc, (cudaStream_t)stream),
+                  "batch decode");
+}
+
+size_t fl_x2x_prep_bytes(const fl_ctx* ctx, int n) {
+  if (!ctx || n < 0) return 0;
+  return (size_t)n * (ctx->L + 2) * ctx->N * sizeof(uint32_t);
+}
+
+int fl_x2x_prepare(fl_ctx* ctx, int n, const uint32_t* r_dev, const uint32_t* v_dev, uint32_t* prep_dev,
+                   void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_batch(ctx))) return rc;
+  if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
+  if (n == 0) return FL_OK;
+  if ((rc = check_ptrs({r_dev, v_dev, prep_dev}))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = ctx->L, N = ctx->N;
+  const long long stride = (long long)(L + 2) * N;
+  cudaError_t e;
+  // rows [0, L): lift of encode(2r) per limb, then NTT in place
+  if ((e = fl::launch_batch_encode(ctx->logN, n, r_dev, 2, prep_dev, stride, L, tw_t(ctx), ctx->tc, ctx->cc, st)))
+    return cuda_fail(e, "encode 2r");
+  if ((e = fl::launch_ntt_fwd(ctx->logN, n * L, prep_dev, L, L + 2, prep_dev, L, L + 2, 1, ctx->tw, ctx->cc, st)))
+    return cuda_fail(e, "ntt of 2r");
+  // row L: encode(v) in [0, t); row L+1: r^2 - r + v mod t (direct encoding)
+  if ((e = fl::launch_batch_encode(ctx->logN, n, v_dev, 1, prep_dev + (size_t)L * N, stride, 0, tw_t(ctx), ctx->tc,
+                                   ctx->cc, st)))
+    return cuda_fail(e, "encode v");
+  return launched(fl::launch_x2x_const(r_dev, v_dev, prep_dev + (size_t)(L + 1) * N, stride, n, N, ctx->tc, st),
+                  "r^2 - r + v");
+}
+
+int fl_x2x_round1(fl_ctx* ctx, int n, const uint32_t* prep_dev, const uint32_t* ct_z_dev, uint32_t* ct_out_dev,
+                  void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_batch(ctx))) return rc;
+  if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
+  if (n == 0) return FL_OK;
+  if ((rc = check_ptrs({prep_dev, ct_z_dev, ct_out_dev}))) return rc;
+  return launched(fl::launch_x2x_round1(ctx->logN, n, prep_dev, ct_z_dev, ct_out_dev, ctx->tw, ctx->cc,
+                                        (cudaStream_t)stream),
+                  "x2x round 1");
+}
+
+int fl_x2x_round2(fl_ctx* ctx, int n, const uint32_t* prep_dev, const uint32_t* ct_x_dev, const uint32_t* ct_y_dev,
+                  uint32_t* ct_out_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_batch(ctx))) return rc;
+  if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
+  if (n == 0) return FL_OK;
+  if ((rc = check_ptrs({prep_dev, ct_x_dev, ct_y_dev, ct_out_dev}))) return rc;
+  return launched(fl::launch_x2x_round2(prep_dev, ct_x_dev, ct_y_dev, ct_out_dev, n, ctx->N, ctx->cc,
+                                        (cudaStream_t)stream),
+                  "x2x round 2");
+}
+
+int fl_repack_outputs(const fl_conv_geom* prev, const fl_conv_geom* next, int B, const uint32_t* src_dev,
+                      uint32_t* dst_dev, void* stream) {
+  if (!prev || !next) return fail(FL_ERR_ARG, "null geometry");
+  fl_conv_geom a, b;
+  int rc;
+  if ((rc = fl_conv_geom_make(prev->N, prev->Cin, prev->Cout, prev->H, prev->W, prev->k, prev->stride, prev->pad,
+                              &a)) ||
+      (rc = fl_conv_geom_make(next->N, next->Cin, next->Cout, next->H, next->W, next->k, next->stride, next->pad,
+                              &b)))
+    return rc;
+  if (memcmp(&a, prev, sizeof a) || memcmp(&b, next, sizeof b))
+    return fail(FL_ERR_SHAPE, "geometry fields are inconsistent (build them with fl_conv_geom_make)");
+  if (prev->N != next->N || prev->Cout != next->Cin || prev->Ho != next->H || prev->Wo != next->W)
+    return fail(FL_ERR_SHAPE, "layer outputs %dx%dx%d (N=%d) do not match next inputs %dx%dx%d (N=%d)", prev->Cout,
+                prev->Ho, prev->Wo, prev->N, next->Cin, next->H, next->W, next->N);
+  if (B < 0) return fail(FL_ERR_ARG, "B=%d", B);
+  if (B == 0) return FL_OK;
+  if ((rc = check_ptrs({src_dev, dst_dev}))) return rc;
+  return launched(fl::launch_repack(src_dev, dst_dev, dims_of(*prev), dims_of(*next), B, next->N,
+                                    (cudaStream_t)stream),
+                  "repack");
 }
 
 }  // extern "C"

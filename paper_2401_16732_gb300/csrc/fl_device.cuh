@@ -97,6 +97,13 @@ template <> struct Plan<12> { static constexpr int R1 = 4, R2 = 3; };
 template <> struct Plan<13> { static constexpr int R1 = 4, R2 = 4; };
 template <> struct Plan<14> { static constexpr int R1 = 5, R2 = 4; };
 
+// Resident CTAs per SM the register budget (64 per thread) is sized for:
+// 1024 threads per SM.  Kernels on two polynomials run 2 * N/32 threads (one
+// group per ciphertext component) on two padded polynomials of shared memory,
+// so at N = 8192 two CTAs fit with about 90 KiB of L1 left for the twiddles.
+template <int LOGN> constexpr int minb_two_polys() { return (512 >> (LOGN - 5)) > 0 ? (512 >> (LOGN - 5)) : 1; }
+template <int LOGN> constexpr int minb_one_poly() { return 1024 >> (LOGN - 5); }
+
 template <int LOGN> struct Geo {
   static constexpr int N = 1 << LOGN;
   static constexpr int T = N / 32;                 // threads per polynomial

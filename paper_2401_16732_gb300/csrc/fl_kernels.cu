@@ -18,12 +18,6 @@
 
 namespace fl {
 
-// Resident CTAs per SM the register budget (64 per thread) is sized for:
-// 1024 threads per SM.  The fused kernel runs 2 * N/32 threads (one group per
-// output component) on two padded polynomials of shared memory, so at
-// N = 8192 two CTAs fit with about 90 KiB of L1 left for the twiddles.
-template <int LOGN> constexpr int minb_two_polys() { return (512 >> (LOGN - 5)) > 0 ? (512 >> (LOGN - 5)) : 1; }
-template <int LOGN> constexpr int minb_one_poly() { return 1024 >> (LOGN - 5); }
 
 // --------------------------------------------------------------------------
 // Forward NTT: one CTA per polynomial row.  Row r of the source starts at

@@ -83,4 +83,20 @@ cudaError_t launch_w_scatter(const int8_t* w, uint32_t* w_hat, const GeomDims& g
 cudaError_t launch_sk_expand(const int8_t* s, uint32_t* out, int N, const CtxConst& cc,
                              cudaStream_t st);
 
+// x^2 + x protocol and batch encoding (fl_act.cu)
+cudaError_t launch_act_setup(int logn);
+cudaError_t launch_batch_decode(int logn, int n, const uint32_t* m, uint32_t* slots, const uint32_t* tw_t,
+                                const LimbConst& tc, cudaStream_t st);
+cudaError_t launch_batch_encode(int logn, int n, const uint32_t* slots, uint32_t scale, uint32_t* dst,
+                                long long dst_stride, int lift_L, const uint32_t* tw_t, const LimbConst& tc,
+                                const CtxConst& cc, cudaStream_t st);
+cudaError_t launch_x2x_const(const uint32_t* r, const uint32_t* v, uint32_t* dst, long long dst_stride, int n, int N,
+                             const LimbConst& tc, cudaStream_t st);
+cudaError_t launch_x2x_round1(int logn, int n, const uint32_t* prep, const uint32_t* ct, uint32_t* out,
+                              const uint32_t* tw, const CtxConst& cc, cudaStream_t st);
+cudaError_t launch_x2x_round2(const uint32_t* prep, const uint32_t* X, const uint32_t* Y, uint32_t* out, int n,
+                              int N, const CtxConst& cc, cudaStream_t st);
+cudaError_t launch_repack(const uint32_t* src, uint32_t* dst, const GeomDims& pv, const GeomDims& nx, int B, int N,
+                          cudaStream_t st);
+
 }  // namespace fl

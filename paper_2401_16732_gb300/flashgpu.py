@@ -73,6 +73,13 @@ _SIGS = {
     "fl_he_conv2d_mask_noalloc": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "fl_ctx_set_stack_kernel": ([_vp, _i], _i),
     "fl_ctx_get_stack_kernel": ([_vp], _i),
+    "fl_batch_encode": ([_vp, _i, _vp, _vp, _vp], _i),
+    "fl_batch_decode": ([_vp, _i, _vp, _vp, _vp], _i),
+    "fl_x2x_prep_bytes": ([_vp, _i], _sz),
+    "fl_x2x_prepare": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
+    "fl_x2x_round1": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
+    "fl_x2x_round2": ([_vp, _i, _vp, _vp, _vp, _vp, _vp], _i),
+    "fl_repack_outputs": ([_gp, _gp, _i, _vp, _vp, _vp], _i),
     "fl_ntt_forward": ([_vp, _i, _vp, _vp], _i),
     "fl_ntt_inverse": ([_vp, _i, _vp, _vp], _i),
 }
@@ -122,6 +129,17 @@ def _dev_u32(t: torch.Tensor, shape, name):
     if tuple(t.shape) != tuple(shape):
         raise FlashError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
     return t
+
+
+def repack_outputs(prev: ConvGeom, nxt: ConvGeom, src, out=None, stream=None) -> torch.Tensor:
+    """Plain vectors [B][prev.n_out][N] in prev's output layout -> [B][nxt.n_in][N]
+    in nxt's zero-padded input layout."""
+    B = src.shape[0]
+    _dev_u32(src, (B, prev.n_out, prev.N), "src")
+    if out is None:
+        out = torch.empty((B, nxt.n_in, nxt.N), dtype=src.dtype, device=src.device)
+    _check(_lib.fl_repack_outputs(ctypes.byref(prev), ctypes.byref(nxt), B, _ptr(src), _ptr(out), _stream(stream)))
+    return out
 
 
 class Context:
@@ -285,6 +303,51 @@ class Context:
         n = ct.numel() // (2 * self.L * self.N)
         _check(_lib.fl_mask_to_share(self.h, n, _ptr(ct), _ptr(r), _stream(stream)))
         return ct
+
+    # -- x^2 + x protocol, server side (Sec. 5.2) and batch encoding ---------
+    def _n_vec(self, t, name):
+        if t.numel() % self.N:
+            raise FlashError(f"{name}: size {t.numel()} is not a multiple of N={self.N}")
+        return _dev_u32(t, t.shape, name).numel() // self.N
+
+    def batch_encode(self, slots, out=None, stream=None) -> torch.Tensor:
+        """slots [..., N] -> plaintext polynomials [..., N] in [0, t)."""
+        n = self._n_vec(slots, "slots")
+        out = torch.empty_like(slots) if out is None else out
+        _check(_lib.fl_batch_encode(self.h, n, _ptr(slots), _ptr(out), _stream(stream)))
+        return out
+
+    def batch_decode(self, m, out=None, stream=None) -> torch.Tensor:
+        """plaintext polynomials [..., N] (values in [0, t)) -> slots [..., N]."""
+        n = self._n_vec(m, "m")
+        out = torch.empty_like(m) if out is None else out
+        _check(_lib.fl_batch_decode(self.h, n, _ptr(m), _ptr(out), _stream(stream)))
+        return out
+
+    def x2x_prepare(self, r, v, out=None, stream=None) -> torch.Tensor:
+        """Offline step: masks r, v [..., N] -> prep [n][L+2][N]."""
+        n = self._n_vec(r, "r")
+        _dev_u32(v, r.shape, "v")
+        out = self._new(n, self.L + 2, self.N) if out is None else _dev_u32(out, (n, self.L + 2, self.N), "prep")
+        _check(_lib.fl_x2x_prepare(self.h, n, _ptr(r), _ptr(v), _ptr(out), _stream(stream)))
+        return out
+
+    def x2x_round1(self, prep, ct_z, out=None, stream=None) -> torch.Tensor:
+        """<2rz + v> (batch encoded) from <z> (batch encoded) [n][2][L][N]."""
+        n = prep.shape[0]
+        _dev_u32(ct_z, (n, 2, self.L, self.N), "ct_z")
+        out = self._new(n, 2, self.L, self.N) if out is None else out
+        _check(_lib.fl_x2x_round1(self.h, n, _ptr(prep), _ptr(ct_z), _ptr(out), _stream(stream)))
+        return out
+
+    def x2x_round2(self, prep, ct_x, ct_y, out=None, stream=None) -> torch.Tensor:
+        """<a^2 + a> = <X> - <Y> + (r^2 - r + v), direct encoded [n][2][L][N]."""
+        n = prep.shape[0]
+        _dev_u32(ct_x, (n, 2, self.L, self.N), "ct_x")
+        _dev_u32(ct_y, (n, 2, self.L, self.N), "ct_y")
+        out = self._new(n, 2, self.L, self.N) if out is None else out
+        _check(_lib.fl_x2x_round2(self.h, n, _ptr(prep), _ptr(ct_x), _ptr(ct_y), _ptr(out), _stream(stream)))
+        return out
 
     def ntt_forward(self, data, stream=None):
         _check(_lib.fl_ntt_forward(self.h, data.numel() // (self.L * self.N), _ptr(data), _stream(stream)))
