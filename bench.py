@@ -38,7 +38,7 @@ L2_BYTES = 129e6
 ALU_BFLY_PEAK = 152 * 4 * 16 * 2.07e9 / 4
 # DRAM bytes (read + write) of one step's launches of the dominant kernel, from
 # one ncu capture of the same command (profiles/); a kernel change voids them.
-TRAFFIC = {("resnet18", "per_layer"): 2.660e9}
+TRAFFIC = {("resnet18", "per_layer"): 2.660e9, ("x2x", "round1"): 1.032e9, ("x2x", "round2"): 1.071e9}
 
 
 def peaks():
@@ -474,7 +474,7 @@ def run_gpu(args, wl, rank, world, local_rank):
 def run_x2x(args, rank, world, local_rank):
     """Server rounds 1 and 2 of the x^2 + x protocol over every activation
     ciphertext of ResNet-18 CIFAR, B=16 (N=8192, L=3).  The offline step (r, v
-    and their encodings) is untimed, as in Sec. 6.2."""
+    and their encodings) is untimed, as in Sec. 6.3."""
     import torch
 
     from paper_2401_16732_gb300 import flashgpu
@@ -573,12 +573,14 @@ def run_x2x(args, rank, world, local_rank):
     roof = {"bound": "alu", "achieved": alu1 / 1e12, "peak": ALU_BFLY_PEAK / 1e12, "unit": "T butterflies/s",
             "frac": alu1 / ALU_BFLY_PEAK,
             "peak_source": "derived: 152 SMs x 4 x 16 ALU lanes x 2.07 GHz / 4 ALU ops per butterfly",
-            "traffic": None, "kernel": "k_x2x_round1: forward NTT x2, NTT-domain PMult, inverse NTT x2, + encode(v)",
+            "traffic": TRAFFIC.get(("x2x", "round1")),
+            "kernel": "k_x2x_round1: forward NTT x2, NTT-domain PMult, inverse NTT x2, + encode(v)",
             "kernel_ms_per_step": k1, "algorithmic_butterflies_per_step": bfly1,
             "hbm_view": {"achieved": hbm1, "peak": hbm, "frac": hbm1 / hbm, "algorithmic_bytes_per_step": bytes1},
             "other_kernels": [{"kernel": "k_x2x_round2: <X> - <Y> + Delta*(r^2 - r + v)", "bound": "hbm",
                                "kernel_ms_per_step": k2, "achieved": hbm2, "peak": hbm, "unit": "GB/s",
-                               "frac": hbm2 / hbm, "peak_source": peak_kind, "algorithmic_bytes_per_step": bytes2}]}
+                               "frac": hbm2 / hbm, "peak_source": peak_kind, "algorithmic_bytes_per_step": bytes2,
+                               "traffic": TRAFFIC.get(("x2x", "round2"))}]}
     line = {
         "metric": "x^2+x activations/s (server rounds 1+2)", "value": world * acts * args.steps / (ms * 1e-3),
         "unit": "activations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

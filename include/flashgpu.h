@@ -294,7 +294,7 @@ int fl_batch_decode(fl_ctx *ctx, int n, const uint32_t *m_dev, uint32_t *slots_d
  * holds fl_x2x_prep_bytes(ctx, n) bytes laid out [n][L+2][N].  Rows
  * [0, L) hold NTT_l of the batch encoding of 2r, lifted to (-t/2, t/2] mod
  * q_l.  Row L holds the batch encoding of v in [0, t).  Row L+1 holds
- * r^2 - r + v mod t (direct encoding).  Sec. 6.2 pre-generates r, v and
+ * r^2 - r + v mod t (direct encoding).  Sec. 6.3 pre-generates r, v and
  * r^2. */
 size_t fl_x2x_prep_bytes(const fl_ctx *ctx, int n);
 int fl_x2x_prepare(fl_ctx *ctx, int n, const uint32_t *r_dev, const uint32_t *v_dev, uint32_t *prep_dev,

@@ -11,7 +11,7 @@
 // Protocol, with z = a + r the client's masked activations (one vector of N
 // values per ciphertext), X = z^2 + z and Y = 2rz + v:
 //   offline   prep rows: NTT(lift(encode(2r))) per limb, encode(v), and the
-//             direct-encoded constant r^2 - r + v (Sec. 6.2 keeps r, v and
+//             direct-encoded constant r^2 - r + v (Sec. 6.3 keeps r, v and
 //             r^2 precomputed)
 //   round 1   <2rz + v>_batch = PMult(<z>_batch, encode(2r)) + encode(v)
 //   round 2   <a^2 + a>      = <X> - <Y> + (r^2 - r + v), direct encoding
