@@ -36,6 +36,9 @@ L2_BYTES = 129e6
 # subtract as add + min, difference) and 3 multiplies; the ALU pipe retires 16
 # lanes per clock per SM sub-partition.  152 SMs x 4 x 16 x 2.07 GHz / 4.
 ALU_BFLY_PEAK = 152 * 4 * 16 * 2.07e9 / 4
+# Direct form: one signed 32x32->64-bit multiply-add per lane per clock on the
+# 16-lane integer multiply pipe (an upper bound).
+DIRECT_MAC_PEAK = 152 * 4 * 16 * 2.07e9
 # DRAM bytes (read + write) of one step's launches of the dominant kernel, from
 # one ncu capture of the same command (profiles/); a kernel change voids them.
 TRAFFIC = {("resnet18", "per_layer"): 2.660e9, ("x2x", "round1"): 1.032e9, ("x2x", "round2"): 1.071e9}
@@ -305,17 +308,22 @@ def run_gpu(args, wl, rank, world, local_rank):
         x = synth.activations(seed, (B, g.Cin, g.H, g.W), li)
         a = synth.device_uniform_residues(seed, ctx.primes, (B, g.n_in, L, N), li, device=dev)
         e = synth.device_cbd_noise(seed, (B, g.n_in, N), li, device=dev)
-        lay = {"g": g, "w_hat": ctx.encode_weights(g, to_dev(w, torch.int8)),
+        w_dev = to_dev(w, torch.int8)
+        lay = {"g": g, "w": w_dev, "w_hat": ctx.encode_weights(g, w_dev) if args.form == "ntt" else None,
                "ct": ctx.encrypt(sk, g, to_dev(x), a, e),
                "r": synth.device_masks(seed, (B, g.n_out, N), T_PLAIN, li, device=dev),
                "out": torch.empty((B, g.n_out, 2, L, N), dtype=torch.int32, device=dev)}
         del a, e
         layers.append(lay)
-    arr = ctx.stack_layers([{"g": lay["g"], "w_hat": lay["w_hat"], "ct_in": lay["ct"], "r": lay["r"],
-                             "out": lay["out"]} for lay in layers])
-    ws = ctx.stack_workspace(arr)
+    arr = ws = None
+    if args.form == "ntt":
+        arr = ctx.stack_layers([{"g": lay["g"], "w_hat": lay["w_hat"], "ct_in": lay["ct"], "r": lay["r"],
+                                 "out": lay["out"]} for lay in layers])
+        ws = ctx.stack_workspace(arr)
     torch.cuda.synchronize()
-    if args.stack_kernel == "auto":
+    if args.form == "direct":
+        tuned = {"kernel": "direct", "ms": None}
+    elif args.stack_kernel == "auto":
         from paper_2401_16732_gb300.autotune import tune_stack
         tuned = tune_stack(ctx, [{"g": lay["g"], "ct_in": lay["ct"], "r": lay["r"]} for lay in layers], arr, ws,
                            stream=stream, cache=None)
@@ -329,6 +337,15 @@ def run_gpu(args, wl, rank, world, local_rank):
         # persistent contraction + inverse NTT + mask kernel over all layers
         if events is not None:
             events[0].record(stream)
+        if args.form == "direct":
+            # the paper's DRot + CMult form on the GPU: one launch per layer, no NTT
+            if events is not None:
+                events[1].record(stream)
+            for lay in layers:
+                ctx.he_conv2d_direct(lay["g"], lay["w"], lay["ct"], out=lay["out"], r=lay["r"], stream=stream)
+            if events is not None:
+                events[2].record(stream)
+            return
         ctx.he_conv2d_stack(arr, ws, stream=stream, stage="ntt")
         if events is not None:
             events[1].record(stream)
@@ -343,7 +360,7 @@ def run_gpu(args, wl, rank, world, local_rank):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         step()
-    launches_per_step = 2 if tuned["kernel"] == "persistent" else 1 + len(layers)
+    launches_per_step = {"persistent": 2, "direct": len(layers)}.get(tuned["kernel"], 1 + len(layers))
 
     def barrier():
         if world > 1:
@@ -384,7 +401,7 @@ def run_gpu(args, wl, rank, world, local_rank):
         stream.synchronize()
         kern["ntt"] += evs[0].elapsed_time(evs[1]) / nrep
         kern["conv"] += evs[1].elapsed_time(evs[2]) / nrep
-    err_word = ctx.stack_error(ws, stream=stream)
+    err_word = ctx.stack_error(ws, stream=stream) if ws is not None else 0
     if err_word:
         raise RuntimeError(f"persistent kernel reported a timed-out wait (error word {err_word})")
 
@@ -450,6 +467,18 @@ def run_gpu(args, wl, rank, world, local_rank):
                  "algorithmic_butterflies_per_step": bfly, "hbm_floor_ms": hbm_floor * 1e3,
                  "alu_floor_ms": alu_floor * 1e3, "other_roofline": other,
                  "ntt_inputs_ms_per_step": kern["ntt"]})
+    if tuned["kernel"] == "direct":
+        # Cin*k^2 signed 32x32->64-bit multiply-adds per output coefficient,
+        # against one such multiply-add per lane per clock on the 16-lane
+        # integer multiply pipe of each SM sub-partition
+        dmacs = sum(B * g.n_out * 2 * L * N * g.Cin * g.k * g.k for g in geoms)
+        rate = dmacs / kern_s
+        roof = {"bound": "alu", "achieved": rate / 1e12, "peak": DIRECT_MAC_PEAK / 1e12, "unit": "T MAC/s",
+                "frac": rate / DIRECT_MAC_PEAK, "traffic": None,
+                "peak_source": "derived: 152 SMs x 4 x 16 integer-multiply lanes x 2.07 GHz, one MAC per lane-clock",
+                "kernel": "k_direct (one launch per layer): DRot + CMult, no NTT", "kernel_ms_per_step": kern["conv"],
+                "algorithmic_macs_per_step": dmacs}
+        kname = roof["kernel"]
     line = {
         "metric": "encrypted conv layers/s", "value": value, "unit": "layers/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -457,7 +486,7 @@ def run_gpu(args, wl, rank, world, local_rank):
         "config": {"workload": wl.name, "layers": len(layers), "batch": B, "N": N, "L": L, "t": T_PLAIN,
                    "l2": f"no flush: {step_bytes / 1e9:.2f} GB of algorithmic traffic per step > {L2_BYTES / 1e6:.0f} MB L2",
                    "graph": "one CUDA graph per step: input NTT of all layers + the contraction/INTT/mask kernel(s)",
-                   "stack_kernel": tuned["kernel"], "autotune_ms": tuned["ms"]},
+                   "stack_kernel": tuned["kernel"], "autotune_ms": tuned["ms"], "form": args.form},
         "slot_mac_per_s": world * macs * args.steps / (ms * 1e-3),
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,
@@ -654,6 +683,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--form", default="ntt", choices=["ntt", "direct"],
+                    help="ntt: the NTT route (default); direct: the paper's DRot + CMult form on the GPU")
     ap.add_argument("--stack-kernel", default="auto", choices=["auto", "per_layer", "persistent"],
                     help="kernel for the contraction/INTT/mask stage (auto: time both, keep the faster)")
     args = ap.parse_args()

@@ -176,6 +176,22 @@ int fl_he_conv2d_from_ntt(fl_ctx *ctx, const fl_conv_geom *geom, int B, const ui
                           const void *workspace_dev, size_t workspace_bytes, const uint32_t *r_dev,
                           uint32_t *ct_out_dev, void *stream);
 
+/* Direct form of the same convolution: Algorithm 1's DRot + CMult, where
+ * DRot by e is multiplication by x^-e (Eq. 2).  It runs on the GPU with no
+ * NTT, from the int8 filters w_dev [Cout][Cin][k][k] as they are (no encoded
+ * weights).  Products are accumulated exactly in signed 64 bits and reduced
+ * once per coefficient (lazy reduction, Sec. 6.1).  The result is
+ * bit-identical to fl_he_conv2d, plus the mask when r_dev is not NULL.  It
+ * costs Cin*k^2 multiply-adds per output coefficient, against about G for the
+ * NTT route plus the transforms.  So it only pays for layers with few taps,
+ * such as a 3-channel stem, or a single small layer.  Needs
+ * Cin*k^2 <= FL_DIRECT_MAX_TAPS (FL_ERR_SHAPE otherwise).  ct_in_dev,
+ * ct_out_dev and r_dev are 16-byte aligned.  The output must not overlap the
+ * input. */
+#define FL_DIRECT_MAX_TAPS 16384
+int fl_he_conv2d_direct(fl_ctx *ctx, const fl_conv_geom *geom, int B, const int8_t *w_dev,
+                        const uint32_t *ct_in_dev, const uint32_t *r_dev, uint32_t *ct_out_dev, void *stream);
+
 /* ---- Many layers in one launch ---- */
 
 /* One layer of a stack: its geometry (host pointer), batch size, encoded

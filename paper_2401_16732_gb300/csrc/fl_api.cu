@@ -311,7 +311,8 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
     return cuda_fail(e, "SM count");
   }
   if ((e = fl::launch_setup(logN)) != cudaSuccess || (e = fl::launch_stack_setup(logN)) != cudaSuccess ||
-      (e = fl::launch_ntt_multi_setup(logN)) != cudaSuccess || (e = fl::launch_act_setup(logN)) != cudaSuccess) {
+      (e = fl::launch_ntt_multi_setup(logN)) != cudaSuccess || (e = fl::launch_act_setup(logN)) != cudaSuccess ||
+      (e = fl::launch_direct_setup(logN)) != cudaSuccess) {
     delete c;
     return cuda_fail(e, "kernel set-up");
   }
@@ -544,6 +545,23 @@ int fl_he_conv2d_mask(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32
   if (!r_dev) return fail(FL_ERR_ARG, "null mask");
   return he_conv2d_impl(ctx, geom, B, w_hat_dev, ct_in_dev, r_dev, ct_out_dev, workspace_dev, workspace_bytes,
                         stream);
+}
+
+int fl_he_conv2d_direct(fl_ctx* ctx, const fl_conv_geom* geom, int B, const int8_t* w_dev, const uint32_t* ct_in_dev,
+                        const uint32_t* r_dev, uint32_t* ct_out_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_geom(ctx, geom))) return rc;
+  if (B < 0) return fail(FL_ERR_ARG, "B=%d", B);
+  if ((long long)geom->Cin * geom->k * geom->k > FL_DIRECT_MAX_TAPS)
+    return fail(FL_ERR_SHAPE, "Cin*k*k=%lld above %d for the direct form",
+                (long long)geom->Cin * geom->k * geom->k, FL_DIRECT_MAX_TAPS);
+  if (B == 0) return FL_OK;
+  if (!w_dev) return fail(FL_ERR_ARG, "null filters");
+  if ((rc = check_ptrs({ct_in_dev, ct_out_dev}))) return rc;
+  if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
+  return launched(fl::launch_direct(ctx->logN, B, dims_of(*geom), w_dev, ct_in_dev, ct_out_dev, r_dev, ctx->cc,
+                                    (cudaStream_t)stream),
+                  "direct conv");
 }
 
 int fl_mask_to_share(fl_ctx* ctx, int n, uint32_t* ct_dev, const uint32_t* r_dev, void* stream) {

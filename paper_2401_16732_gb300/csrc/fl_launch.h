@@ -83,6 +83,11 @@ cudaError_t launch_w_scatter(const int8_t* w, uint32_t* w_hat, const GeomDims& g
 cudaError_t launch_sk_expand(const int8_t* s, uint32_t* out, int N, const CtxConst& cc,
                              cudaStream_t st);
 
+// direct form (fl_direct.cu)
+cudaError_t launch_direct_setup(int logn);
+cudaError_t launch_direct(int logn, int B, const GeomDims& g, const int8_t* w, const uint32_t* ct, uint32_t* out,
+                          const uint32_t* r, const CtxConst& cc, cudaStream_t st);
+
 // x^2 + x protocol and batch encoding (fl_act.cu)
 cudaError_t launch_act_setup(int logn);
 cudaError_t launch_batch_decode(int logn, int n, const uint32_t* m, uint32_t* slots, const uint32_t* tw_t,
