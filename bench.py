@@ -328,8 +328,8 @@ def run_gpu(args, wl, rank, world, local_rank):
         tuned = tune_stack(ctx, [{"g": lay["g"], "ct_in": lay["ct"], "r": lay["r"]} for lay in layers], arr, ws,
                            stream=stream, cache=None)
     else:
-        ctx.stack_kernel = (flashgpu.FL_STACK_PERSISTENT if args.stack_kernel == "persistent"
-                            else flashgpu.FL_STACK_PER_LAYER)
+        ctx.stack_kernel = {"per_layer": flashgpu.FL_STACK_PER_LAYER, "persistent": flashgpu.FL_STACK_PERSISTENT,
+                            "queue": flashgpu.FL_STACK_QUEUE}[args.stack_kernel]
         tuned = {"kernel": args.stack_kernel, "ms": None}
 
     def step(events=None):
@@ -360,7 +360,7 @@ def run_gpu(args, wl, rank, world, local_rank):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         step()
-    launches_per_step = {"persistent": 2, "direct": len(layers)}.get(tuned["kernel"], 1 + len(layers))
+    launches_per_step = {"persistent": 2, "queue": 2, "direct": len(layers)}.get(tuned["kernel"], 1 + len(layers))
 
     def barrier():
         if world > 1:
@@ -453,8 +453,9 @@ def run_gpu(args, wl, rank, world, local_rank):
     achieved_bfly = bfly / kern_s
     hbm_floor, alu_floor = conv_bytes / (hbm * 1e9), bfly / ALU_BFLY_PEAK
     value = world * B * len(layers) * args.steps / (ms * 1e-3)
-    kname = ("k_stack (persistent, all layers)" if tuned["kernel"] == "persistent" else
-             "k_conv_intt (one launch per layer)") + ": contraction + inverse NTT + mask"
+    kname = {"persistent": "k_stack (persistent, warp-specialised, all layers)",
+             "queue": "k_conv_queue (resident CTAs over one queue of all layers' items)"}.get(
+        tuned["kernel"], "k_conv_intt (one launch per layer)") + ": contraction + inverse NTT + mask"
     traffic = TRAFFIC.get((args.config, tuned["kernel"]))
     hbm_line = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_source": peak_kind, "traffic": traffic}
@@ -685,7 +686,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--form", default="ntt", choices=["ntt", "direct"],
                     help="ntt: the NTT route (default); direct: the paper's DRot + CMult form on the GPU")
-    ap.add_argument("--stack-kernel", default="auto", choices=["auto", "per_layer", "persistent"],
+    ap.add_argument("--stack-kernel", default="auto", choices=["auto", "per_layer", "persistent", "queue"],
                     help="kernel for the contraction/INTT/mask stage (auto: time both, keep the faster)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -238,12 +238,17 @@ int fl_he_conv2d_stack_run(fl_ctx *ctx, const fl_stack_layer *layers, int n_laye
  *   once from different host threads);
  * FL_STACK_PERSISTENT: one persistent warp-specialised launch over all
  *   layers (a cp.async-fed contraction team and an inverse-NTT team per SM
- *   handing items over through shared-memory mbarriers).
- * Both give identical outputs; which is faster depends on the stack's shapes
- * (the Python package's autotuner times both and picks).  Default:
+ *   handing items over through shared-memory mbarriers);
+ * FL_STACK_QUEUE: one launch of resident CTAs that pull the fused items
+ *   (image/band, output channel, limb) of every layer from a queue in the
+ *   workspace, each running the contraction + inverse NTT + mask of
+ *   FL_STACK_PER_LAYER; no per-layer wave tails or launch gaps.
+ * All give identical outputs; which is faster depends on the stack's shapes
+ * (the Python package's autotuner times them and picks).  Default:
  * FL_STACK_PER_LAYER. */
 #define FL_STACK_PER_LAYER 0
 #define FL_STACK_PERSISTENT 1
+#define FL_STACK_QUEUE 2
 int fl_ctx_set_stack_kernel(fl_ctx *ctx, int kernel);
 int fl_ctx_get_stack_kernel(const fl_ctx *ctx);
 

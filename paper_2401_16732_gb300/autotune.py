@@ -1,4 +1,4 @@
-"""Pick the faster stack kernel for a workload by timing both on the device.
+"""Pick the fastest stack kernel for a workload by timing each on the device.
 
 The choice depends only on the stack's shapes (ring degree, limbs, layer
 geometries, batch sizes), so it is cached in a JSON file keyed by them.
@@ -13,6 +13,8 @@ import torch
 
 from . import flashgpu
 
+KERNELS = ((flashgpu.FL_STACK_PER_LAYER, "per_layer"), (flashgpu.FL_STACK_PERSISTENT, "persistent"),
+           (flashgpu.FL_STACK_QUEUE, "queue"))
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "flashgpu_autotune.json")
 
 
@@ -40,8 +42,8 @@ def _time(ctx, arr, ws, stream, reps):
 
 
 def tune_stack(ctx: flashgpu.Context, specs, arr, ws, stream=None, reps: int = 3, cache: str | None = DEFAULT_CACHE):
-    """Time both stack kernels on the stack `arr` (inputs already in place),
-    set the faster one on `ctx` and return {"kernel": name, "ms": {...}}."""
+    """Time every stack kernel on the stack `arr` (inputs already in place),
+    set the fastest on `ctx` and return {"kernel": name, "ms": {...}}."""
     stream = stream or torch.cuda.current_stream()
     key = _key(ctx, specs)
     table = {}
@@ -56,13 +58,13 @@ def tune_stack(ctx: flashgpu.Context, specs, arr, ws, stream=None, reps: int = 3
         return {"kernel": table[key]["kernel"], "ms": table[key]["ms"], "cached": True}
     ctx.he_conv2d_stack(arr, ws, stream=stream, stage="ntt")
     ms = {}
-    for kid, name in ((flashgpu.FL_STACK_PER_LAYER, "per_layer"), (flashgpu.FL_STACK_PERSISTENT, "persistent")):
+    for kid, name in KERNELS:
         ctx.stack_kernel = kid
         ms[name] = _time(ctx, arr, ws, stream, reps)
         if ctx.stack_error(ws, stream=stream):
             ms[name] = float("inf")
     best = min(ms, key=ms.get)
-    kid = flashgpu.FL_STACK_PER_LAYER if best == "per_layer" else flashgpu.FL_STACK_PERSISTENT
+    kid = dict((n, k) for k, n in KERNELS)[best]
     ctx.stack_kernel = kid
     table[key] = {"kernel": best, "kernel_id": kid, "ms": ms}
     if cache:

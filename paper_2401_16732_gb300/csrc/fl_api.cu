@@ -24,7 +24,7 @@ constexpr int kAuxStreams = 3;
 
 struct fl_ctx {
   int N, logN, L, device, sms;
-  int stack_kernel;  // FL_STACK_PER_LAYER or FL_STACK_PERSISTENT
+  int stack_kernel;  // FL_STACK_PER_LAYER, FL_STACK_PERSISTENT or FL_STACK_QUEUE
   // per-layer stack launches fan out over these (fork/join through events)
   cudaStream_t aux[kAuxStreams];
   cudaEvent_t fork_ev, join_ev[kAuxStreams];
@@ -645,6 +645,8 @@ static int stack_impl(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, v
   if (!(stages & 2)) return FL_OK;
   if (ctx->stack_kernel == FL_STACK_PERSISTENT)
     return launched(fl::launch_stack(ctx->logN, a, ctl, ctx->tw, ctx->cc, ctx->sms, st), "stack");
+  if (ctx->stack_kernel == FL_STACK_QUEUE)
+    return launched(fl::launch_conv_queue(ctx->logN, a, ctl, ctx->tw, ctx->cc, ctx->sms, st), "stack queue");
   // per-layer fused launches; the error word stays 0 (these kernels never
   // wait).  The layers are independent, so they fan out over the context's
   // auxiliary streams and join back into `st`.
@@ -676,7 +678,8 @@ static int stack_impl(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, v
 
 int fl_ctx_set_stack_kernel(fl_ctx* ctx, int kernel) {
   if (!ctx) return fail(FL_ERR_ARG, "null context");
-  if (kernel != FL_STACK_PER_LAYER && kernel != FL_STACK_PERSISTENT) return fail(FL_ERR_ARG, "kernel=%d", kernel);
+  if (kernel != FL_STACK_PER_LAYER && kernel != FL_STACK_PERSISTENT && kernel != FL_STACK_QUEUE)
+    return fail(FL_ERR_ARG, "kernel=%d", kernel);
   ctx->stack_kernel = kernel;
   return FL_OK;
 }

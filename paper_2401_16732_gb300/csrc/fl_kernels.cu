@@ -71,17 +71,18 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
 // reduced once, inverse-transformed in shared memory and stored with
 // streaming stores; c0 optionally gets + Delta_l * r[u].
 // --------------------------------------------------------------------------
-template <int LOGN, bool MASK>
-__global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>())
-    k_conv_intt(const uint32_t* __restrict__ w_hat, const uint32_t* __restrict__ c_hat,
-                uint32_t* __restrict__ out, const uint32_t* __restrict__ r, ConvDims cd,
-                const uint32_t* __restrict__ tw, CtxConst cc) {
+// One output item: image/band bb, output channel i, limb l.  2 * N/32
+// threads, two padded polynomials of shared memory at `sm`.  r may be null
+// (no mask).
+template <int LOGN>
+__device__ __forceinline__ void conv_item(const uint32_t* __restrict__ w_hat, const uint32_t* __restrict__ c_hat,
+                                          uint32_t* __restrict__ out, const uint32_t* __restrict__ r,
+                                          const ConvDims& cd, int bb, int i, int l, const uint32_t* __restrict__ tw,
+                                          const CtxConst& cc, uint32_t* sm) {
   constexpr int N = 1 << LOGN, T = N / 32, T2 = 2 * T, SW = Geo<LOGN>::SMEM_WORDS;
-  extern __shared__ uint32_t sm[];
   uint32_t* s0 = sm;
   uint32_t* s1 = sm + SW;
-  const int tid = threadIdx.x;
-  const int bb = blockIdx.x, i = blockIdx.y, l = blockIdx.z, L = cc.L;
+  const int tid = threadIdx.x, L = cc.L;
   const int b = bb / cd.bands, band = bb % cd.bands;
   const LimbConst lc = cc.limb[l];
   const size_t ct_words = (size_t)2 * L * N;
@@ -127,12 +128,46 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
   const int h = tid >= T, lt = tid - h * T;
   const size_t oct = (size_t)b * cd.n_out + (size_t)i * cd.bands + band;
   uint32_t* op = out + oct * ct_words + (size_t)h * L * N + (size_t)l * N;
-  const uint32_t* rr = (MASK && h == 0) ? r + oct * N : nullptr;
+  const uint32_t* rr = (r && h == 0) ? r + oct * N : nullptr;
   intt_from_smem<LOGN>(h ? s1 : s0, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, lt, [&](uint32_t v, int u) {
     uint32_t x = v;
-    if (MASK && rr) x += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, lc.q);
+    if (rr) x += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, lc.q);
     __stcs(op + u, csub(csub(x, lc.two_q), lc.q));
   });
+}
+
+// Fused contraction + inverse NTT (+ mask).  Grid (B*bands, Cout, L).
+//   Y_c[u] = sum_g W[l][i][g][u] * C[b][band*G+g][c][l][u]  mod q_l
+// accumulated in 64 bits (products < 2^60; a Barrett fold every 16 terms),
+// reduced once, inverse-transformed in shared memory and stored with
+// streaming stores; c0 optionally gets + Delta_l * r[u].
+template <int LOGN, bool MASK>
+__global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>())
+    k_conv_intt(const uint32_t* __restrict__ w_hat, const uint32_t* __restrict__ c_hat,
+                uint32_t* __restrict__ out, const uint32_t* __restrict__ r, ConvDims cd,
+                const uint32_t* __restrict__ tw, CtxConst cc) {
+  extern __shared__ uint32_t sm[];
+  conv_item<LOGN>(w_hat, c_hat, out, MASK ? r : nullptr, cd, blockIdx.x, blockIdx.y, blockIdx.z, tw, cc, sm);
+}
+
+// The same items for every layer of a stack, pulled from one queue by
+// persistent CTAs (grid = resident CTAs): no wave tails per layer, no gaps
+// between launches.  ctl[0] is the queue head, zeroed before the launch.
+template <int LOGN>
+__global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>())
+    k_conv_queue(StackArgs a, unsigned long long* __restrict__ ctl, const uint32_t* __restrict__ tw, CtxConst cc) {
+  extern __shared__ uint32_t sm[];
+  __shared__ long long s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(ctl, 1ull);
+    __syncthreads();  // also: every thread is done with the previous item's shared memory
+    const long long it = s_item;
+    if (it >= a.n_items) break;
+    const Item x = decode(a, it);
+    const StackLayer& y = a.layer[x.li];
+    const ConvDims cd{y.Cout, y.G, y.n_in, y.n_out, y.bands};
+    conv_item<LOGN>(y.w_hat, y.c_hat, y.out, y.r, cd, x.bb, x.i, x.l, tw, cc, sm);
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -338,6 +373,8 @@ static cudaError_t setup_smem() {
   if ((e = cudaFuncSetAttribute(k_ntt_inv<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4))) return e;
   if ((e = cudaFuncSetAttribute(k_conv_intt<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SW * 4))) return e;
   if ((e = cudaFuncSetAttribute(k_conv_intt<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SW * 4))) return e;
+  if ((e = cudaFuncSetAttribute(k_conv_queue<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SW * 4))) return e;
+  if ((e = cudaFuncSetAttribute(k_conv_queue<LOGN>, cudaFuncAttributePreferredSharedMemoryCarveout, 60))) return e;
   if ((e = cudaFuncSetAttribute(k_pmul_intt<LOGN, MODE_DEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4))) return e;
   if ((e = cudaFuncSetAttribute(k_pmul_intt<LOGN, MODE_ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4))) return e;
   // every kernel here is sized for ~135 KiB of shared memory per SM; the
@@ -402,6 +439,28 @@ cudaError_t launch_conv_intt(int logn, int B, const ConvDims& cd, const uint32_t
     FL_DISPATCH(logn, (k_conv_intt<LG, false><<<grid, N / 16, smem, st>>>(w_hat, c_hat, out, r, cd, tw, cc)));
   }
   return cudaGetLastError();
+}
+
+template <int LOGN>
+static cudaError_t conv_queue_launch(const StackArgs& a, unsigned long long* ctl, const uint32_t* tw,
+                                     const CtxConst& cc, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)2 * Geo<LOGN>::SMEM_WORDS * 4;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_queue<LOGN>, 2 * (1 << LOGN) / 32, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const long long slots = (long long)sms * per_sm;
+  const int grid = (int)(a.n_items < slots ? a.n_items : slots);
+  k_conv_queue<LOGN><<<grid, 2 * (1 << LOGN) / 32, smem, st>>>(a, ctl, tw, cc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv_queue(int logn, const StackArgs& a, unsigned long long* ctl, const uint32_t* tw,
+                              const CtxConst& cc, int sms, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess || a.n_items == 0) return e;
+  FL_DISPATCH(logn, return conv_queue_launch<LG>(a, ctl, tw, cc, sms, st));
+  return cudaSuccess;
 }
 
 cudaError_t launch_pmul_intt(int logn, int mode, int n, uint32_t* ws, uint32_t* ct, const uint32_t* sk,

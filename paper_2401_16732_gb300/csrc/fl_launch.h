@@ -43,6 +43,35 @@ struct StackArgs {
   long long n_items;
 };
 
+#ifdef __CUDACC__
+// Item index of a stack queue -> (layer, image*bands + band, output channel,
+// limb).  Items of a layer run limb-major, then output channel, then
+// image/band, so neighbouring items share weights (over images) or inputs
+// (over output channels).  Linear scan: a stack holds at most FL_STACK_MAX
+// layers.
+struct Item {
+  int li, bb, i, l;
+};
+
+__device__ __forceinline__ int find_layer(const StackArgs& a, long long it) {
+  int li = 0;
+  while (li + 1 < a.n_layers && it >= a.layer[li + 1].item_begin) ++li;
+  return li;
+}
+
+__device__ __forceinline__ Item decode(const StackArgs& a, long long it) {
+  Item x;
+  x.li = find_layer(a, it);
+  const StackLayer& s = a.layer[x.li];
+  long long r = it - s.item_begin;
+  x.bb = (int)(r % s.BB);
+  r /= s.BB;
+  x.i = (int)(r % s.Cout);
+  x.l = (int)(r / s.Cout);
+  return x;
+}
+#endif
+
 struct NttSegs {  // forward NTT of several contiguous row ranges in one launch
   const uint32_t* src[FL_STACK_MAX];
   uint32_t* dst[FL_STACK_MAX];
@@ -64,6 +93,8 @@ cudaError_t launch_ntt_fwd(int logn, int rows, const uint32_t* src, int src_per,
                            const uint32_t* tw, const CtxConst& cc, cudaStream_t st);
 cudaError_t launch_ntt_inv(int logn, int rows, uint32_t* data, const uint32_t* tw, const CtxConst& cc,
                            cudaStream_t st);
+cudaError_t launch_conv_queue(int logn, const StackArgs& a, unsigned long long* ctl, const uint32_t* tw,
+                              const CtxConst& cc, int sms, cudaStream_t st);
 cudaError_t launch_conv_intt(int logn, int B, const ConvDims& cd, const uint32_t* w_hat,
                              const uint32_t* c_hat, uint32_t* out, const uint32_t* r,
                              const uint32_t* tw, const CtxConst& cc, cudaStream_t st);

@@ -82,29 +82,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
 
-// Item index -> layer (linear scan: stacks hold at most FL_STACK_MAX layers).
-__device__ __forceinline__ int find_layer(const StackArgs& a, long long it) {
-  int li = 0;
-  while (li + 1 < a.n_layers && it >= a.layer[li + 1].item_begin) ++li;
-  return li;
-}
-
-struct Item {
-  int li, bb, i, l;
-};
-
-__device__ __forceinline__ Item decode(const StackArgs& a, long long it) {
-  Item x;
-  x.li = find_layer(a, it);
-  const StackLayer& s = a.layer[x.li];
-  long long r = it - s.item_begin;
-  x.bb = (int)(r % s.BB);
-  r /= s.BB;
-  x.i = (int)(r % s.Cout);
-  x.l = (int)(r / s.Cout);
-  return x;
-}
-
 }  // namespace
 
 // PAR = 2: the consumer team has 2 * N/32 threads and transforms both

@@ -24,7 +24,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 FL_OK, FL_ERR_ARG, FL_ERR_SHAPE, FL_ERR_CUDA, FL_ERR_OOM = 0, -1, -2, -3, -4
-FL_STACK_PER_LAYER, FL_STACK_PERSISTENT = 0, 1
+FL_STACK_PER_LAYER, FL_STACK_PERSISTENT, FL_STACK_QUEUE = 0, 1, 2
 FL_NOALLOC_SCRATCH_BYTES = 16 << 20
 FL_STACK_MAX_LAYERS = 64
 

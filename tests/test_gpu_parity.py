@@ -333,11 +333,12 @@ STACKS = [
 ]
 
 
-@pytest.mark.parametrize("kernel", ["per_layer", "persistent"])
+@pytest.mark.parametrize("kernel", ["per_layer", "persistent", "queue"])
 @pytest.mark.parametrize("N,L,layers", STACKS)
 def test_stack_equals_single_layer_and_oracle(fg, oracle, N, L, layers, kernel):
     c = ctx(fg, N, L)
-    c.stack_kernel = fg.FL_STACK_PERSISTENT if kernel == "persistent" else fg.FL_STACK_PER_LAYER
+    c.stack_kernel = {"per_layer": fg.FL_STACK_PER_LAYER, "persistent": fg.FL_STACK_PERSISTENT,
+                      "queue": fg.FL_STACK_QUEUE}[kernel]
     specs, ref = [], []
     for li, (shape, B, masked) in enumerate(layers):
         g = c.geom(*shape)
