@@ -41,7 +41,7 @@ ALU_BFLY_PEAK = 152 * 4 * 16 * 2.07e9 / 4
 DIRECT_MAC_PEAK = 152 * 4 * 16 * 2.07e9
 # DRAM bytes (read + write) of one step's launches of the dominant kernel, from
 # one ncu capture of the same command (profiles/); a kernel change voids them.
-TRAFFIC = {("resnet18", "per_layer"): 2.660e9, ("x2x", "round1"): 1.032e9, ("x2x", "round2"): 1.071e9}
+TRAFFIC = {("resnet18", "queue"): 3.207e9, ("x2x", "round1"): 1.032e9, ("x2x", "round2"): 1.071e9}
 
 
 def peaks():
@@ -321,8 +321,11 @@ def run_gpu(args, wl, rank, world, local_rank):
                                  "out": lay["out"]} for lay in layers])
         ws = ctx.stack_workspace(arr)
     torch.cuda.synchronize()
-    if args.form == "direct":
-        tuned = {"kernel": "direct", "ms": None}
+    if args.form in ("direct", "otf"):
+        tuned = {"kernel": args.form, "ms": None}
+        if args.form == "otf":
+            for lay in layers:
+                lay["ws"] = ctx.workspace(lay["g"], B)
     elif args.stack_kernel == "auto":
         from paper_2401_16732_gb300.autotune import tune_stack
         tuned = tune_stack(ctx, [{"g": lay["g"], "ct_in": lay["ct"], "r": lay["r"]} for lay in layers], arr, ws,
@@ -346,6 +349,17 @@ def run_gpu(args, wl, rank, world, local_rank):
             if events is not None:
                 events[2].record(stream)
             return
+        if args.form == "otf":
+            # input NTT + on-the-fly-weight kernel per layer (the two stages are
+            # not separated here: events[1] == events[0])
+            if events is not None:
+                events[1].record(stream)
+            for lay in layers:
+                ctx.he_conv2d_otf(lay["g"], lay["w"], lay["ct"], out=lay["out"], workspace=lay["ws"], r=lay["r"],
+                                  stream=stream)
+            if events is not None:
+                events[2].record(stream)
+            return
         ctx.he_conv2d_stack(arr, ws, stream=stream, stage="ntt")
         if events is not None:
             events[1].record(stream)
@@ -360,7 +374,8 @@ def run_gpu(args, wl, rank, world, local_rank):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         step()
-    launches_per_step = {"persistent": 2, "queue": 2, "direct": len(layers)}.get(tuned["kernel"], 1 + len(layers))
+    launches_per_step = {"persistent": 2, "queue": 2, "direct": len(layers), "otf": 2 * len(layers)}.get(
+        tuned["kernel"], 1 + len(layers))
 
     def barrier():
         if world > 1:
@@ -479,6 +494,20 @@ def run_gpu(args, wl, rank, world, local_rank):
                 "peak_source": "derived: 152 SMs x 4 x 16 integer-multiply lanes x 2.07 GHz, one MAC per lane-clock",
                 "kernel": "k_direct (one launch per layer): DRot + CMult, no NTT", "kernel_ms_per_step": kern["conv"],
                 "algorithmic_macs_per_step": dmacs}
+        kname = roof["kernel"]
+    if tuned["kernel"] == "otf":
+        # forward NTTs of the rebuilt weight polynomials + the output INTTs;
+        # HBM traffic without the weight stream
+        wbfly = sum(B * g.bands * g.Cout * L * g.G * (N // 2) * (N.bit_length() - 1) for g in geoms)
+        rate = (bfly + wbfly) / kern_s
+        obytes = sum(layer_bytes(g, B, L, N) - L * g.Cout * g.G * N * 4 + ntt_bytes(g, B, L, N) for g in geoms)
+        roof = {"bound": "alu", "achieved": rate / 1e12, "peak": ALU_BFLY_PEAK / 1e12, "unit": "T butterflies/s",
+                "frac": rate / ALU_BFLY_PEAK, "traffic": None,
+                "peak_source": "derived: 152 SMs x 4 x 16 ALU lanes x 2.07 GHz / 4 ALU ops per butterfly",
+                "kernel": "k_ntt_fwd + k_conv_otf per layer: weight polynomials rebuilt and transformed in shared memory",
+                "kernel_ms_per_step": kern["conv"], "algorithmic_butterflies_per_step": bfly + wbfly,
+                "weight_ntt_butterflies_per_step": wbfly, "hbm_bytes_per_step": obytes,
+                "encoded_weight_bytes_avoided": sum(L * g.Cout * g.G * N * 4 for g in geoms)}
         kname = roof["kernel"]
     line = {
         "metric": "encrypted conv layers/s", "value": value, "unit": "layers/s", "n_gpus": world,
@@ -684,8 +713,9 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--form", default="ntt", choices=["ntt", "direct"],
-                    help="ntt: the NTT route (default); direct: the paper's DRot + CMult form on the GPU")
+    ap.add_argument("--form", default="ntt", choices=["ntt", "direct", "otf"],
+                    help="ntt: the NTT route with encoded weights (default); direct: the paper's DRot + CMult form "
+                         "on the GPU; otf: the NTT route with weights rebuilt on the fly (no encoded weights)")
     ap.add_argument("--stack-kernel", default="auto", choices=["auto", "per_layer", "persistent", "queue"],
                     help="kernel for the contraction/INTT/mask stage (auto: time both, keep the faster)")
     args = ap.parse_args()

@@ -176,6 +176,20 @@ int fl_he_conv2d_from_ntt(fl_ctx *ctx, const fl_conv_geom *geom, int B, const ui
                           const void *workspace_dev, size_t workspace_bytes, const uint32_t *r_dev,
                           uint32_t *ct_out_dev, void *stream);
 
+/* The same convolution with on-the-fly weights.  It takes the int8 filters
+ * w_dev [Cout][Cin][k][k] in place of fl_encode_weights' output.  Every CTA
+ * rebuilds the weight polynomials W_{i,g} it needs in shared memory from
+ * their c_n*k^2 taps (Algorithm 1's DRot offsets, x^-e = -x^(N-e)).  It
+ * forward-transforms them there and uses them at once, so no NTT-domain
+ * weights are stored.  That removes the footprint of Table 3's PMult
+ * comparison: Cout*G*L*N*4 bytes per layer, 56.7 GiB for ResNet-50 at
+ * N = 16384.  The cost is one forward NTT per (image, output channel, limb,
+ * input ciphertext).  The workspace, its size and the result (bit-identical,
+ * plus the mask when r_dev is not NULL) are those of fl_he_conv2d_mask. */
+int fl_he_conv2d_otf(fl_ctx *ctx, const fl_conv_geom *geom, int B, const int8_t *w_dev,
+                     const uint32_t *ct_in_dev, const uint32_t *r_dev, uint32_t *ct_out_dev,
+                     void *workspace_dev, size_t workspace_bytes, void *stream);
+
 /* Direct form of the same convolution: Algorithm 1's DRot + CMult, where
  * DRot by e is multiplication by x^-e (Eq. 2).  It runs on the GPU with no
  * NTT, from the int8 filters w_dev [Cout][Cin][k][k] as they are (no encoded

@@ -312,7 +312,7 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
   }
   if ((e = fl::launch_setup(logN)) != cudaSuccess || (e = fl::launch_stack_setup(logN)) != cudaSuccess ||
       (e = fl::launch_ntt_multi_setup(logN)) != cudaSuccess || (e = fl::launch_act_setup(logN)) != cudaSuccess ||
-      (e = fl::launch_direct_setup(logN)) != cudaSuccess) {
+      (e = fl::launch_direct_setup(logN)) != cudaSuccess || (e = fl::launch_otf_setup(logN)) != cudaSuccess) {
     delete c;
     return cuda_fail(e, "kernel set-up");
   }
@@ -545,6 +545,22 @@ int fl_he_conv2d_mask(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32
   if (!r_dev) return fail(FL_ERR_ARG, "null mask");
   return he_conv2d_impl(ctx, geom, B, w_hat_dev, ct_in_dev, r_dev, ct_out_dev, workspace_dev, workspace_bytes,
                         stream);
+}
+
+int fl_he_conv2d_otf(fl_ctx* ctx, const fl_conv_geom* geom, int B, const int8_t* w_dev, const uint32_t* ct_in_dev,
+                     const uint32_t* r_dev, uint32_t* ct_out_dev, void* workspace_dev, size_t workspace_bytes,
+                     void* stream) {
+  int rc;
+  if ((rc = conv_checks(ctx, geom, B, workspace_bytes))) return rc;
+  if (B == 0) return FL_OK;
+  if (!w_dev) return fail(FL_ERR_ARG, "null filters");
+  if ((rc = check_ptrs({ct_in_dev, ct_out_dev, workspace_dev}))) return rc;
+  if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = stage_ntt(ctx, geom, B, ct_in_dev, workspace_dev, st))) return rc;
+  return launched(fl::launch_conv_otf(ctx->logN, B, dims_of(*geom), w_dev, (const uint32_t*)workspace_dev, ct_out_dev,
+                                      r_dev, ctx->tw, ctx->cc, st),
+                  "on-the-fly conv");
 }
 
 int fl_he_conv2d_direct(fl_ctx* ctx, const fl_conv_geom* geom, int B, const int8_t* w_dev, const uint32_t* ct_in_dev,

@@ -114,6 +114,12 @@ cudaError_t launch_w_scatter(const int8_t* w, uint32_t* w_hat, const GeomDims& g
 cudaError_t launch_sk_expand(const int8_t* s, uint32_t* out, int N, const CtxConst& cc,
                              cudaStream_t st);
 
+// on-the-fly weights (fl_otf.cu)
+cudaError_t launch_otf_setup(int logn);
+cudaError_t launch_conv_otf(int logn, int B, const GeomDims& gd, const int8_t* w, const uint32_t* c_hat,
+                            uint32_t* out, const uint32_t* r, const uint32_t* tw, const CtxConst& cc,
+                            cudaStream_t st);
+
 // direct form (fl_direct.cu)
 cudaError_t launch_direct_setup(int logn);
 cudaError_t launch_direct(int logn, int B, const GeomDims& g, const int8_t* w, const uint32_t* ct, uint32_t* out,

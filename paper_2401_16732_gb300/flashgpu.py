@@ -63,6 +63,7 @@ _SIGS = {
     "fl_he_conv2d": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_mask_to_share": ([_vp, _i, _vp, _vp, _vp], _i),
     "fl_he_conv2d_direct": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp], _i),
+    "fl_he_conv2d_otf": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_he_conv2d_mask": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_he_conv2d_ntt_inputs": ([_vp, _gp, _i, _vp, _vp, _sz, _vp], _i),
     "fl_he_conv2d_from_ntt": ([_vp, _gp, _i, _vp, _vp, _sz, _vp, _vp, _vp], _i),
@@ -297,6 +298,22 @@ class Context:
         caller's [B][n_out][2][L][N] buffer."""
         _check(_lib.fl_he_conv2d_mask_noalloc(self.h, ctypes.byref(g), ct_in.shape[0], _ptr(w_hat), _ptr(ct_in),
                                               _ptr(r), _ptr(out), _stream(stream)))
+        return out
+
+    def he_conv2d_otf(self, g, w, ct_in, out=None, workspace=None, r=None, stream=None) -> torch.Tensor:
+        """On-the-fly weights: the same ciphertexts as he_conv2d (plus the mask
+        when r is given) from int8 filters w [Cout][Cin][k][k], with no
+        encoded weights."""
+        B = ct_in.shape[0]
+        if w.dtype != torch.int8 or not w.is_cuda or not w.is_contiguous() or \
+                tuple(w.shape) != (g.Cout, g.Cin, g.k, g.k):
+            raise FlashError("w: expected a contiguous int8 CUDA tensor [Cout][Cin][k][k]")
+        _dev_u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
+        out = self._new(B, g.n_out, 2, self.L, self.N) if out is None else out
+        workspace = self.workspace(g, B) if workspace is None else workspace
+        _check(_lib.fl_he_conv2d_otf(self.h, ctypes.byref(g), B, _ptr(w), _ptr(ct_in), _ptr(r), _ptr(out),
+                                     _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                     _stream(stream)))
         return out
 
     def he_conv2d_direct(self, g, w, ct_in, out=None, r=None, stream=None) -> torch.Tensor:

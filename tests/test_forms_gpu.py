@@ -1,6 +1,7 @@
-"""Parity of the direct-form GPU convolution (Algorithm 1's DRot + CMult, no
-NTT) with the oracle's Algorithm 1 (route O2) and with the NTT route.  All
-comparisons are bit-exact."""
+"""Parity of the two other GPU forms of the convolution with the oracle's
+Algorithm 1 (route O2) and with the NTT route: the direct form (DRot + CMult,
+no NTT) and on-the-fly weights (weight polynomials rebuilt and transformed
+in shared memory, no encoded weights).  All comparisons are bit-exact."""
 import numpy as np
 import pytest
 
@@ -99,3 +100,30 @@ def test_direct_form_limits(fg):
     g2 = c.geom(3, 2, 8, 8, 3, 1, 1)
     empty = torch.empty((0, g2.n_in, 2, 1, 2048), dtype=torch.int32, device="cuda")
     assert c.he_conv2d_direct(g2, torch.zeros((2, 3, 3, 3), dtype=torch.int8, device="cuda"), empty).shape[0] == 0
+
+
+# ------------------------------------------------------------------ on-the-fly weights
+OTF_CASES = CASES + [
+    (2048, 3, (8, 101, 6, 6, 3, 1, 1), 2),       # odd Cout, many CTAs, G = 1
+    (4096, 2, (40, 7, 8, 8, 1, 1, 0), 1),        # 1x1, 40 taps per polynomial
+]
+
+
+@pytest.mark.parametrize("N,L,shape,B", OTF_CASES)
+def test_otf_weights_bit_exact(fg, oracle, N, L, shape, B):
+    c = ctx(fg, N, L)
+    g = c.geom(*shape)
+    geo = oracle.geometry(N, *shape)
+    w = synth.weights(13, (g.Cout, g.Cin, g.k, g.k))
+    ct = synth.raw_ciphertexts(13, c.primes, (B, g.n_in, 2, L, N))
+    r = synth.masks(13, (B, g.n_out, N), T)
+    dw, dct, dr = dev(w, torch.int8), dev(ct), dev(r)
+    ym = u32(c.he_conv2d_otf(g, dw, dct, r=dr))
+    y = u32(c.he_conv2d_otf(g, dw, dct))
+    assert (ym == u32(c.he_conv2d(g, c.encode_weights(g, dw), dct, r=dr))).all()
+    for b in range(B):
+        for i in ([0, g.Cout - 1] if g.Cout > 1 else [0]):
+            want = oracle.conv_alg1(ct[b], w, geo, c.primes, i, i + 1)
+            sl = slice(i * g.bands, (i + 1) * g.bands)
+            assert (y[b, sl] == want).all()
+            assert (ym[b, sl] == oracle.mask(want, r[b, sl], c.primes)).all()
