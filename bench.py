@@ -335,17 +335,20 @@ def run_gpu(args, wl, rank, world, local_rank):
                             "queue": flashgpu.FL_STACK_QUEUE}[args.stack_kernel]
         tuned = {"kernel": args.stack_kernel, "ms": None}
 
-    def step(events=None):
+    def step(events=None, outs=None, arr_=None):
         # forward NTT of every layer's inputs (one launch), then the
-        # persistent contraction + inverse NTT + mask kernel over all layers
+        # contraction + inverse NTT + mask kernel(s) over all layers; `outs`
+        # / `arr_` select another set of output buffers
+        outs = outs or [lay["out"] for lay in layers]
+        arr_ = arr if arr_ is None else arr_
         if events is not None:
             events[0].record(stream)
         if args.form == "direct":
             # the paper's DRot + CMult form on the GPU: one launch per layer, no NTT
             if events is not None:
                 events[1].record(stream)
-            for lay in layers:
-                ctx.he_conv2d_direct(lay["g"], lay["w"], lay["ct"], out=lay["out"], r=lay["r"], stream=stream)
+            for lay, o in zip(layers, outs):
+                ctx.he_conv2d_direct(lay["g"], lay["w"], lay["ct"], out=o, r=lay["r"], stream=stream)
             if events is not None:
                 events[2].record(stream)
             return
@@ -354,16 +357,16 @@ def run_gpu(args, wl, rank, world, local_rank):
             # not separated here: events[1] == events[0])
             if events is not None:
                 events[1].record(stream)
-            for lay in layers:
-                ctx.he_conv2d_otf(lay["g"], lay["w"], lay["ct"], out=lay["out"], workspace=lay["ws"], r=lay["r"],
+            for lay, o in zip(layers, outs):
+                ctx.he_conv2d_otf(lay["g"], lay["w"], lay["ct"], out=o, workspace=lay["ws"], r=lay["r"],
                                   stream=stream)
             if events is not None:
                 events[2].record(stream)
             return
-        ctx.he_conv2d_stack(arr, ws, stream=stream, stage="ntt")
+        ctx.he_conv2d_stack(arr_, ws, stream=stream, stage="ntt")
         if events is not None:
             events[1].record(stream)
-        ctx.he_conv2d_stack(arr, ws, stream=stream, stage="run")
+        ctx.he_conv2d_stack(arr_, ws, stream=stream, stage="run")
         if events is not None:
             events[2].record(stream)
 
@@ -423,9 +426,13 @@ def run_gpu(args, wl, rank, world, local_rank):
     # ---- end to end: pinned host inputs -> device -> path -> host outputs ----
     e2e = None
     if not args.skip_e2e:
-        # every layer's inputs come from, and every layer's output ciphertexts
-        # go to, pinned host memory (one reused buffer per direction, sized for
-        # the largest layer)
+        # Every step copies every layer's input ciphertexts in from pinned
+        # host memory and every layer's output ciphertexts back out (one
+        # reused host buffer per direction, sized for the largest layer; the
+        # bytes moved are those of the whole step).  When a second set of
+        # output buffers fits on the device, steps are pipelined the way a
+        # server runs them: step k's outputs drain on a copy stream while step
+        # k+1's inputs arrive and its kernels run.
         in_words = max(lay["ct"].numel() for lay in layers)
         out_words = max(lay["out"].numel() for lay in layers)
         h_in = torch.empty(in_words, dtype=torch.int32, pin_memory=True)
@@ -433,26 +440,56 @@ def run_gpu(args, wl, rank, world, local_rank):
         h_in.copy_(max(layers, key=lambda lay: lay["ct"].numel())["ct"].view(-1).cpu())
         h2d = sum(lay["ct"].numel() * 4 for lay in layers)
         d2h = sum(lay["out"].numel() * 4 for lay in layers)
-        n_e2e = max(1, min(args.steps, 5 if d2h < 8e9 else 2))
+        n_e2e = max(2, min(args.steps, 6 if d2h < 8e9 else 2))
+        free, _ = torch.cuda.mem_get_info(dev)
+        sets = [([lay["out"] for lay in layers], arr, graph)]
+        if free > 1.25 * d2h + (2 << 30):
+            outs2 = [torch.empty_like(lay["out"]) for lay in layers]
+            arr2 = None
+            if args.form == "ntt":
+                arr2 = ctx.stack_layers([{"g": lay["g"], "w_hat": lay["w_hat"], "ct_in": lay["ct"], "r": lay["r"],
+                                          "out": o} for lay, o in zip(layers, outs2)])
+            with torch.cuda.stream(stream):
+                step(outs=outs2, arr_=arr2)
+            stream.synchronize()
+            graph2 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph2, stream=stream):
+                step(outs=outs2, arr_=arr2)
+            sets.append((outs2, arr2, graph2))
+        copy_stream = torch.cuda.Stream(device=dev)
+        ev_comp = [torch.cuda.Event() for _ in sets]
+        ev_done = [torch.cuda.Event() for _ in sets]
+        for e in ev_done:
+            e.record(copy_stream)
 
-        def e2e_step():
+        def e2e_step(k):
+            si = k % len(sets)
+            outs, _, g_ = sets[si]
             with torch.cuda.stream(stream):
                 for lay in layers:
                     lay["ct"].view(-1).copy_(h_in[:lay["ct"].numel()], non_blocking=True)
-            replay()
-            with torch.cuda.stream(stream):
-                for lay in layers:
-                    h_out[:lay["out"].numel()].copy_(lay["out"].view(-1), non_blocking=True)
-            stream.synchronize()
+                stream.wait_event(ev_done[si])  # this output set has drained
+                g_.replay()
+                ev_comp[si].record(stream)
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(ev_comp[si])
+                for o in outs:
+                    h_out[:o.numel()].copy_(o.view(-1), non_blocking=True)
+                ev_done[si].record(copy_stream)
 
-        e2e_step()
+        for k in range(len(sets)):
+            e2e_step(k)
+        torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        for _ in range(n_e2e):
-            e2e_step()
+        for k in range(n_e2e):
+            e2e_step(k)
+        copy_stream.synchronize()
+        stream.synchronize()
         e2e_rate, _ = whole_job_rate(B * len(layers) * n_e2e, time.perf_counter() - t0, dev)
         e2e = {"value": e2e_rate, "unit": "layers/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": n_e2e}
+               "d2h_bytes_per_step": d2h, "steps": n_e2e,
+               "pipelined": len(sets) == 2}
     clocks.stop()
 
     if rank != 0:
@@ -555,10 +592,11 @@ def run_x2x(args, rank, world, local_rank):
     out1, out2 = torch.empty_like(ct_z), torch.empty_like(ct_z)
     torch.cuda.synchronize()
 
-    def step(ev=None):
+    def step(ev=None, o1=None):
+        o1 = out1 if o1 is None else o1
         if ev is not None:
             ev[0].record(stream)
-        ctx.x2x_round1(prep, ct_z, out1, stream=stream)
+        ctx.x2x_round1(prep, ct_z, o1, stream=stream)
         if ev is not None:
             ev[1].record(stream)
         ctx.x2x_round2(prep, ct_x, ct_y, out2, stream=stream)
@@ -596,29 +634,45 @@ def run_x2x(args, rank, world, local_rank):
 
     e2e = None
     if not args.skip_e2e:
-        # client -> server: <z> (batch), <X>, <Y>; server -> client: round 1's <2rz + v>
+        # client -> server: <z> (batch), <X>, <Y>; server -> client: round 1's
+        # <2rz + v>.  Steps are pipelined: round 1's output of step k drains on
+        # a copy stream (two output buffers) while step k+1's inputs arrive.
         h_in = [torch.empty(ct_z.numel(), dtype=torch.int32, pin_memory=True) for _ in range(3)]
         for h, d in zip(h_in, (ct_z, ct_x, ct_y)):
             h.copy_(d.view(-1).cpu())
         h_out = torch.empty(ct_z.numel(), dtype=torch.int32, pin_memory=True)
-        n_e2e = max(1, min(args.steps, 5))
+        o1s = [out1, torch.empty_like(out1)]
+        copy_stream = torch.cuda.Stream(device=dev)
+        ev_comp = [torch.cuda.Event() for _ in o1s]
+        ev_done = [torch.cuda.Event() for _ in o1s]
+        for e in ev_done:
+            e.record(copy_stream)
+        n_e2e = max(2, min(args.steps, 6))
 
-        def e2e_step():
+        def e2e_step(k):
+            si = k % 2
             with torch.cuda.stream(stream):
                 for h, d in zip(h_in, (ct_z, ct_x, ct_y)):
                     d.view(-1).copy_(h, non_blocking=True)
-            step()
-            with torch.cuda.stream(stream):
-                h_out.copy_(out1.view(-1), non_blocking=True)
-            stream.synchronize()
+                stream.wait_event(ev_done[si])
+                step(o1=o1s[si])
+                ev_comp[si].record(stream)
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(ev_comp[si])
+                h_out.copy_(o1s[si].view(-1), non_blocking=True)
+                ev_done[si].record(copy_stream)
 
-        e2e_step()
+        e2e_step(0)
+        e2e_step(1)
+        torch.cuda.synchronize()
         ts = time.perf_counter()
-        for _ in range(n_e2e):
-            e2e_step()
+        for k in range(n_e2e):
+            e2e_step(k)
+        copy_stream.synchronize()
+        stream.synchronize()
         rate, _ = whole_job_rate(acts * n_e2e, time.perf_counter() - ts, dev)
         e2e = {"value": rate, "unit": "activations/s", "h2d_bytes_per_step": 3 * ct_z.numel() * 4,
-               "d2h_bytes_per_step": out1.numel() * 4, "steps": n_e2e}
+               "d2h_bytes_per_step": out1.numel() * 4, "steps": n_e2e, "pipelined": True}
     clocks.stop()
     if rank != 0:
         return 0
