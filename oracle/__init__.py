@@ -300,6 +300,27 @@ def noise_inf(s, ct, m_expected, primes, t=T_DEFAULT) -> int:
     return int(max(abs(int(z)) for z in v.ravel()))
 
 
+def mod_switch(ct, primes, L_out) -> np.ndarray:
+    """BFV modulus switching (Fan and Vercauteren's scale-and-round by q'/q),
+    dropping the last RNS primes one at a time: each step replaces the CRT
+    value x in [0, q) of every coefficient of both components by the nearest
+    integer to x / q_last (never a tie: q_last is odd), reduced mod q' = q /
+    q_last.  The result decrypts under the first L_out primes.  The paper
+    keeps one modulus and does not switch; this reduces the volume of output
+    ciphertexts.  ct [..][2][L][N] -> [..][2][L_out][N]."""
+    cur = list(primes)
+    res = _u32(ct)
+    while len(cur) > L_out:
+        ql, nxt = cur[-1], cur[:-1]
+        x = crt(res, cur)
+        xr = ((2 * x + ql) // (2 * ql)) % math.prod(nxt)
+        out = np.empty(res.shape[:-2] + (len(nxt), res.shape[-1]), np.uint32)
+        for i, qi in enumerate(nxt):
+            out[..., i, :] = (xr % qi).astype(np.int64)
+        res, cur = out, nxt
+    return res
+
+
 def mask(ct: np.ndarray, r: np.ndarray, primes, t=T_DEFAULT) -> np.ndarray:
     """c0 <- c0 + Delta*r for cts [n][2][L][N], r[n][N] in [0, t)."""
     ct = _u32(ct).copy()

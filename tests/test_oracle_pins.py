@@ -403,3 +403,51 @@ def test_x2x_protocol_end_to_end(oracle):
     ct_y = enc(Yb[None], 3)                                              # re-encrypt, direct
     out = oracle.x2x_server_round2(ct_x, ct_y, r, v, primes)             # server round 2
     assert (oracle.decrypt(s, out, primes) == (a * a + a) % T).all()
+
+
+# ----------------------------------------------------------------- modulus switching
+def test_mod_switch_rounds_to_nearest(oracle):
+    """Each dropped prime leaves x' with |q_last * x' - x| <= q_last / 2 on the
+    CRT values (the defining property of rounding to the nearest integer),
+    checked against big-integer CRT of input and output."""
+    N, L = 64, 3
+    primes = oracle.find_primes(2048, L)
+    ct = synth.raw_ciphertexts(70, primes, (2, 2, L, N))
+    out = oracle.mod_switch(ct, primes, L - 1)
+    x = oracle.crt(ct, primes)
+    xp = oracle.crt(out, primes[:-1])
+    ql, qn = primes[-1], math.prod(primes[:-1])
+    for a, b in zip(x.ravel(), xp.ravel()):
+        d = ql * int(b) - int(a)
+        # x' is taken mod q'; undo a wrap at the top of the range
+        if d < -(ql // 2):
+            d += ql * qn
+        assert abs(d) <= ql // 2
+
+
+@pytest.mark.parametrize("L,L_out", [(3, 2), (4, 2), (4, 3)])
+def test_mod_switch_keeps_the_message(oracle, L, L_out):
+    """Decrypting under the first L_out primes after switching gives the same
+    plaintext, including after a convolution and the mask; the noise is the
+    scaled noise plus at most (1 + ||s||_1)/2 of rounding."""
+    N, T_ = 256, T
+    primes = oracle.find_primes(N, L)
+    geo = oracle.geometry(N, 2, 3, 6, 6, 3, 1, 1)
+    s = synth.secret_key(71, N)
+    x = synth.activations(71, (2, 6, 6))
+    w = synth.weights(71, (3, 2, 3, 3))
+    m = oracle.pack_inputs(x, geo)
+    ct = oracle.encrypt(s, synth.uniform_residues(71, primes, (geo.n_in, L, N)),
+                        synth.cbd_noise(71, (geo.n_in, N)), m, primes)
+    r = synth.masks(71, (geo.n_out, N), T_)
+    y = oracle.mask(oracle.conv_alg1(ct, w, geo, primes), r, primes)
+    want = oracle.decrypt(s, y, primes)
+    ys = oracle.mod_switch(y, primes, L_out)
+    assert ys.shape == (geo.n_out, 2, L_out, N)
+    assert (oracle.decrypt(s, ys, primes[:L_out]) == want).all()
+    q, qs = math.prod(primes), math.prod(primes[:L_out])
+    v = oracle.noise_inf(s, y, want, primes)
+    vs = oracle.noise_inf(s, ys, want, primes[:L_out])
+    # Delta' m differs from (q'/q) Delta m by less than t; rounding adds (1+||s||_1)/2 per drop
+    steps = L - L_out
+    assert vs <= v * qs // q + steps * (1 + int(np.abs(s).sum())) // 2 + T_ + steps
