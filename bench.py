@@ -424,7 +424,7 @@ def run_gpu(args, wl, rank, world, local_rank):
         raise RuntimeError(f"persistent kernel reported a timed-out wait (error word {err_word})")
 
     # ---- end to end: pinned host inputs -> device -> path -> host outputs ----
-    e2e = None
+    e2e = e2e_switched = None
     if not args.skip_e2e:
         # Every step copies every layer's input ciphertexts in from pinned
         # host memory and every layer's output ciphertexts back out (one
@@ -457,39 +457,65 @@ def run_gpu(args, wl, rank, world, local_rank):
                 step(outs=outs2, arr_=arr2)
             sets.append((outs2, arr2, graph2))
         copy_stream = torch.cuda.Stream(device=dev)
-        ev_comp = [torch.cuda.Event() for _ in sets]
-        ev_done = [torch.cuda.Event() for _ in sets]
-        for e in ev_done:
-            e.record(copy_stream)
 
-        def e2e_step(k):
-            si = k % len(sets)
-            outs, _, g_ = sets[si]
-            with torch.cuda.stream(stream):
-                for lay in layers:
-                    lay["ct"].view(-1).copy_(h_in[:lay["ct"].numel()], non_blocking=True)
-                stream.wait_event(ev_done[si])  # this output set has drained
-                g_.replay()
-                ev_comp[si].record(stream)
-            with torch.cuda.stream(copy_stream):
-                copy_stream.wait_event(ev_comp[si])
-                for o in outs:
-                    h_out[:o.numel()].copy_(o.view(-1), non_blocking=True)
-                ev_done[si].record(copy_stream)
+        def run_e2e(L_out=None):
+            # L_out: switch every output to its first L_out primes on the
+            # device (BFV modulus switching) before it leaves
+            nb = 2 if len(sets) == 2 else 1
+            drain = None
+            if L_out:
+                need = d2h * L_out // L
+                free_now, _ = torch.cuda.mem_get_info(dev)
+                nb = 2 if free_now > 2 * need + (2 << 30) else 1 if free_now > need + (1 << 30) else 0
+                if nb == 0:
+                    return None
+                drain = [[torch.empty(tuple(o.shape[:-2]) + (L_out, N), dtype=o.dtype, device=dev) for o in sets[0][0]]
+                         for _ in range(nb)]
+            ev_comp = [torch.cuda.Event() for _ in range(nb)]
+            ev_done = [torch.cuda.Event() for _ in range(nb)]
+            for e in ev_done:
+                e.record(copy_stream)
 
-        for k in range(len(sets)):
-            e2e_step(k)
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        for k in range(n_e2e):
-            e2e_step(k)
-        copy_stream.synchronize()
-        stream.synchronize()
-        e2e_rate, _ = whole_job_rate(B * len(layers) * n_e2e, time.perf_counter() - t0, dev)
-        e2e = {"value": e2e_rate, "unit": "layers/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": n_e2e,
-               "pipelined": len(sets) == 2}
+            def e2e_step(k):
+                outs, _, g_ = sets[k % len(sets)]
+                di = k % nb
+                with torch.cuda.stream(stream):
+                    for lay in layers:
+                        lay["ct"].view(-1).copy_(h_in[:lay["ct"].numel()], non_blocking=True)
+                    if not L_out:
+                        stream.wait_event(ev_done[di])  # this output set has drained
+                    g_.replay()
+                    if L_out:
+                        stream.wait_event(ev_done[di])
+                        for o, d in zip(outs, drain[di]):
+                            ctx.mod_switch(o, L_out, out=d, stream=stream)
+                    ev_comp[di].record(stream)
+                with torch.cuda.stream(copy_stream):
+                    copy_stream.wait_event(ev_comp[di])
+                    for o in (drain[di] if L_out else outs):
+                        h_out[:o.numel()].copy_(o.view(-1), non_blocking=True)
+                    ev_done[di].record(copy_stream)
+
+            for k in range(2):
+                e2e_step(k)
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            for k in range(n_e2e):
+                e2e_step(k)
+            copy_stream.synchronize()
+            stream.synchronize()
+            rate, _ = whole_job_rate(B * len(layers) * n_e2e, time.perf_counter() - t0, dev)
+            out_bytes = d2h if not L_out else d2h * L_out // L
+            return {"value": rate, "unit": "layers/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": out_bytes,
+                    "steps": n_e2e, "pipelined": nb == 2}
+
+        e2e = run_e2e()
+        if L > 2:
+            e2e_switched = run_e2e(2)
+        if e2e_switched is not None:
+            e2e_switched["note"] = ("outputs switched to their first 2 RNS primes on the device before the copy "
+                                    "(BFV modulus switching, an addition to the paper's protocol)")
     clocks.stop()
 
     if rank != 0:
@@ -561,6 +587,8 @@ def run_gpu(args, wl, rank, world, local_rank):
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if e2e_switched is not None:
+        line["e2e_switched"] = e2e_switched
     if world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(wl, args.seed)
     print(json.dumps(line), flush=True)

@@ -270,6 +270,22 @@ int fl_ctx_get_stack_kernel(const fl_ctx *ctx);
  * fl_he_conv2d_stack (0: no internal wait ran out). */
 int fl_stack_error(const void *workspace_dev, void *stream, uint64_t *error_host);
 
+/* ---- Output volume ---- */
+
+/* BFV modulus switching: n ciphertexts ct_in_dev [n][2][L][N] ->
+ * ct_out_dev [n][2][L_out][N], dropping the last L - L_out primes one at a
+ * time with rounding (Fan and Vercauteren's scale-and-round by q'/q; each
+ * coefficient becomes the nearest integer to x / p mod q' for every dropped
+ * prime p).  The result decrypts under a context of the first L_out primes
+ * (fl_ctx_create(N, L_out, t) picks exactly those) to the same plaintext.
+ * The noise is scaled by q'/q, plus at most (1 + ||s||_1)/2 per dropped
+ * prime.  The paper keeps one modulus; this only shrinks what leaves the
+ * device (output volume, one factor L / L_out).  Decryption needs q' well
+ * above t^2, so with t = 65537 and 30-bit primes keep L_out >= 2.
+ * 1 <= L_out <= L (FL_ERR_ARG otherwise).  The buffers must not overlap
+ * (FL_ERR_ARG). */
+int fl_mod_switch(fl_ctx *ctx, int n, const uint32_t *ct_in_dev, int L_out, uint32_t *ct_out_dev, void *stream);
+
 /* ---- For callers that may not allocate device memory ---- */
 
 /* fl_he_conv2d_mask_noalloc: the same computation and arguments as

@@ -547,6 +547,34 @@ int fl_he_conv2d_mask(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32
                         stream);
 }
 
+int fl_mod_switch(fl_ctx* ctx, int n, const uint32_t* ct_in_dev, int L_out, uint32_t* ct_out_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
+  if (L_out < 1 || L_out > ctx->L) return fail(FL_ERR_ARG, "L_out=%d outside [1, %d]", L_out, ctx->L);
+  if (n == 0) return FL_OK;
+  if ((rc = check_ptrs({ct_in_dev, ct_out_dev}))) return rc;
+  const char* a = (const char*)ct_in_dev;
+  const char* b = (const char*)ct_out_dev;
+  const size_t in_bytes = (size_t)n * 2 * ctx->L * ctx->N * 4, out_bytes = (size_t)n * 2 * L_out * ctx->N * 4;
+  if (a < b + out_bytes && b < a + in_bytes) return fail(FL_ERR_ARG, "input and output overlap");
+  fl::ModSwitchConst mc;
+  memset(&mc, 0, sizeof mc);
+  mc.L = ctx->L;
+  mc.L_out = L_out;
+  for (int d = 0; d < ctx->L; ++d) {
+    const uint32_t p = ctx->cc.limb[d].q;
+    mc.q[d] = p;
+    for (int i = 0; i < d; ++i) {
+      const uint32_t qi = ctx->cc.limb[i].q;
+      mc.inv[d][i] = (uint32_t)powmod(p % qi, qi - 2, qi);
+      mc.inv_sh[d][i] = shoup(mc.inv[d][i], qi);
+    }
+  }
+  return launched(fl::launch_mod_switch(ct_in_dev, ct_out_dev, 2LL * n, ctx->N, mc, (cudaStream_t)stream),
+                  "modulus switch");
+}
+
 int fl_he_conv2d_otf(fl_ctx* ctx, const fl_conv_geom* geom, int B, const int8_t* w_dev, const uint32_t* ct_in_dev,
                      const uint32_t* r_dev, uint32_t* ct_out_dev, void* workspace_dev, size_t workspace_bytes,
                      void* stream) {

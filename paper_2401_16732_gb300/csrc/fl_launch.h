@@ -26,6 +26,12 @@ struct DecConst {  // exact RNS scale-and-round constants
   int L;
 };
 
+struct ModSwitchConst {  // modulus switching from L to L_out limbs
+  uint32_t q[FL_MAX_L];
+  uint32_t inv[FL_MAX_L][FL_MAX_L], inv_sh[FL_MAX_L][FL_MAX_L];  // q_d^-1 mod q_i (i < d), Shoup companion
+  int L, L_out;
+};
+
 #define FL_STACK_MAX 64
 
 struct StackLayer {  // one layer of a persistent stack launch
@@ -113,6 +119,10 @@ cudaError_t launch_w_scatter(const int8_t* w, uint32_t* w_hat, const GeomDims& g
                              const CtxConst& cc, cudaStream_t st);
 cudaError_t launch_sk_expand(const int8_t* s, uint32_t* out, int N, const CtxConst& cc,
                              cudaStream_t st);
+
+// modulus switching (fl_modswitch.cu)
+cudaError_t launch_mod_switch(const uint32_t* in, uint32_t* out, long long rows, int N, const ModSwitchConst& mc,
+                              cudaStream_t st);
 
 // on-the-fly weights (fl_otf.cu)
 cudaError_t launch_otf_setup(int logn);

@@ -63,6 +63,7 @@ _SIGS = {
     "fl_he_conv2d": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_mask_to_share": ([_vp, _i, _vp, _vp, _vp], _i),
     "fl_he_conv2d_direct": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp], _i),
+    "fl_mod_switch": ([_vp, _i, _vp, _i, _vp, _vp], _i),
     "fl_he_conv2d_otf": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_he_conv2d_mask": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_he_conv2d_ntt_inputs": ([_vp, _gp, _i, _vp, _vp, _sz, _vp], _i),
@@ -327,6 +328,16 @@ class Context:
         out = self._new(B, g.n_out, 2, self.L, self.N) if out is None else out
         _check(_lib.fl_he_conv2d_direct(self.h, ctypes.byref(g), B, _ptr(w), _ptr(ct_in), _ptr(r), _ptr(out),
                                         _stream(stream)))
+        return out
+
+    def mod_switch(self, ct, L_out: int, out=None, stream=None) -> torch.Tensor:
+        """Ciphertexts [..., 2, L, N] -> [..., 2, L_out, N] under the first L_out primes."""
+        if ct.shape[-3:] != (2, self.L, self.N):
+            raise FlashError(f"ct: expected [..., 2, {self.L}, {self.N}], got {tuple(ct.shape)}")
+        n = ct.numel() // (2 * self.L * self.N)
+        if out is None:
+            out = torch.empty(tuple(ct.shape[:-2]) + (L_out, self.N), dtype=ct.dtype, device=ct.device)
+        _check(_lib.fl_mod_switch(self.h, n, _ptr(ct), L_out, _ptr(out), _stream(stream)))
         return out
 
     def mask_to_share(self, ct, r, stream=None) -> torch.Tensor:
