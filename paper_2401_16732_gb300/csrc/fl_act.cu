@@ -130,10 +130,10 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const uint4 p = __ldg(P4 + j);
-      v[4 * j + 0] = barrett64((uint64_t)csub(csub(v[4 * j + 0], two_q), q) * p.x, q, lc.mu);
-      v[4 * j + 1] = barrett64((uint64_t)csub(csub(v[4 * j + 1], two_q), q) * p.y, q, lc.mu);
-      v[4 * j + 2] = barrett64((uint64_t)csub(csub(v[4 * j + 2], two_q), q) * p.z, q, lc.mu);
-      v[4 * j + 3] = barrett64((uint64_t)csub(csub(v[4 * j + 3], two_q), q) * p.w, q, lc.mu);
+      v[4 * j + 0] = red64((uint64_t)csub(csub(v[4 * j + 0], two_q), q) * p.x, lc);
+      v[4 * j + 1] = red64((uint64_t)csub(csub(v[4 * j + 1], two_q), q) * p.y, lc);
+      v[4 * j + 2] = red64((uint64_t)csub(csub(v[4 * j + 2], two_q), q) * p.z, lc);
+      v[4 * j + 3] = red64((uint64_t)csub(csub(v[4 * j + 3], two_q), q) * p.w, lc);
     }
     pass32<true>(v, tgi, T, lt, q, two_q);
 #pragma unroll

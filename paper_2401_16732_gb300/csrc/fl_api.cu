@@ -150,6 +150,8 @@ void build_tables(uint32_t q, int N, int logN, uint32_t* Tw, fl::LimbConst& lc, 
   lc.last_w = (uint32_t)mulmod(iv[1], lc.n_inv, q);
   lc.last_w_sh = shoup(lc.last_w, q);
   lc.mu = ~0ull / q;
+  lc.r32 = (uint32_t)((1ull << 32) % q);
+  lc.r32_sh = shoup(lc.r32, q);
 }
 
 GeomDims dims_of(const fl_conv_geom& g) {

@@ -35,6 +35,7 @@ struct LimbConst {
   uint32_t last_w, last_w_sh;  // psi^-(N/2) * N^-1: last inverse stage
   uint32_t delta, delta_sh;    // Delta mod q (Delta = floor(Q / t))
   uint64_t mu;                 // floor(2^64 / q)
+  uint32_t r32, r32_sh;        // 2^32 mod q and its Shoup companion
 };
 
 struct CtxConst {
@@ -71,6 +72,18 @@ __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t q, uint64_t m
   uint64_t qh = __umul64hi(x, mu);
   uint32_t r = (uint32_t)x - (uint32_t)qh * q;  // true remainder < 2q, exact mod 2^32
   return csub(r, q);
+}
+
+// x mod q for any 64-bit x, in [0, q): with x = hi*2^32 + lo,
+// x = hi*(2^32 mod q) + lo (mod q).  One Shoup product on the multiply pipe
+// plus conditional subtractions on the ALU pipe (q in (2^29, 2^30), so
+// lo < 2^32 < 8q and 4q fits 32 bits).
+__device__ __forceinline__ uint32_t red64(uint64_t x, const LimbConst& lc) {
+  const uint32_t q = lc.q, two_q = lc.two_q;
+  const uint32_t a = shoup_mul((uint32_t)(x >> 32), lc.r32, lc.r32_sh, q);  // [0, 2q)
+  const uint32_t lo = (uint32_t)x;
+  const uint32_t b = csub(csub(lo, 2 * two_q), two_q);                      // [0, 2q)
+  return csub(csub(a + b, two_q), q);                                        // [0, 4q) -> [0, q)
 }
 
 __device__ __forceinline__ void ct_bfly(uint32_t& X, uint32_t& Y, uint32_t w, uint32_t wsh,

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
 // --------------------------------------------------------------------------
 // Fused contraction + inverse NTT (+ mask).  Grid (B*bands, Cout, L).
 //   Y_c[u] = sum_g W[l][i][g][u] * C[b][band*G+g][c][l][u]  mod q_l
-// accumulated in 64 bits (products < 2^60; a Barrett fold every 16 terms),
+// accumulated in 64 bits (products < 2^60; a fold every 16 terms),
 // reduced once, inverse-transformed in shared memory and stored with
 // streaming stores; c0 optionally gets + Delta_l * r[u].
 // --------------------------------------------------------------------------
@@ -110,16 +110,16 @@ __device__ __forceinline__ void conv_item(const uint32_t* __restrict__ w_hat, co
       if (((g + 1) & 15) == 0 && g + 1 < cd.G) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          a0[j] = barrett64(a0[j], lc.q, lc.mu);
-          a1[j] = barrett64(a1[j], lc.q, lc.mu);
+          a0[j] = red64(a0[j], lc);
+          a1[j] = red64(a1[j], lc);
         }
       }
     }
     const int pu = pad(4 * v);  // the 4 slots share one 32-word row
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      s0[pu + j] = barrett64(a0[j], lc.q, lc.mu);
-      s1[pu + j] = barrett64(a1[j], lc.q, lc.mu);
+      s0[pu + j] = red64(a0[j], lc);
+      s1[pu + j] = red64(a1[j], lc);
     }
   }
   __syncthreads();
@@ -138,7 +138,7 @@ __device__ __forceinline__ void conv_item(const uint32_t* __restrict__ w_hat, co
 
 // Fused contraction + inverse NTT (+ mask).  Grid (B*bands, Cout, L).
 //   Y_c[u] = sum_g W[l][i][g][u] * C[b][band*G+g][c][l][u]  mod q_l
-// accumulated in 64 bits (products < 2^60; a Barrett fold every 16 terms),
+// accumulated in 64 bits (products < 2^60; a fold every 16 terms),
 // reduced once, inverse-transformed in shared memory and stored with
 // streaming stores; c0 optionally gets + Delta_l * r[u].
 template <int LOGN, bool MASK>
