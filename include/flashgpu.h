@@ -51,6 +51,7 @@ extern "C" {
 #define FL_ERR_SHAPE (-2) /* geometry that the packing cannot represent */
 #define FL_ERR_CUDA (-3)  /* a CUDA runtime call failed (message has the reason) */
 #define FL_ERR_OOM (-4)   /* the context's own tables could not be allocated */
+#define FL_ERR_TIMEOUT (-5) /* a bounded device-side wait gave up (kernel returned early) */
 #define FL_MAX_LIMBS 4
 
 typedef struct fl_ctx fl_ctx; /* opaque: parameters + device twiddle tables */
@@ -267,8 +268,20 @@ int fl_ctx_set_stack_kernel(fl_ctx *ctx, int kernel);
 int fl_ctx_get_stack_kernel(const fl_ctx *ctx);
 
 /* Synchronise `stream` and read the error word of a workspace last used by
- * fl_he_conv2d_stack (0: no internal wait ran out). */
+ * fl_he_conv2d_stack into *error_host.  Returns FL_OK when the word is 0 and
+ * FL_ERR_TIMEOUT when an internal wait ran out: bit 0 means the contraction
+ * team gave up, bit 1 the inverse-NTT team.  The kernel then returned early,
+ * its outputs are incomplete and the context stays usable. */
 int fl_stack_error(const void *workspace_dev, void *stream, uint64_t *error_host);
+
+/* Self-test of the device-side wait bound (failure detection without a
+ * fault).  It launches one CTA that waits, through the persistent kernel's
+ * bounded mbarrier wait, on a barrier that nothing completes.  The wait gives
+ * up after its 2 s limit, sets bit 2 of an error word and returns, and the
+ * call reads the word into *error_host.  The expected result is
+ * FL_ERR_TIMEOUT with bit 2 set; FL_OK would mean the bound does not work.
+ * It allocates 8 bytes of device memory and synchronises `stream`. */
+int fl_selftest_wait_timeout(void *stream, uint64_t *error_host);
 
 /* ---- Output volume ---- */
 

@@ -755,7 +755,23 @@ int fl_stack_error(const void* workspace_dev, void* stream, uint64_t* error_host
   e = cudaMemcpy(&v, (const unsigned long long*)workspace_dev + 1, sizeof v, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "error word read");
   *error_host = v;
-  return FL_OK;
+  return v ? fail(FL_ERR_TIMEOUT, "a bounded device wait gave up (error word 0x%llx)", v) : FL_OK;
+}
+
+int fl_selftest_wait_timeout(void* stream, uint64_t* error_host) {
+  if (!error_host) return fail(FL_ERR_ARG, "null pointer");
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof *d);
+  if (e != cudaSuccess) return cuda_fail(e, "error word");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long v = 0;
+  if ((e = cudaMemsetAsync(d, 0, sizeof *d, st)) == cudaSuccess &&
+      (e = fl::launch_wait_timeout_probe(d, st)) == cudaSuccess && (e = cudaStreamSynchronize(st)) == cudaSuccess)
+    e = cudaMemcpy(&v, d, sizeof v, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+  *error_host = v;
+  return v ? fail(FL_ERR_TIMEOUT, "the probe's wait gave up as designed (error word 0x%llx)", v) : FL_OK;
 }
 
 int fl_ntt_forward(fl_ctx* ctx, int n, uint32_t* data_dev, void* stream) {

@@ -87,6 +87,7 @@ struct NttSegs {  // forward NTT of several contiguous row ranges in one launch
 
 cudaError_t launch_setup(int logn);
 cudaError_t launch_stack_setup(int logn);
+cudaError_t launch_wait_timeout_probe(unsigned long long* err, cudaStream_t st);
 cudaError_t launch_ntt_multi_setup(int logn);
 int stack_ctas_per_sm(int logn);
 cudaError_t launch_stack(int logn, const StackArgs& a, unsigned long long* ctl, const uint32_t* tw,

@@ -57,11 +57,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
                : "memory");
 }
 
-// Wait for the phase with the given parity to complete; false on timeout.
+// Wait for the phase with the given parity to complete; false on timeout
+// (kWaitLimitNs of wall clock, or kWaitMaxPolls polls, whichever comes first).
+constexpr unsigned kWaitMaxPolls = 1u << 26;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
   const unsigned long long t0 = globaltimer();
-  while (true) {
+  for (unsigned polls = 0; polls < kWaitMaxPolls; ++polls) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
@@ -72,6 +74,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
     if (done) return true;
     if (globaltimer() - t0 > kWaitLimitNs) return false;
   }
+  return false;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
@@ -418,6 +421,24 @@ static cudaError_t stack_launch(const StackArgs& a, unsigned long long* ctl, con
                                 int grid, cudaStream_t st) {
   using C = StackCfg<LOGN>;
   k_stack<LOGN, C::PT, C::PAR, C::DEPTH, C::GS, C::MINB><<<grid, C::THREADS, stack_smem<LOGN>(), st>>>(a, ctl, tw, cc);
+  return cudaGetLastError();
+}
+
+// Self-test of the bounded wait: an mbarrier that expects one arrival which
+// never comes.  The wait must give up, set bit 2 of the error word and
+// return, leaving the context usable.
+__global__ void k_wait_timeout_probe(unsigned long long* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) atomicOr(err, 4ull);
+}
+
+cudaError_t launch_wait_timeout_probe(unsigned long long* err, cudaStream_t st) {
+  k_wait_timeout_probe<<<1, 32, 0, st>>>(err);
   return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
                       "(there is no CPU fallback)")
 _lib = ctypes.CDLL(LIB_PATH)
 
-FL_OK, FL_ERR_ARG, FL_ERR_SHAPE, FL_ERR_CUDA, FL_ERR_OOM = 0, -1, -2, -3, -4
+FL_OK, FL_ERR_ARG, FL_ERR_SHAPE, FL_ERR_CUDA, FL_ERR_OOM, FL_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 FL_STACK_PER_LAYER, FL_STACK_PERSISTENT, FL_STACK_QUEUE = 0, 1, 2
 FL_NOALLOC_SCRATCH_BYTES = 16 << 20
 FL_STACK_MAX_LAYERS = 64
@@ -83,6 +83,7 @@ _SIGS = {
     "fl_x2x_round1": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
     "fl_x2x_round2": ([_vp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "fl_repack_outputs": ([_gp, _gp, _i, _vp, _vp, _vp], _i),
+    "fl_selftest_wait_timeout": ([_vp, ctypes.POINTER(ctypes.c_uint64)], _i),
     "fl_ntt_forward": ([_vp, _i, _vp, _vp], _i),
     "fl_ntt_inverse": ([_vp, _i, _vp, _vp], _i),
 }
@@ -132,6 +133,13 @@ def _dev_u32(t: torch.Tensor, shape, name):
     if tuple(t.shape) != tuple(shape):
         raise FlashError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
     return t
+
+
+def selftest_wait_timeout(stream=None) -> tuple[int, int]:
+    """Run the bounded-wait self-test; returns (status, error word)."""
+    v = ctypes.c_uint64()
+    rc = _lib.fl_selftest_wait_timeout(_stream(stream), ctypes.byref(v))
+    return rc, v.value
 
 
 def repack_outputs(prev: ConvGeom, nxt: ConvGeom, src, out=None, stream=None) -> torch.Tensor:
@@ -289,7 +297,9 @@ class Context:
 
     def stack_error(self, workspace, stream=None) -> int:
         v = ctypes.c_uint64()
-        _check(_lib.fl_stack_error(_ptr(workspace), _stream(stream), ctypes.byref(v)))
+        rc = _lib.fl_stack_error(_ptr(workspace), _stream(stream), ctypes.byref(v))
+        if rc not in (FL_OK, FL_ERR_TIMEOUT):
+            _check(rc)
         return v.value
 
     def he_conv2d_mask_noalloc(self, g, w_hat, ct_in, r, out, stream=None) -> torch.Tensor:

@@ -11,6 +11,12 @@ memory allows (admission by the request's peak live set: the largest layer's
 inputs, NTT workspace, masks and outputs).  Latency is arrival to the round
 in which the request's last layer is done (outputs resident, ready to send).
 
+Host-side failure handling (no device fault is involved): a request whose
+peak live set exceeds the whole memory budget is rejected at admission
+instead of being admitted alone; `cancel(rid)` withdraws a request, pending
+or active, before the next round and releases its reservation; a stack
+kernel that reports a timed-out wait raises before any later round runs.
+
 Inputs of every (request, layer) are fresh synthetic encryptions drawn on the
 device from a seed (request id, layer), so any (request, layer) can be
 recomputed by the oracle and results do not depend on which other requests
@@ -49,6 +55,7 @@ class Request:
     next_layer: int = 0
     admitted: float | None = None
     done: float | None = None
+    error: str | None = None
     outputs: dict = field(default_factory=dict)  # layer -> output tensor, when kept
 
 
@@ -102,6 +109,13 @@ class Server:
         self.layer_images = 0
         self.peak_reserved = 0
         self.peak_active = 0
+        self.rejected = []    # requests refused at admission (q.error says why)
+        self.cancelled = []   # requests withdrawn by cancel()
+        self._cancel = set()
+
+    def cancel(self, rid: int):
+        """Withdraw request `rid` before the next round (pending or active)."""
+        self._cancel.add(rid)
 
     # -- one round: the next layer of every active request ----------------
     def _round(self, active):
@@ -141,19 +155,39 @@ class Server:
         self.rounds += 1
         return now_done
 
-    def run(self, requests: list[Request], realtime: bool = True, t0: float | None = None):
+    def run(self, requests: list[Request], realtime: bool = True, t0: float | None = None, on_round=None):
         """Serve `requests` (sorted by arrival).  With realtime, a request can
-        only be admitted once the wall clock has passed its arrival time."""
+        only be admitted once the wall clock has passed its arrival time.
+        `on_round(server, finished_so_far)` runs after every round."""
         pending = sorted(requests, key=lambda q: q.arrival)
         active, finished = [], []
         reserved = 0
         start = time.perf_counter() if t0 is None else t0
+
+        def drop_cancelled():
+            nonlocal reserved
+            for q in [q for q in pending + active if q.rid in self._cancel]:
+                if q in active:
+                    active.remove(q)
+                    reserved -= q.reserved
+                else:
+                    pending.remove(q)
+                q.error = "cancelled"
+                self.cancelled.append(q)
+            self._cancel.clear()
+
         while pending or active:
+            drop_cancelled()
             now = time.perf_counter() - start
             # admit in arrival order while the memory budget allows
             while pending and (not realtime or pending[0].arrival <= now):
                 q = pending[0]
                 need = self.res[q.model].peak_bytes(q.B)
+                if need > self.mem_budget:
+                    pending.pop(0)
+                    q.error = f"needs {need} bytes of device memory, above the budget of {self.mem_budget}"
+                    self.rejected.append(q)
+                    continue
                 if reserved + need > self.mem_budget and active:
                     break
                 pending.pop(0)
@@ -164,7 +198,8 @@ class Server:
                 self.peak_reserved = max(self.peak_reserved, reserved)
                 self.peak_active = max(self.peak_active, len(active))
             if not active:
-                time.sleep(max(0.0, min(pending[0].arrival - now, 0.01)))
+                if pending:
+                    time.sleep(max(0.0, min(pending[0].arrival - now, 0.01)))
                 continue
             done = self._round(active)
             now = time.perf_counter() - start
@@ -173,6 +208,8 @@ class Server:
                 reserved -= q.reserved
                 active.remove(q)
                 finished.append(q)
+            if on_round is not None:
+                on_round(self, finished)
         wall = time.perf_counter() - start
         return finished, wall
 

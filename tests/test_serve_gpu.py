@@ -57,3 +57,59 @@ def test_admission_respects_the_memory_budget():
     assert 2 <= srv.peak_active < 6  # requests overlap, but the budget holds the rest back
     st = serve.latency_stats(finished)
     assert st["p50_ms"] <= st["p99_ms"]
+
+
+def test_oversized_request_is_rejected_not_admitted():
+    """A request whose peak live set exceeds the whole budget is refused at
+    admission (host-side fault: an admission request larger than memory);
+    the others are served."""
+    from paper_2401_16732_gb300 import serve
+    srv = serve.Server(models())
+    srv.mem_budget = srv.res["a"].peak_bytes(2) + srv.res["b"].peak_bytes(2)
+    big = serve.Request(rid=99, model="a", B=64, arrival=0.0, seed=4)
+    reqs = [serve.Request(rid=i, model="ab"[i % 2], B=1, arrival=0.0, seed=4) for i in range(4)] + [big]
+    finished, _ = srv.run(reqs, realtime=False)
+    assert sorted(q.rid for q in finished) == [0, 1, 2, 3]
+    assert srv.rejected == [big] and "above the budget" in big.error
+    assert big.done is None and big.admitted is None
+
+
+def test_cancel_mid_queue_releases_the_request():
+    """Cancelling between rounds withdraws a pending and an active request
+    (host-side fault: a client that goes away); the rest finish, with the
+    same outputs as without the cancellation."""
+    from paper_2401_16732_gb300 import serve
+    reqs = [serve.Request(rid=i, model="a", B=1, arrival=0.0, seed=4) for i in range(5)]
+    keep = {(q.rid, li) for q in reqs for li in range(2)}
+    srv = serve.Server(models(), keep_outputs=keep)
+    srv.mem_budget = 2 * srv.res["a"].peak_bytes(1)  # two at a time: the rest wait in the queue
+
+    def on_round(server, finished):
+        if server.rounds == 1:
+            server.cancel(0)   # active, one layer done
+            server.cancel(4)   # still pending
+    finished, _ = srv.run(reqs, realtime=False, on_round=on_round)
+    assert sorted(q.rid for q in finished) == [1, 2, 3]
+    assert sorted(q.rid for q in srv.cancelled) == [0, 4]
+    assert all(q.error == "cancelled" and q.done is None for q in srv.cancelled)
+    ref = serve.Server(models(), keep_outputs={(2, 0), (2, 1)})
+    alone = serve.Request(rid=2, model="a", B=1, arrival=0.0, seed=4)
+    ref.run([alone], realtime=False)
+    q2 = next(q for q in finished if q.rid == 2)
+    assert torch.equal(q2.outputs[1], alone.outputs[1])
+
+
+def test_device_wait_bound_reports_timeout():
+    """Failure detection on the GPU without a fault: a wait on a barrier that
+    nothing completes gives up after its bound, the call reports
+    FL_ERR_TIMEOUT with the probe's bit, and the context keeps working."""
+    from paper_2401_16732_gb300 import flashgpu, synth
+    rc, word = flashgpu.selftest_wait_timeout()
+    assert rc == flashgpu.FL_ERR_TIMEOUT and word == 4
+    assert "gave up" in flashgpu.fl_last_error()
+    c = flashgpu.Context(2048, 1)
+    x = torch.from_numpy(synth.raw_ciphertexts(3, c.primes, (2, 1, 2048)).view(np.int32)).cuda()
+    y = x.clone()
+    c.ntt_forward(y)
+    c.ntt_inverse(y)
+    assert torch.equal(x, y)
