@@ -387,6 +387,14 @@ int fl_x2x_round2(fl_ctx *ctx, int n, const uint32_t *prep_dev, const uint32_t *
 int fl_repack_outputs(const fl_conv_geom *prev, const fl_conv_geom *next, int B, const uint32_t *src_dev,
                       uint32_t *dst_dev, void *stream);
 
+/* Measured multiply-add rate of a warp-level tensor-core instruction on the
+ * current device: kind 0 = mma.sync m16n8k32 u8 x u8 -> s32, kind 1 =
+ * mma.sync m16n8k16 bf16 x bf16 -> f32.  Four 256-thread CTAs per SM, each
+ * warp issuing `iters` rounds of 8 independent MMAs on registers.  This is
+ * the ceiling of a byte-split contraction built on them (tcgen05 has no
+ * integer kind on sm_103a). */
+int fl_probe_mma_rate(int kind, int iters, double *macs_per_s);
+
 /* ---- Building blocks, exposed for tests ---- */
 
 /* In-place negacyclic NTT / inverse NTT of n RNS polynomials data_dev

@@ -83,6 +83,7 @@ _SIGS = {
     "fl_x2x_round1": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
     "fl_x2x_round2": ([_vp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "fl_repack_outputs": ([_gp, _gp, _i, _vp, _vp, _vp], _i),
+    "fl_probe_mma_rate": ([_i, _i, ctypes.POINTER(ctypes.c_double)], _i),
     "fl_selftest_wait_timeout": ([_vp, ctypes.POINTER(ctypes.c_uint64)], _i),
     "fl_ntt_forward": ([_vp, _i, _vp, _vp], _i),
     "fl_ntt_inverse": ([_vp, _i, _vp, _vp], _i),
@@ -133,6 +134,13 @@ def _dev_u32(t: torch.Tensor, shape, name):
     if tuple(t.shape) != tuple(shape):
         raise FlashError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
     return t
+
+
+def probe_mma_rate(kind: int, iters: int = 4096) -> float:
+    """Measured multiply-adds/s of mma.sync u8 (kind 0) or bf16 (kind 1)."""
+    v = ctypes.c_double()
+    _check(_lib.fl_probe_mma_rate(kind, iters, ctypes.byref(v)))
+    return v.value
 
 
 def selftest_wait_timeout(stream=None) -> tuple[int, int]:
