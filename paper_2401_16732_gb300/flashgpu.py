@@ -269,13 +269,15 @@ class Context:
     # -- many layers in one launch ------------------------------------------
     def stack_layers(self, specs):
         """specs: list of dicts with keys g, w_hat, ct_in, out and optional r.
-        Returns the ctypes array fl_he_conv2d_stack takes (keeps the geometry
-        objects alive through the returned array's `_keep`)."""
+        Returns the ctypes array fl_he_conv2d_stack takes.  The array holds
+        raw device pointers, so it keeps every geometry and tensor it points
+        to alive through its `_keep` list: a tensor built inline in `specs`
+        is not freed (and its memory reused) while the array exists."""
         arr = (StackLayer * len(specs))()
         keep = []
         for k, sp in enumerate(specs):
             g = sp["g"]
-            keep.append(g)
+            keep.extend([g, sp["w_hat"], sp["ct_in"], sp["out"], sp.get("r")])
             arr[k].geom = ctypes.pointer(g)
             arr[k].B = sp["ct_in"].shape[0]
             arr[k].w_hat_dev = sp["w_hat"].data_ptr()

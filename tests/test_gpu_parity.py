@@ -385,3 +385,28 @@ def test_stack_empty(fg):
     ws = torch.empty(64, dtype=torch.int32, device="cuda")
     c.he_conv2d_stack(arr, ws)
     assert c.stack_error(ws) == 0
+
+
+def test_stack_keeps_inline_tensors_alive(fg):
+    """A mask built inline in the layer specs must stay allocated while the
+    layer array exists: otherwise the workspace allocated next reuses its
+    memory and every masked output differs."""
+    N, L = 4096, 2
+    c = ctx(fg, N, L)
+    g = c.geom(16, 16, 16, 16, 3, 1, 1)
+    w = synth.weights(90, (16, 16, 3, 3))
+    ct = dev(synth.raw_ciphertexts(90, c.primes, (1, g.n_in, 2, L, N)))
+    r = synth.masks(90, (1, g.n_out, N), T)
+    wh = c.encode_weights(g, dev(w, torch.int8))
+    want = c.he_conv2d(g, wh, ct, r=dev(r))
+    for kernel in (fg.FL_STACK_PER_LAYER, fg.FL_STACK_QUEUE, fg.FL_STACK_PERSISTENT):
+        c.stack_kernel = kernel
+        outs = [torch.zeros_like(want) for _ in range(2)]
+        arr = c.stack_layers([{"g": g, "w_hat": wh, "ct_in": ct, "r": dev(r), "out": o} for o in outs])
+        ws = c.stack_workspace(arr)  # would reuse the masks' memory if they had been freed
+        ws.fill_(-1)
+        c.he_conv2d_stack(arr, ws)
+        assert c.stack_error(ws) == 0
+        for o in outs:
+            assert torch.equal(o, want)
+    c.stack_kernel = fg.FL_STACK_PER_LAYER
