@@ -196,6 +196,11 @@ int check_ptrs(std::initializer_list<const void*> ps) {
 
 int launched(cudaError_t e, const char* what) { return e == cudaSuccess ? FL_OK : cuda_fail(e, what); }
 
+// Row and CTA counts are passed to launchers as int: reject larger jobs.
+int rows_ok(long long rows, const char* what) {
+  return rows <= 0x7fffffffLL ? FL_OK : fail(FL_ERR_ARG, "%s: %lld rows exceed one launch", what, rows);
+}
+
 }  // namespace
 
 namespace fl {
@@ -381,6 +386,7 @@ int fl_encrypt(fl_ctx* ctx, const uint32_t* sk_dev, const fl_conv_geom* geom, in
   if ((rc = check_ptrs({sk_dev, a_dev, ct_dev})) || !x_dev || !e_dev)
     return rc ? rc : fail(FL_ERR_ARG, "null input");
   cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = rows_ok((long long)B * geom->n_in * 2 * ctx->L, "encrypt"))) return rc;
   const int n = B * geom->n_in, L = ctx->L, N = ctx->N;
   // c1 = a
   cudaError_t e = cudaMemcpy2DAsync(ct_dev + (size_t)L * N, (size_t)2 * L * N * 4, a_dev, (size_t)L * N * 4,
@@ -404,6 +410,7 @@ int fl_encrypt_online(fl_ctx* ctx, const fl_conv_geom* geom, int B, const int32_
   if (B < 0) return fail(FL_ERR_ARG, "B=%d", B);
   if (B == 0) return FL_OK;
   if ((rc = check_ptrs({enc0_dev, ct_dev})) || !x_dev) return rc ? rc : fail(FL_ERR_ARG, "null input");
+  if ((rc = rows_ok((long long)B * geom->n_in * 2 * ctx->L, "online encryption"))) return rc;
   return launched(fl::launch_enc_online(enc0_dev, ct_dev, x_dev, dims_of(*geom), B * geom->n_in, ctx->N,
                                         ctx->cc, (cudaStream_t)stream),
                   "online encrypt");
@@ -419,7 +426,8 @@ int fl_decrypt(fl_ctx* ctx, const uint32_t* sk_dev, int n, const uint32_t* ct_de
   if ((rc = check_ctx(ctx))) return rc;
   if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
   if (n == 0) return FL_OK;
-  if ((rc = check_ptrs({sk_dev, ct_dev, m_dev, workspace_dev}))) return rc;
+  if ((rc = check_ptrs({sk_dev, ct_dev, m_dev, workspace_dev})) || (rc = rows_ok((long long)n * 2 * ctx->L, "decrypt")))
+    return rc;
   if (workspace_bytes < fl_decrypt_workspace_bytes(ctx, n))
     return fail(FL_ERR_ARG, "workspace %zu bytes, need %zu", workspace_bytes, fl_decrypt_workspace_bytes(ctx, n));
   cudaStream_t st = (cudaStream_t)stream;
@@ -466,6 +474,7 @@ int fl_encode_weights(fl_ctx* ctx, const fl_conv_geom* geom, const int8_t* w_dev
   if (e != cudaSuccess) return cuda_fail(e, "weights memset");
   if ((rc = launched(fl::launch_w_scatter(w_dev, w_hat_dev, dims_of(*geom), ctx->N, ctx->cc, st), "w scatter")))
     return rc;
+  if ((rc = rows_ok((long long)ctx->L * geom->Cout * geom->G, "weight rows"))) return rc;
   const int rows = ctx->L * geom->Cout * geom->G;
   return launched(fl::launch_ntt_fwd(ctx->logN, rows, w_hat_dev, rows, 0, w_hat_dev, rows, 0, geom->Cout * geom->G,
                                      ctx->tw, ctx->cc, st),
@@ -483,7 +492,8 @@ static int conv_checks(fl_ctx* ctx, const fl_conv_geom* geom, int B, size_t work
   const size_t need = fl_he_conv2d_workspace_bytes(ctx, geom, B);
   if (workspace_bytes < need) return fail(FL_ERR_ARG, "workspace %zu bytes, need %zu", workspace_bytes, need);
   if ((long long)B * geom->bands > 0x7fffffff) return fail(FL_ERR_ARG, "batch too large");
-  return FL_OK;
+  if ((rc = rows_ok((long long)B * geom->n_in * 2 * ctx->L, "input rows"))) return rc;
+  return rows_ok((long long)B * geom->n_out * 2 * ctx->L, "output rows");
 }
 
 static int stage_ntt(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* ct_in_dev, void* ws,
@@ -792,7 +802,7 @@ int fl_ntt_forward(fl_ctx* ctx, int n, uint32_t* data_dev, void* stream) {
   if ((rc = check_ctx(ctx))) return rc;
   if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
   if (n == 0) return FL_OK;
-  if ((rc = check_ptrs({data_dev}))) return rc;
+  if ((rc = check_ptrs({data_dev})) || (rc = rows_ok((long long)n * ctx->L, "ntt"))) return rc;
   const int rows = n * ctx->L;
   return launched(fl::launch_ntt_fwd(ctx->logN, rows, data_dev, rows, 0, data_dev, rows, 0, 1, ctx->tw, ctx->cc,
                                      (cudaStream_t)stream),
@@ -804,7 +814,7 @@ int fl_ntt_inverse(fl_ctx* ctx, int n, uint32_t* data_dev, void* stream) {
   if ((rc = check_ctx(ctx))) return rc;
   if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
   if (n == 0) return FL_OK;
-  if ((rc = check_ptrs({data_dev}))) return rc;
+  if ((rc = check_ptrs({data_dev})) || (rc = rows_ok((long long)n * ctx->L, "intt"))) return rc;
   return launched(fl::launch_ntt_inv(ctx->logN, n * ctx->L, data_dev, ctx->tw, ctx->cc, (cudaStream_t)stream),
                   "intt");
 }
@@ -857,7 +867,8 @@ int fl_x2x_prepare(fl_ctx* ctx, int n, const uint32_t* r_dev, const uint32_t* v_
   if ((rc = check_ctx(ctx)) || (rc = check_batch(ctx))) return rc;
   if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
   if (n == 0) return FL_OK;
-  if ((rc = check_ptrs({r_dev, v_dev, prep_dev}))) return rc;
+  if ((rc = check_ptrs({r_dev, v_dev, prep_dev})) || (rc = rows_ok((long long)n * (ctx->L + 2), "x2x prepare")))
+    return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int L = ctx->L, N = ctx->N;
   const long long stride = (long long)(L + 2) * N;
@@ -881,7 +892,8 @@ int fl_x2x_round1(fl_ctx* ctx, int n, const uint32_t* prep_dev, const uint32_t* 
   if ((rc = check_ctx(ctx)) || (rc = check_batch(ctx))) return rc;
   if (n < 0) return fail(FL_ERR_ARG, "n=%d", n);
   if (n == 0) return FL_OK;
-  if ((rc = check_ptrs({prep_dev, ct_z_dev, ct_out_dev}))) return rc;
+  if ((rc = check_ptrs({prep_dev, ct_z_dev, ct_out_dev})) || (rc = rows_ok((long long)n * 2 * ctx->L, "x2x round 1")))
+    return rc;
   return launched(fl::launch_x2x_round1(ctx->logN, n, prep_dev, ct_z_dev, ct_out_dev, ctx->tw, ctx->cc,
                                         (cudaStream_t)stream),
                   "x2x round 1");

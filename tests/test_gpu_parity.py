@@ -298,6 +298,11 @@ def test_empty_batch_and_argument_errors(fg):
     assert lib.fl_he_conv2d(c.h, ctypes.byref(g3), 1, fg._ptr(wh), fg._ptr(ct), fg._ptr(out), fg._ptr(ws),
                             ws.numel() * 4, None) == fg.FL_ERR_SHAPE
     assert "inconsistent" in fg.fl_last_error()
+    # a batch whose row count does not fit one launch is refused before any pointer is used
+    huge = (1 << 31) // (g.n_in * 2 * 2) + 1
+    assert lib.fl_he_conv2d(c.h, ctypes.byref(g), huge, None, None, None, None, ctypes.c_size_t(-1).value,
+                            None) == fg.FL_ERR_ARG
+    assert "exceed one launch" in fg.fl_last_error()
     with pytest.raises(fg.FlashError):
         fg.Context(1000, 2)
     with pytest.raises(fg.FlashError):
