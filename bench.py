@@ -363,12 +363,15 @@ def run_gpu(args, wl, rank, world, local_rank):
             if events is not None:
                 events[2].record(stream)
             return
+        if events is None:
+            # one call: the conv kernel can follow the input NTT as a
+            # programmatic dependent launch
+            ctx.he_conv2d_stack(arr_, ws, stream=stream, stage="all")
+            return
         ctx.he_conv2d_stack(arr_, ws, stream=stream, stage="ntt")
-        if events is not None:
-            events[1].record(stream)
+        events[1].record(stream)
         ctx.he_conv2d_stack(arr_, ws, stream=stream, stage="run")
-        if events is not None:
-            events[2].record(stream)
+        events[2].record(stream)
 
     # capture one step in a CUDA graph (40 launches for ResNet-18)
     with torch.cuda.stream(stream):

@@ -507,8 +507,10 @@ static int stage_ntt(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_
 static int stage_conv(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_hat_dev, const void* ws,
                       const uint32_t* r_dev, uint32_t* ct_out_dev, cudaStream_t st) {
   fl::ConvDims cd{geom->Cout, geom->G, geom->n_in, geom->n_out, geom->bands};
+  // launched as a programmatic dependent of the previous grid in `st` (the
+  // input NTT when called from he_conv2d_impl); the kernel waits for it
   return launched(fl::launch_conv_intt(ctx->logN, B, cd, w_hat_dev, (const uint32_t*)ws, ct_out_dev, r_dev, ctx->tw,
-                                       ctx->cc, st),
+                                       ctx->cc, st, true),
                   "contraction + intt");
 }
 
@@ -696,6 +698,12 @@ static int stack_impl(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, v
   a.n_items = items;
   cudaStream_t st = (cudaStream_t)stream;
   unsigned long long* ctl = (unsigned long long*)workspace_dev;
+  cudaError_t e;
+  // queue head and error word: zeroed before the input NTT, so that the
+  // queue kernel can follow the NTT directly as a programmatic dependent
+  if ((stages & 2) && ctx->stack_kernel == FL_STACK_QUEUE &&
+      (e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
+    return cuda_fail(e, "control reset");
   if ((stages & 1) && (rc = launched(fl::launch_ntt_multi(ctx->logN, segs, ctx->tw, ctx->cc, st), "stack input ntt")))
     return rc;
   if (!(stages & 2)) return FL_OK;
@@ -706,8 +714,8 @@ static int stack_impl(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, v
   // per-layer fused launches; the error word stays 0 (these kernels never
   // wait).  The layers are independent, so they fan out over the context's
   // auxiliary streams and join back into `st`.
-  cudaError_t e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return cuda_fail(e, "control reset");
+  if ((e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
+    return cuda_fail(e, "control reset");
   const int fan = a.n_layers < kAuxStreams ? a.n_layers : kAuxStreams;
   if (fan > 1) {
     if ((e = cudaEventRecord(ctx->fork_ev, st)) != cudaSuccess) return cuda_fail(e, "fork");
@@ -718,8 +726,9 @@ static int stack_impl(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, v
     const fl::StackLayer& y = a.layer[k];
     fl::ConvDims cd{y.Cout, y.G, y.n_in, y.n_out, y.bands};
     cudaStream_t sk = fan > 1 ? ctx->aux[k % fan] : st;
+    // on `st` itself (one layer) the launch follows the input NTT as a programmatic dependent
     if ((rc = launched(fl::launch_conv_intt(ctx->logN, y.BB / y.bands, cd, y.w_hat, y.c_hat, y.out, y.r, ctx->tw,
-                                            ctx->cc, sk),
+                                            ctx->cc, sk, fan <= 1),
                        "stack layer")))
       return rc;
   }

@@ -66,6 +66,14 @@ __device__ __forceinline__ uint32_t shoup_mul(uint32_t x, uint32_t w, uint32_t w
   return x * w - __umulhi(x, wsh) * q;  // [0, 2q)
 }
 
+// Programmatic dependent launch.  A grid launched with programmatic stream
+// serialization may start while its predecessor in the stream is finishing;
+// pdl_wait() blocks until that predecessor has completed and its writes are
+// visible (a no-op for an ordinary launch).  pdl_trigger() lets the dependent
+// grid be scheduled once every CTA of this grid has passed it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m) { return min(x, x - m); }  // x < 2m
 
 __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t q, uint64_t mu) {

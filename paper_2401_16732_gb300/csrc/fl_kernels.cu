@@ -32,6 +32,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
   constexpr int N = 1 << LOGN, T = N / 32;
   extern __shared__ uint32_t sm[];
   const int r = blockIdx.x, tid = threadIdx.x;
+  pdl_trigger();  // a dependent conv grid may be scheduled once every CTA is running
   const int l = (r / limb_div) % cc.L;
   const LimbConst lc = cc.limb[l];
   const uint32_t* x = src + ((size_t)(r / src_per) * src_stride + r % src_per) * N;
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
                 uint32_t* __restrict__ out, const uint32_t* __restrict__ r, ConvDims cd,
                 const uint32_t* __restrict__ tw, CtxConst cc) {
   extern __shared__ uint32_t sm[];
+  pdl_wait();  // the NTT-domain inputs come from the previous grid in the stream
   conv_item<LOGN>(w_hat, c_hat, out, MASK ? r : nullptr, cd, blockIdx.x, blockIdx.y, blockIdx.z, tw, cc, sm);
 }
 
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
     k_conv_queue(StackArgs a, unsigned long long* __restrict__ ctl, const uint32_t* __restrict__ tw, CtxConst cc) {
   extern __shared__ uint32_t sm[];
   __shared__ long long s_item;
+  pdl_wait();  // the NTT-domain inputs (and the zeroed queue head) come from earlier work in the stream
   for (;;) {
     if (threadIdx.x == 0) s_item = (long long)atomicAdd(ctl, 1ull);
     __syncthreads();  // also: every thread is done with the previous item's shared memory
@@ -427,18 +430,38 @@ cudaError_t launch_ntt_inv(int logn, int rows, uint32_t* data, const uint32_t* t
   return cudaGetLastError();
 }
 
+template <int LOGN, bool MASK>
+static cudaError_t conv_intt_launch(dim3 grid, size_t smem, bool pdl, const uint32_t* w_hat, const uint32_t* c_hat,
+                                    uint32_t* out, const uint32_t* r, const ConvDims& cd, const uint32_t* tw,
+                                    const CtxConst& cc, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(2 * (1 << LOGN) / 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_conv_intt<LOGN, MASK>, w_hat, c_hat, out, r, cd, tw, cc);
+}
+
+// pdl: the previous operation in `st` is the forward NTT of these inputs
+// (programmatic dependent launch; the kernel waits for it before reading).
 cudaError_t launch_conv_intt(int logn, int B, const ConvDims& cd, const uint32_t* w_hat,
                              const uint32_t* c_hat, uint32_t* out, const uint32_t* r,
-                             const uint32_t* tw, const CtxConst& cc, cudaStream_t st) {
+                             const uint32_t* tw, const CtxConst& cc, cudaStream_t st, bool pdl) {
   const int N = 1 << logn;
   const size_t smem = (size_t)2 * (N + N / 32) * 4;
   dim3 grid(B * cd.bands, cd.Cout, cc.L);
+  cudaError_t e = cudaSuccess;
   if (r) {
-    FL_DISPATCH(logn, (k_conv_intt<LG, true><<<grid, N / 16, smem, st>>>(w_hat, c_hat, out, r, cd, tw, cc)));
+    FL_DISPATCH(logn, (e = conv_intt_launch<LG, true>(grid, smem, pdl, w_hat, c_hat, out, r, cd, tw, cc, st)));
   } else {
-    FL_DISPATCH(logn, (k_conv_intt<LG, false><<<grid, N / 16, smem, st>>>(w_hat, c_hat, out, r, cd, tw, cc)));
+    FL_DISPATCH(logn, (e = conv_intt_launch<LG, false>(grid, smem, pdl, w_hat, c_hat, out, r, cd, tw, cc, st)));
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int LOGN>
@@ -451,16 +474,28 @@ static cudaError_t conv_queue_launch(const StackArgs& a, unsigned long long* ctl
   if (per_sm < 1) per_sm = 1;
   const long long slots = (long long)sms * per_sm;
   const int grid = (int)(a.n_items < slots ? a.n_items : slots);
-  k_conv_queue<LOGN><<<grid, 2 * (1 << LOGN) / 32, smem, st>>>(a, ctl, tw, cc);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(2 * (1 << LOGN) / 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_conv_queue<LOGN>, a, ctl, tw, cc);
 }
 
+// The queue head ctl[0] must be zero when the kernel starts: the caller
+// zeroes it earlier in `st` (before the stack's input NTT, so that the kernel
+// can follow the NTT as a programmatic dependent launch).
 cudaError_t launch_conv_queue(int logn, const StackArgs& a, unsigned long long* ctl, const uint32_t* tw,
                               const CtxConst& cc, int sms, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), st);
-  if (e != cudaSuccess || a.n_items == 0) return e;
-  FL_DISPATCH(logn, return conv_queue_launch<LG>(a, ctl, tw, cc, sms, st));
-  return cudaSuccess;
+  if (a.n_items == 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  FL_DISPATCH(logn, e = conv_queue_launch<LG>(a, ctl, tw, cc, sms, st));
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_pmul_intt(int logn, int mode, int n, uint32_t* ws, uint32_t* ct, const uint32_t* sk,

@@ -104,7 +104,7 @@ cudaError_t launch_conv_queue(int logn, const StackArgs& a, unsigned long long* 
                               const CtxConst& cc, int sms, cudaStream_t st);
 cudaError_t launch_conv_intt(int logn, int B, const ConvDims& cd, const uint32_t* w_hat,
                              const uint32_t* c_hat, uint32_t* out, const uint32_t* r,
-                             const uint32_t* tw, const CtxConst& cc, cudaStream_t st);
+                             const uint32_t* tw, const CtxConst& cc, cudaStream_t st, bool pdl = false);
 cudaError_t launch_pmul_intt(int logn, int mode, int n, uint32_t* ws, uint32_t* ct, const uint32_t* sk,
                              const int32_t* x, const int32_t* e, const GeomDims& gd,
                              const uint32_t* tw, const CtxConst& cc, cudaStream_t st);

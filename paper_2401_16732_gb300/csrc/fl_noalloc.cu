@@ -95,7 +95,8 @@ extern "C" int fl_he_conv2d_mask_noalloc(fl_ctx* ctx, const fl_conv_geom* geom, 
   if ((e = fl::launch_ntt_fwd(logN, rows, ct_in_dev, rows, 0, scratch, rows, 0, 1, tw, *cc, st)) != cudaSuccess)
     return fl::fail_msg(FL_ERR_CUDA, "input ntt: %s", cudaGetErrorString(e));
   fl::ConvDims cd{geom->Cout, geom->G, geom->n_in, geom->n_out, geom->bands};
-  if ((e = fl::launch_conv_intt(logN, B, cd, w_hat_dev, scratch, ct_out_dev, r_dev, tw, *cc, st)) != cudaSuccess)
+  if ((e = fl::launch_conv_intt(logN, B, cd, w_hat_dev, scratch, ct_out_dev, r_dev, tw, *cc, st, true)) !=
+      cudaSuccess)
     return fl::fail_msg(FL_ERR_CUDA, "contraction + intt: %s", cudaGetErrorString(e));
   return FL_OK;
 }

@@ -469,6 +469,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, 1024 >> (LOGN - 5))
   constexpr int N = 1 << LOGN, T = N / 32;
   extern __shared__ uint32_t sm[];
   const int r = blockIdx.x, tid = threadIdx.x;
+  pdl_trigger();  // the stack's conv grid may be scheduled once every CTA is running
   int s = 0;
   while (s + 1 < segs.n && r >= segs.row_begin[s + 1]) ++s;
   const int lr = r - segs.row_begin[s];
