@@ -748,7 +748,8 @@ def run_x2x(args, rank, world, local_rank):
 def run_serve(args, rank, world, local_rank):
     """Serving loop (continuous batching) on ResNet-18 (N=8192) and ResNet-50
     (N=16384) requests: Poisson arrivals at 200 requests/s, 70% / 30%, batch
-    size uniform in 1..8.  Reports served layers/s and per-request p50/p99."""
+    size uniform in 1..8.  Reports served layers/s and per-request p50/p99,
+    and the same loop at 12 requests/s, below one GPU's capacity."""
     import torch
 
     from paper_2401_16732_gb300 import serve
@@ -767,6 +768,16 @@ def run_serve(args, rank, world, local_rank):
     srv.layer_images = 0
     torch.cuda.synchronize()
     finished, wall = srv.run(reqs, realtime=True)
+    # the same loop below capacity (about half of what one GPU serves), where
+    # the latencies are service times rather than queueing
+    low_rate = 12.0
+    low = serve.poisson_requests(40, low_rate, mix, seed=args.seed + 200)
+    for q in low:
+        q.rid += 10_000
+    srv.keep = set()
+    low_done, low_wall = srv.run(low, realtime=True)
+    low_stats = serve.latency_stats(low_done)
+    low_li = sum(q.B * len(models[q.model].layers) for q in low_done)
     if rank != 0:
         return 0
     stats = serve.latency_stats(finished)
@@ -784,6 +795,9 @@ def run_serve(args, rank, world, local_rank):
         "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "mean_ms": stats.get("mean_ms"),
         "wall_s": wall, "rounds": srv.rounds, "peak_active_requests": srv.peak_active,
         "offered_layers_per_s": offered, "offered_over_served": offered / (li / wall),
+        "below_capacity": {"rate_req_s": low_rate, "requests": len(low), "served": len(low_done),
+                           "p50_ms": low_stats["p50_ms"], "p99_ms": low_stats["p99_ms"],
+                           "mean_ms": low_stats.get("mean_ms"), "layers_per_s": low_li / low_wall},
     }), flush=True)
     return 0
 
