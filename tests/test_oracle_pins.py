@@ -451,3 +451,24 @@ def test_mod_switch_keeps_the_message(oracle, L, L_out):
     # Delta' m differs from (q'/q) Delta m by less than t; rounding adds (1+||s||_1)/2 per drop
     steps = L - L_out
     assert vs <= v * qs // q + steps * (1 + int(np.abs(s).sum())) // 2 + T_ + steps
+
+
+def test_pmult_lifts_plaintexts_centred(oracle):
+    """PMult by the constant t - 1 is multiplication by -1 (the centred lift
+    of t - 1), so it negates the ciphertext exactly; by 1 it is the identity;
+    by x it is the negacyclic shift (a DRot by N - 1)."""
+    N, L = 64, 3
+    primes = oracle.find_primes(2048, L)
+    ct = synth.raw_ciphertexts(72, primes, (1, 2, L, N))
+    one, minus_one, xpoly = np.zeros((1, N), np.uint32), np.zeros((1, N), np.uint32), np.zeros((1, N), np.uint32)
+    one[0, 0], minus_one[0, 0], xpoly[0, 1] = 1, T - 1, 1
+    assert (oracle.pmult(ct, one, primes) == ct).all()
+    neg = oracle.pmult(ct, minus_one, primes)
+    for l, q in enumerate(primes):
+        assert (neg[0, :, l] == (q - ct[0, :, l].astype(np.int64)) % q).all()
+    shifted = oracle.pmult(ct, xpoly, primes)
+    for l, q in enumerate(primes):
+        for c in range(2):
+            a = ct[0, c, l].astype(np.int64)
+            want = np.concatenate([[(q - a[-1]) % q], a[:-1]])
+            assert (shifted[0, c, l] == want).all()
