@@ -166,7 +166,12 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
     __syncthreads();  // also: every thread is done with the previous item's shared memory
     const long long it = s_item;
     if (it >= a.n_items) break;
-    const Item x = decode(a, it);
+    // claims alternate between the two ends of the item list: even claims walk
+    // forward from the first layers, odd claims backward from the last ones,
+    // so the CTAs sharing an SM tend to mix contraction-heavy (large G) and
+    // transform-heavy (small G) items; each end keeps consecutive items together
+    const long long pos = (it & 1) ? a.n_items - 1 - (it >> 1) : (it >> 1);
+    const Item x = decode(a, pos);
     const StackLayer& y = a.layer[x.li];
     const ConvDims cd{y.Cout, y.G, y.n_in, y.n_out, y.bands};
     conv_item<LOGN>(y.w_hat, y.c_hat, y.out, y.r, cd, x.bb, x.i, x.l, tw, cc, sm);
