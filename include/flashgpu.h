@@ -131,7 +131,9 @@ size_t fl_weights_bytes(const fl_ctx *ctx, const fl_conv_geom *geom);
  * weight polynomials W_{i,g}(x) = sum_{j in g} sum_{ky,kx} w[i][j][ky][kx] *
  * x^-(ky*Wp + kx + (j mod c_n)*P) -- Algorithm 1's DRot/CMult sequence for
  * output channel i folded into one plaintext (Eq. 2: DRot(c, e) = c*x^-e).
- * w_hat_dev uint32 [L][Cout][G][N] (fl_weights_bytes bytes). */
+ * Each image is multiplied by N^-1 mod q_l, which the convolution's inverse
+ * NTT then leaves out.  w_hat_dev uint32 [L][Cout][G][N] (fl_weights_bytes
+ * bytes). */
 int fl_encode_weights(fl_ctx *ctx, const fl_conv_geom *geom, const int8_t *w_dev,
                       uint32_t *w_hat_dev, void *stream);
 
@@ -357,7 +359,7 @@ int fl_batch_decode(fl_ctx *ctx, int n, const uint32_t *m_dev, uint32_t *slots_d
 /* Offline step: r_dev, v_dev [n][N] (reduced mod t) -> prep_dev, which
  * holds fl_x2x_prep_bytes(ctx, n) bytes laid out [n][L+2][N].  Rows
  * [0, L) hold NTT_l of the batch encoding of 2r, lifted to (-t/2, t/2] mod
- * q_l.  Row L holds the batch encoding of v in [0, t).  Row L+1 holds
+ * q_l and multiplied by N^-1 (round 1's inverse NTT leaves that factor out).  Row L holds the batch encoding of v in [0, t).  Row L+1 holds
  * r^2 - r + v mod t (direct encoding).  Sec. 6.3 pre-generates r, v and
  * r^2. */
 size_t fl_x2x_prep_bytes(const fl_ctx *ctx, int n);

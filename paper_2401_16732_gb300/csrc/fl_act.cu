@@ -10,7 +10,7 @@
 //
 // Protocol, with z = a + r the client's masked activations (one vector of N
 // values per ciphertext), X = z^2 + z and Y = 2rz + v:
-//   offline   prep rows: NTT(lift(encode(2r))) per limb, encode(v), and the
+//   offline   prep rows: NTT(N^-1 * lift(encode(2r))) per limb, encode(v), and the
 //             direct-encoded constant r^2 - r + v (Sec. 6.3 keeps r, v and
 //             r^2 precomputed)
 //   round 1   <2rz + v>_batch = PMult(<z>_batch, encode(2r)) + encode(v)
@@ -53,8 +53,9 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
 
 // Plaintext c = encode(scale * slots[c] mod t).  lift_L == 0: written in
 // [0, t) to dst + c*dst_stride.  lift_L > 0: the centred representative in
-// (-t/2, t/2] is written mod q_l to dst + c*dst_stride + l*N, l < lift_L
-// (the plaintext as a polynomial of R_q, the form PMult multiplies by).
+// (-t/2, t/2], times N^-1, is written mod q_l to dst + c*dst_stride + l*N,
+// l < lift_L (the plaintext as a polynomial of R_q, the form PMult
+// multiplies by, pre-scaled for round 1's unscaled inverse NTT).
 template <int LOGN>
 __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
     k_batch_encode(const uint32_t* __restrict__ slots, uint32_t scale, uint32_t* __restrict__ dst,
@@ -74,7 +75,12 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
     if (lift_L == 0) {
       o[u] = m;
     } else {
-      for (int l = 0; l < lift_L; ++l) o[(size_t)l * N + u] = m > half ? cc.limb[l].q - (t - m) : m;
+      // centred lift, times N^-1 mod q_l (round 1's inverse NTT leaves that factor out)
+      for (int l = 0; l < lift_L; ++l) {
+        const LimbConst& lq = cc.limb[l];
+        const uint32_t lifted = m > half ? lq.q - (t - m) : m;
+        o[(size_t)l * N + u] = csub(shoup_mul(lifted, lq.n_inv, lq.n_inv_sh, lq.q), lq.q);
+      }
     }
   });
 }
@@ -145,9 +151,10 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
     if (h == 0) x += shoup_mul(__ldg(V + u), lc.delta, lc.delta_sh, q);  // [0, 4q)
     __stcs(o + u, csub(csub(x, two_q), q));
   };
-  inv_pass<LOGN, T, R1, R2, false>(s, fi, lc, lt, epi);
+  // the prepared 2r carries N^-1, so the transform skips that scaling
+  inv_pass<LOGN, T, R1, R2, false, decltype(epi), false>(s, fi, lc, lt, epi);
   __syncthreads();
-  inv_pass<LOGN, T, 0, R1, true>(s, fi, lc, lt, epi);
+  inv_pass<LOGN, T, 0, R1, true, decltype(epi), false>(s, fi, lc, lt, epi);
 }
 
 // Round 2: out = X - Y, c0 += Delta_l * const.  One thread per 4 coefficients

@@ -185,9 +185,12 @@ __device__ __forceinline__ void fwd_pass(uint32_t* __restrict__ s, const uint32_
 }
 
 // Inverse pass over stages [S0, S0+R), applied from the highest stage down.
-// LAST: this pass contains stage 0; fold N^-1 into it and hand each final
-// value (in [0, 2q)) with its coefficient index to `epi`, which stores it.
-template <int LOGN, int T, int S0, int R, bool LAST, class Epi>
+// LAST: this pass contains stage 0; hand each final value (in [0, 2q)) with
+// its coefficient index to `epi`, which stores it.  SCALE: fold N^-1 into
+// stage 0 (one more Shoup product per butterfly there); without it the
+// result is N times the inverse transform, for inputs that already carry the
+// factor N^-1 (the encoded weights and the prepared x^2+x plaintexts).
+template <int LOGN, int T, int S0, int R, bool LAST, class Epi, bool SCALE = true>
 __device__ __forceinline__ void inv_pass(uint32_t* __restrict__ s, const uint2* __restrict__ tw,
                                          const LimbConst& lc, int tid, Epi& epi) {
   using PG = PassGeo<LOGN, S0, R>;
@@ -206,7 +209,7 @@ __device__ __forceinline__ void inv_pass(uint32_t* __restrict__ s, const uint2* 
 #pragma unroll
       for (int k = 0; k < RAD; ++k) {
         if (k & half) continue;
-        if (LAST && S0 + d == 0) {
+        if (LAST && SCALE && S0 + d == 0) {
           uint32_t X = v[k], Y = v[k + half];
           v[k] = shoup_mul(X + Y, lc.n_inv, lc.n_inv_sh, q);
           v[k + half] = shoup_mul(X - Y + two_q, lc.last_w, lc.last_w_sh, q);
@@ -285,7 +288,7 @@ __device__ __forceinline__ void ntt_forward_to_smem(uint32_t* s, const uint32_t*
 // `epi(value_in_[0,2q), u)`.  `bar()` synchronises every thread that takes
 // part (several polynomials may be transformed side by side by disjoint
 // thread groups sharing one barrier).
-template <int LOGN, class Epi, class Bar>
+template <int LOGN, class Epi, class Bar, bool SCALE = true>
 __device__ __forceinline__ void intt_from_smem_bar(uint32_t* s, const uint32_t* __restrict__ tw_l,
                                                    const LimbConst& lc, int tid, Epi epi, Bar bar) {
   constexpr int N = 1 << LOGN, T = N / 32, R1 = Plan<LOGN>::R1, R2 = Plan<LOGN>::R2;
@@ -301,9 +304,9 @@ __device__ __forceinline__ void intt_from_smem_bar(uint32_t* s, const uint32_t* 
     for (int k = 0; k < 32; ++k) s[pb + k] = v[k];
   }
   bar();
-  inv_pass<LOGN, T, R1, R2, false>(s, f, lc, tid, epi);
+  inv_pass<LOGN, T, R1, R2, false, Epi, SCALE>(s, f, lc, tid, epi);
   bar();
-  inv_pass<LOGN, T, 0, R1, true>(s, f, lc, tid, epi);
+  inv_pass<LOGN, T, 0, R1, true, Epi, SCALE>(s, f, lc, tid, epi);
 }
 
 // As above with block-wide barriers.
@@ -311,6 +314,14 @@ template <int LOGN, class Epi>
 __device__ __forceinline__ void intt_from_smem(uint32_t* s, const uint32_t* __restrict__ tw_l,
                                                const LimbConst& lc, int tid, Epi epi) {
   intt_from_smem_bar<LOGN>(s, tw_l, lc, tid, epi, [] { __syncthreads(); });
+}
+
+// N times the inverse transform, for inputs that already carry N^-1.
+template <int LOGN, class Epi>
+__device__ __forceinline__ void intt_from_smem_unscaled(uint32_t* s, const uint32_t* __restrict__ tw_l,
+                                                        const LimbConst& lc, int tid, Epi epi) {
+  auto bar = [] { __syncthreads(); };
+  intt_from_smem_bar<LOGN, Epi, decltype(bar), false>(s, tw_l, lc, tid, epi, bar);
 }
 
 }  // namespace fl

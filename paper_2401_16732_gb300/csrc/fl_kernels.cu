@@ -130,7 +130,9 @@ __device__ __forceinline__ void conv_item(const uint32_t* __restrict__ w_hat, co
   const size_t oct = (size_t)b * cd.n_out + (size_t)i * cd.bands + band;
   uint32_t* op = out + oct * ct_words + (size_t)h * L * N + (size_t)l * N;
   const uint32_t* rr = (r && h == 0) ? r + oct * N : nullptr;
-  intt_from_smem<LOGN>(h ? s1 : s0, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, lt, [&](uint32_t v, int u) {
+  // the encoded weights carry N^-1, so the transform skips that scaling
+  intt_from_smem_unscaled<LOGN>(h ? s1 : s0, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, lt,
+                                [&](uint32_t v, int u) {
     uint32_t x = v;
     if (rr) x += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, lc.q);
     __stcs(op + u, csub(csub(x, lc.two_q), lc.q));
@@ -327,7 +329,7 @@ __global__ void k_enc_online(const uint32_t* __restrict__ enc0, uint32_t* __rest
 }
 
 // Weight polynomial construction: one thread per (l, i, j, ky, kx).  Tap
-// w[i][j][ky][kx] lands on x^-e, e = ky*Wp + kx + (j mod c_n)*P, of W_{i,g},
+// w[i][j][ky][kx] (times N^-1 mod q_l) lands on x^-e, e = ky*Wp + kx + (j mod c_n)*P, of W_{i,g},
 // g = j / c_n; x^-e = -x^(N-e) for e > 0.  Exponents within one (i, g) are
 // distinct, so every coefficient is written at most once (buffer pre-zeroed).
 __global__ void k_w_scatter(const int8_t* __restrict__ w, uint32_t* __restrict__ w_hat, GeomDims g,
@@ -354,6 +356,9 @@ __global__ void k_w_scatter(const int8_t* __restrict__ w, uint32_t* __restrict__
     pos = N - e;
     val = wv > 0 ? q - (uint32_t)wv : (uint32_t)(-wv);
   }
+  // times N^-1, which the hot path's inverse NTT then leaves out
+  const LimbConst& lc = cc.limb[l];
+  val = csub(shoup_mul(val, lc.n_inv, lc.n_inv_sh, q), q);
   w_hat[(((size_t)l * g.Cout + i) * g.G + gg) * N + pos] = val;
 }
 

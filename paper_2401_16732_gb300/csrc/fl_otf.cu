@@ -54,8 +54,10 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
       const int jj = t / kk, tap = t % kk;
       const int e = (tap / gd.k) * gd.Wp + tap % gd.k + jj * gd.P;  // 0 <= e < N, distinct per (i, g)
       const int wv = wi[(size_t)(g * gd.c_n + jj) * kk + tap];
-      if (e == 0) sw[0] = wv >= 0 ? (uint32_t)wv : q - (uint32_t)(-wv);
-      else sw[pad(N - e)] = wv > 0 ? q - (uint32_t)wv : (uint32_t)(-wv);
+      // tap value times N^-1 mod q_l (the inverse NTT below leaves that factor out)
+      const uint32_t raw = e == 0 ? (wv >= 0 ? (uint32_t)wv : q - (uint32_t)(-wv))
+                                  : (wv > 0 ? q - (uint32_t)wv : (uint32_t)(-wv));
+      sw[e == 0 ? 0 : pad(N - e)] = csub(shoup_mul(raw, lc.n_inv, lc.n_inv_sh, q), q);
     }
     __syncthreads();
     if (tid < T) fwd_pass<LOGN, T, 0, R1, false>(sw, nullptr, f, q, lc.two_q, tid);
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
   const size_t oct = (size_t)b * gd.n_out + (size_t)i * gd.bands + band;
   uint32_t* op = out + oct * ct_words + (size_t)h * L * N + (size_t)l * N;
   const uint32_t* rr = (r && h == 0) ? r + oct * N : nullptr;
-  intt_from_smem<LOGN>(h ? s1 : s0, tw_l, lc, lt, [&](uint32_t v, int u) {
+  intt_from_smem_unscaled<LOGN>(h ? s1 : s0, tw_l, lc, lt, [&](uint32_t v, int u) {
     uint32_t x = v;
     if (rr) x += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, q);
     __stcs(op + u, csub(csub(x, lc.two_q), q));

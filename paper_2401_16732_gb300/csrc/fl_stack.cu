@@ -360,13 +360,14 @@ __global__ void __launch_bounds__(PT + PAR * ((1 << LOGN) / 32), MINB)
         const uint32_t* rr = (s.r && h == 0) ? s.r + oct * N : nullptr;
         uint32_t* sp = polys + (size_t)h * SW;
         if (hs) named_sync(BAR_CONSUMER, CTN);
-        intt_from_smem_bar<LOGN>(sp, twl, lc, lt,
-                                 [&](uint32_t v, int u) {
-                                   uint32_t y = v;
-                                   if (rr) y += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, lc.q);
-                                   __stcs(op + u, csub(csub(y, lc.two_q), lc.q));
-                                 },
-                                 [] { named_sync(BAR_CONSUMER, CTN); });
+        // the encoded weights carry N^-1, so the transform skips that scaling
+        auto epi = [&](uint32_t v, int u) {
+          uint32_t y = v;
+          if (rr) y += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, lc.q);
+          __stcs(op + u, csub(csub(y, lc.two_q), lc.q));
+        };
+        auto bar = [] { named_sync(BAR_CONSUMER, CTN); };
+        intt_from_smem_bar<LOGN, decltype(epi), decltype(bar), false>(sp, twl, lc, lt, epi, bar);
       }
       named_sync(BAR_CONSUMER, CTN);  // every consumer thread is done with the item
       if (ct == 0) mbar_arrive(&empty[b]);

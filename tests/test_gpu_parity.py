@@ -154,10 +154,12 @@ def test_encode_weights_matches_weight_polynomials(fg, oracle, N, L, shape):
         c.ntt_inverse(tmp)
         got[l] = u32(tmp[:, l]).reshape(g.Cout, g.G, N)
     geo = oracle.geometry(N, *shape)
+    # the encoded weights are NTT(W_{i,g}) * N^-1 (the fused kernel's inverse NTT leaves N^-1 out)
     for l, q in enumerate(c.primes):
         for i in range(g.Cout):
             for gg in range(g.G):
-                assert (got[l, i, gg] == oracle.weight_poly(w, i, gg, geo, q)).all()
+                back = got[l, i, gg].astype(np.int64) * N % q
+                assert (back == oracle.weight_poly(w, i, gg, geo, q)).all()
 
 
 # ------------------------------------------------------------------ the hot path
@@ -167,7 +169,7 @@ CONV_CASES = [
     (4096, 2, (16, 16, 16, 16, 3, 1, 1), 3),     # batch
     (2048, 3, (7, 5, 9, 9, 3, 2, 1), 2),         # stride 2, ragged last ct
     (2048, 2, (9, 6, 12, 12, 1, 2, 0), 2),       # 1x1 stride-2 shortcut
-    (2048, 2, (160, 3, 14, 14, 3, 1, 1), 1),     # G = 20 > 16: Barrett fold in the accumulator
+    (2048, 2, (160, 3, 14, 14, 3, 1, 1), 1),     # G = 20 > 16: a fold in the 64-bit accumulator
     (2048, 2, (3, 4, 40, 40, 7, 2, 3), 2),       # 7x7/2 stem with row bands
     (8192, 3, (3, 8, 32, 32, 3, 1, 1), 1),       # ResNet-18 stem shape, N = 8192
     (16384, 4, (5, 3, 30, 30, 3, 1, 1), 1),      # N = 16384, L = 4

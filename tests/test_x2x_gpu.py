@@ -87,7 +87,9 @@ def test_x2x_prepare_rows(fg, oracle, N, L):
     for i in range(n):
         e2r = oracle.batch_encode((2 * r[i].astype(np.int64)) % T, N)
         for l, q in enumerate(c.primes):
-            assert (lifted[i, l] == oracle.lift_centered(e2r, q)).all()
+            # rows [0, L) carry N^-1 (round 1's inverse NTT leaves it out)
+            back = lifted[i, l].astype(np.int64) * N % q
+            assert (back == oracle.lift_centered(e2r, q)).all()
         assert (got[i, L] == oracle.batch_encode(v[i], N)).all()
         rr = r[i].astype(np.int64)
         assert (got[i, L + 1] == (rr * rr - rr + v[i]) % T).all()
