@@ -41,7 +41,7 @@ ALU_BFLY_PEAK = 152 * 4 * 16 * 2.07e9 / 4
 DIRECT_MAC_PEAK = 152 * 4 * 16 * 2.07e9
 # DRAM bytes (read + write) of one step's launches of the dominant kernel, from
 # one ncu capture of the same command (profiles/); a kernel change voids them.
-TRAFFIC = {("resnet18", "queue"): 3.208e9, ("x2x", "round1"): 1.030e9, ("x2x", "round2"): 1.071e9}
+TRAFFIC = {("resnet18", "queue"): 3.340e9, ("x2x", "round1"): 1.031e9, ("x2x", "round2"): 1.071e9}
 
 
 def peaks():
