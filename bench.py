@@ -757,7 +757,10 @@ def run_serve(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     models = {"resnet18": serve.ModelSpec("resnet18", 8192, 3, resnet18_cifar()),
               "resnet50": serve.ModelSpec("resnet50", 16384, 4, resnet50_imagenet())}
-    srv = serve.Server(models)
+    from paper_2401_16732_gb300 import flashgpu
+    kernel = {"per_layer": flashgpu.FL_STACK_PER_LAYER, "persistent": flashgpu.FL_STACK_PERSISTENT,
+              "queue": flashgpu.FL_STACK_QUEUE}["queue" if args.stack_kernel == "auto" else args.stack_kernel]
+    srv = serve.Server(models, stack_kernel=kernel)
     mix = {"resnet18": 0.7, "resnet50": 0.3}
     warm = serve.poisson_requests(max(args.warmup, 3), 200.0, mix, seed=args.seed + 100)
     srv.run(warm, realtime=False)
@@ -791,7 +794,7 @@ def run_serve(args, rank, world, local_rank):
                                "ImageNet (N=16384, L=4), batch U{1..8}, continuous batching by layer rounds",
                    "requests": n, "admission": "peak live bytes of the request's largest layer",
                    "weights_resident_gib": sum(r.weight_bytes for r in srv.res.values()) / 2 ** 30,
-                   "stack_kernel": "per_layer"},
+                   "stack_kernel": "queue" if args.stack_kernel == "auto" else args.stack_kernel},
         "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "mean_ms": stats.get("mean_ms"),
         "wall_s": wall, "rounds": srv.rounds, "peak_active_requests": srv.peak_active,
         "offered_layers_per_s": offered, "offered_over_served": offered / (li / wall),
