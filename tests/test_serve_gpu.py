@@ -18,11 +18,13 @@ def models():
     }
 
 
-def test_each_result_is_the_same_alone_and_in_the_mix(oracle):
-    from paper_2401_16732_gb300 import serve
+@pytest.mark.parametrize("kernel", ["per_layer", "queue"])
+def test_each_result_is_the_same_alone_and_in_the_mix(oracle, kernel):
+    from paper_2401_16732_gb300 import flashgpu, serve
+    kid = flashgpu.FL_STACK_QUEUE if kernel == "queue" else flashgpu.FL_STACK_PER_LAYER
     reqs = [serve.Request(rid=i, model="ab"[i % 2], B=1 + i % 3, arrival=0.001 * i, seed=4) for i in range(7)]
     keep = {(q.rid, li) for q in reqs for li in range(2)}
-    mix = serve.Server(models(), keep_outputs=keep)
+    mix = serve.Server(models(), keep_outputs=keep, stack_kernel=kid)
     finished, _ = mix.run(reqs, realtime=False)
     assert len(finished) == len(reqs) and mix.rounds >= 2
     for q in finished:
