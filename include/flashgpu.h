@@ -78,8 +78,9 @@ int fl_conv_geom_make(int N, int Cin, int Cout, int H, int W, int k, int stride,
 /* Create a context on the current CUDA device: find the L primes, a
  * primitive 2N-th root of unity per prime, the NTT twiddle tables (allocated
  * on the device and owned by the context) and the per-limb constants
- * (Delta mod q_l, N^-1, CRT constants for decryption).  1 <= L <= 4,
- * 2 <= t < 2^20 odd. */
+ * (Delta mod q_l, N^-1, CRT constants for decryption).  When t is prime with
+ * t = 1 mod 2N it also builds the tables of t for batch encoding.  1 <= L <=
+ * 4, 3 <= t < 2^20 odd.  N and L outside the supported set: FL_ERR_ARG. */
 int fl_ctx_create(int N, int L, uint32_t t, fl_ctx **out);
 /* Free the context and its device tables (the caller has synchronised). */
 void fl_ctx_destroy(fl_ctx *ctx);
@@ -146,7 +147,9 @@ size_t fl_he_conv2d_workspace_bytes(const fl_ctx *ctx, const fl_conv_geom *geom,
 /* Homomorphic convolution (Algorithm 1, evaluated as y_{i,band} =
  * sum_g W_{i,g} * ct_{band*G+g} in R_q): forward NTT of the inputs into the
  * workspace (a3), per-slot contraction mod q_l with lazy 64-bit accumulation
- * (a4, Sec. 6.1) fused with the inverse NTT of each output (a5).
+ * (a4, Sec. 6.1) fused with the inverse NTT of each output (a5; the factor
+ * N^-1 comes with the encoded weights).  The fused kernel is launched as a
+ * programmatic dependent of the input NTT.
  * ct_in_dev [B][n_in][2][L][N]; ct_out_dev [B][n_out][2][L][N].  The result
  * equals Algorithm 1 coefficient for coefficient. */
 int fl_he_conv2d(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_hat_dev,
@@ -230,18 +233,23 @@ typedef struct fl_stack_layer {
 size_t fl_stack_workspace_bytes(const fl_ctx *ctx, const fl_stack_layer *layers, int n_layers);
 
 /* fl_he_conv2d (or fl_he_conv2d_mask where r_dev is set) of up to 64
- * independent layers in three launches: one forward NTT over every layer's
- * inputs (a3), then one persistent kernel (a4-a6) whose CTAs pull
- * (layer, image, output channel, limb) items from a shared queue.  Each
- * output equals the single-layer call's bit for bit.  The persistent kernel
- * bounds every internal wait (2 s); if one runs out it stops and records
- * the failure in the workspace's error word (fl_stack_error). */
+ * independent layers: one forward NTT launch over every layer's inputs (a3),
+ * then the contraction + inverse NTT + mask (a4-a6) by the context's stack
+ * kernel (fl_ctx_set_stack_kernel): per-layer launches, one queue-driven
+ * launch, or one persistent warp-specialised launch.  Each output equals
+ * the single-layer call's bit for bit.  The persistent kernel bounds every
+ * internal wait (2 s); if one runs out it stops and records the failure in
+ * the workspace's error word (fl_stack_error).  The layer array holds device
+ * pointers only: every buffer it names must stay allocated until the
+ * enqueued work completes. */
 int fl_he_conv2d_stack(fl_ctx *ctx, const fl_stack_layer *layers, int n_layers, void *workspace_dev,
                        size_t workspace_bytes, void *stream);
 
 /* The two stages of fl_he_conv2d_stack as separate calls (same arguments,
  * same results): the forward NTT of every layer's inputs into the workspace
- * (a3), then the persistent contraction + inverse NTT + mask kernel (a4-a6). */
+ * (a3), then the contraction + inverse NTT + mask kernel(s) (a4-a6).  In
+ * one fl_he_conv2d_stack call the queue kernel follows the NTT as a
+ * programmatic dependent launch; split calls lose only that overlap. */
 int fl_he_conv2d_stack_ntt(fl_ctx *ctx, const fl_stack_layer *layers, int n_layers, void *workspace_dev,
                            size_t workspace_bytes, void *stream);
 int fl_he_conv2d_stack_run(fl_ctx *ctx, const fl_stack_layer *layers, int n_layers, void *workspace_dev,
