@@ -417,3 +417,48 @@ def test_stack_keeps_inline_tensors_alive(fg):
         for o in outs:
             assert torch.equal(o, want)
     c.stack_kernel = fg.FL_STACK_PER_LAYER
+
+
+@pytest.mark.parametrize("kernel", ["queue", "per_layer"])
+def test_graph_replay_matches_eager(fg, oracle, kernel):
+    """A stack (one call: input NTT, then the conv kernel as a programmatic
+    dependent launch) and a single-layer conv captured in CUDA graphs and
+    replayed on fresh inputs give the eager results bit for bit."""
+    N, L = 4096, 2
+    c = ctx(fg, N, L)
+    c.stack_kernel = fg.FL_STACK_QUEUE if kernel == "queue" else fg.FL_STACK_PER_LAYER
+    shapes = [(16, 16, 16, 16, 3, 1, 1), (16, 8, 16, 16, 1, 2, 0)]
+    geos = [c.geom(*sh) for sh in shapes]
+    whs = [c.encode_weights(g, dev(synth.weights(95, (g.Cout, g.Cin, g.k, g.k), li), torch.int8))
+           for li, g in enumerate(geos)]
+    cts = [dev(synth.raw_ciphertexts(95, c.primes, (2, g.n_in, 2, L, N), li)) for li, g in enumerate(geos)]
+    rs = [dev(synth.masks(95, (2, g.n_out, N), T, li)) for li, g in enumerate(geos)]
+    outs = [torch.zeros((2, g.n_out, 2, L, N), dtype=torch.int32, device="cuda") for g in geos]
+    arr = c.stack_layers([{"g": g, "w_hat": wh, "ct_in": ct, "r": r, "out": o}
+                          for g, wh, ct, r, o in zip(geos, whs, cts, rs, outs)])
+    ws = c.stack_workspace(arr)
+    single_out = torch.zeros_like(outs[0])
+    single_ws = c.workspace(geos[0], 2)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):  # warm-up outside the capture
+        c.he_conv2d_stack(arr, ws, stream=st)
+        c.he_conv2d(geos[0], whs[0], cts[0], out=single_out, workspace=single_ws, r=rs[0], stream=st)
+    st.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        c.he_conv2d_stack(arr, ws, stream=st)
+        c.he_conv2d(geos[0], whs[0], cts[0], out=single_out, workspace=single_ws, r=rs[0], stream=st)
+    for trial in range(2):
+        for li, (g, ct) in enumerate(zip(geos, cts)):  # fresh inputs, same buffers
+            ct.copy_(dev(synth.raw_ciphertexts(96 + trial, c.primes, (2, g.n_in, 2, L, N), li)))
+        for o in outs:
+            o.zero_()
+        single_out.zero_()
+        with torch.cuda.stream(st):
+            graph.replay()
+        st.synchronize()
+        assert c.stack_error(ws) == 0
+        for g, wh, ct, r, o in zip(geos, whs, cts, rs, outs):
+            assert torch.equal(o, c.he_conv2d(g, wh, ct, r=r))
+        assert torch.equal(single_out, outs[0])
+    c.stack_kernel = fg.FL_STACK_PER_LAYER
