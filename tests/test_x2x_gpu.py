@@ -95,7 +95,7 @@ def test_x2x_prepare_rows(fg, oracle, N, L):
         assert (got[i, L + 1] == (rr * rr - rr + v[i]) % T).all()
 
 
-@pytest.mark.parametrize("N,L,n", [(4096, 2, 3), (8192, 3, 2)])
+@pytest.mark.parametrize("N,L,n", [(2048, 1, 3), (4096, 2, 3), (8192, 3, 2), (16384, 2, 1)])
 def test_x2x_round1_matches_oracle(fg, oracle, N, L, n):
     """PMult by the batch encoding of 2r plus encode(v) on uniform residues
     (the step is linear in the ciphertext, so any residues exercise it)."""
