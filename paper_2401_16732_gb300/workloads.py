@@ -1,8 +1,9 @@
 """Convolution stacks the throughput measurements run (layer shapes only).
 
-Each layer is (Cin, Cout, H, W, k, stride, pad).  Inputs of every layer are
-independent fresh encryptions of synthetic activations of that shape: the
-server-side chain through the x^2 + x protocol is not computed.
+Each layer is (Cin, Cout, H, W, k, stride, pad).  In these measurements the
+inputs of every layer are independent fresh encryptions of synthetic
+activations of that shape; the chain from one layer to the next through the
+x^2 + x protocol is built and tested on its own (the x2x rounds).
 """
 from __future__ import annotations
 
