@@ -41,7 +41,7 @@ ALU_BFLY_PEAK = 152 * 4 * 16 * 2.07e9 / 4
 DIRECT_MAC_PEAK = 152 * 4 * 16 * 2.07e9
 # DRAM bytes (read + write) of one step's launches of the dominant kernel, from
 # one ncu capture of the same command (profiles/); a kernel change voids them.
-TRAFFIC = {("resnet18", "queue"): 3.340e9, ("x2x", "round1"): 1.031e9, ("x2x", "round2"): 1.071e9}
+TRAFFIC = {("x2x", "round2"): 1.071e9}
 
 
 def peaks():
@@ -228,7 +228,41 @@ def run_reference_x2x(args):
 # ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
+class NvmlClock:
+    """SM clock and clock-event reasons of one GPU, read through NVML (the
+    driver's management library; read-only queries, nothing is set)."""
+    # clock-event reason bits of nvmlDeviceGetCurrentClocksEventReasons
+    REASONS = ((0x4, "sw_power_cap"), (0x8, "hw_slowdown"), (0x20, "sw_thermal_slowdown"),
+               (0x40, "hw_thermal_slowdown"))
+
+    def __init__(self, index):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0 \
+            else None
+
+    def read(self):
+        mhz, bits = self.ct.c_uint(), self.ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, self.ct.byref(mhz)) != 0:  # NVML_CLOCK_SM
+            return None
+        if self.reasons_fn(self.h, self.ct.byref(bits)) != 0:
+            return None
+        return float(mhz.value), int(bits.value)
+
+
 class ClockSampler:
+    """nvidia-smi samples every 50 ms over the whole run, plus NVML reads
+    every ~0.2 ms inside the timed region (poll_until), which short timed
+    regions need; the summary uses the timed-region reads when there are any."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -237,6 +271,24 @@ class ClockSampler:
         self.dev = device_index
         self.proc = None
         self.samples = []
+        self.win = []
+        try:
+            self.nvml = NvmlClock(device_index)
+        except Exception:
+            self.nvml = None
+
+    def poll_until(self, ev):
+        """Read the clocks until CUDA event `ev` completes; the timed steps
+        are already queued, so the GPU is busy meanwhile."""
+        if self.nvml is None:
+            return
+        while True:
+            r = self.nvml.read()
+            if r is not None:
+                self.win.append(r)
+            if ev.query():
+                return
+            time.sleep(0.0002)
 
     def start(self):
         try:
@@ -266,6 +318,16 @@ class ClockSampler:
                 pass
 
     def summary(self):
+        if self.win:
+            reasons = [name for bit, name in NvmlClock.REASONS if any(b & bit for _, b in self.win)]
+            out = {"sm_mhz": statistics.median(m for m, _ in self.win), "sm_max_mhz": self.nvml.max_mhz,
+                   "reasons": reasons, "samples_timed_region": len(self.win), "source": "nvml"}
+            if self.samples:
+                out["nvidia_smi"] = self._smi_summary()
+            return out
+        return self._smi_summary()
+
+    def _smi_summary(self):
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
         load = [s for s in self.samples if s["util"] > 0] or self.samples
@@ -405,6 +467,7 @@ def run_gpu(args, wl, rank, world, local_rank):
     for _ in range(args.steps):
         replay()
     t_end.record(stream)
+    clocks.poll_until(t_end)
     t_end.synchronize()
     torch.cuda.synchronize()
     barrier()
@@ -647,6 +710,7 @@ def run_x2x(args, rank, world, local_rank):
     for _ in range(args.steps):
         step()
     t1.record(stream)
+    clocks.poll_until(t1)
     t1.synchronize()
     torch.cuda.synchronize()
     if world > 1:

@@ -127,30 +127,25 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
   __syncthreads();
   {
     uint32_t v[32];
-    const int pb = lt * 33;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = s[pb + k];
+    uint32_t* srow = s + lt * ROW;
+    lds_row(srow, v);
     pass32<false>(v, tgf, T, lt, q, two_q);
     // NTT-domain entries lt*32 .. lt*32+31 of this component times those of 2r
     const uint4* P4 = reinterpret_cast<const uint4*>(P + lt * 32);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const uint4 p = __ldg(P4 + j);
-      v[4 * j + 0] = red64((uint64_t)csub(csub(v[4 * j + 0], two_q), q) * p.x, lc);
-      v[4 * j + 1] = red64((uint64_t)csub(csub(v[4 * j + 1], two_q), q) * p.y, lc);
-      v[4 * j + 2] = red64((uint64_t)csub(csub(v[4 * j + 2], two_q), q) * p.z, lc);
-      v[4 * j + 3] = red64((uint64_t)csub(csub(v[4 * j + 3], two_q), q) * p.w, lc);
+      v[4 * j + 0] = red64_2q((uint64_t)v[4 * j + 0] * p.x, lc);
+      v[4 * j + 1] = red64_2q((uint64_t)v[4 * j + 1] * p.y, lc);
+      v[4 * j + 2] = red64_2q((uint64_t)v[4 * j + 2] * p.z, lc);
+      v[4 * j + 3] = red64_2q((uint64_t)v[4 * j + 3] * p.w, lc);
     }
     pass32<true>(v, tgi, T, lt, q, two_q);
-#pragma unroll
-    for (int k = 0; k < 32; ++k) s[pb + k] = v[k];
+    sts_row(srow, v);
   }
   __syncthreads();
   uint32_t* o = out + row * N;
-  auto epi = [&](uint32_t x, int u) {
-    if (h == 0) x += shoup_mul(__ldg(V + u), lc.delta, lc.delta_sh, q);  // [0, 4q)
-    __stcs(o + u, csub(csub(x, two_q), q));
-  };
+  MaskStore epi{o, h == 0 ? V : nullptr, lc};  // c0 += Delta * encode(v)
   // the prepared 2r carries N^-1, so the transform skips that scaling
   inv_pass<LOGN, T, R1, R2, false, decltype(epi), false>(s, fi, lc, lt, epi);
   __syncthreads();

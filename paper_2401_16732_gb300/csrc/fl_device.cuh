@@ -20,10 +20,17 @@
 // (the merged negacyclic form of Longa and Naehrig, 2016).  The transform
 // runs in three passes over shared memory; each thread keeps one radix-2^R
 // group in registers for R consecutive stages.  The last forward / first
-// inverse pass is radix-32 on 32 consecutive coefficients.  Shared memory is
-// padded by one word per 32 so every pass is free of bank conflicts.
+// inverse pass is radix-32 on 32 consecutive coefficients.  In shared memory
+// each row of 32 coefficients is padded to 36 words (144 bytes): one row
+// covers the 32 banks, and the rows of 8 consecutive threads start in 8
+// different bank quads, so both the row-strided passes and the per-thread
+// 128-bit accesses of the radix-32 pass are free of bank conflicts.  In the
+// row-strided passes a thread takes 32/2^R adjacent columns, loaded and
+// stored as one 64- or 128-bit access, sharing one set of twiddles.
 #pragma once
 #include <cstdint>
+#include <type_traits>
+#include <utility>
 
 #define FL_MAX_L 4
 
@@ -86,13 +93,15 @@ __device__ __forceinline__ uint32_t barrett64(uint64_t x, uint32_t q, uint64_t m
 // x = hi*(2^32 mod q) + lo (mod q).  One Shoup product on the multiply pipe
 // plus conditional subtractions on the ALU pipe (q in (2^29, 2^30), so
 // lo < 2^32 < 8q and 4q fits 32 bits).
-__device__ __forceinline__ uint32_t red64(uint64_t x, const LimbConst& lc) {
+// red64_2q stops at [0, 2q), the input range of the inverse transform.
+__device__ __forceinline__ uint32_t red64_2q(uint64_t x, const LimbConst& lc) {
   const uint32_t q = lc.q, two_q = lc.two_q;
   const uint32_t a = shoup_mul((uint32_t)(x >> 32), lc.r32, lc.r32_sh, q);  // [0, 2q)
   const uint32_t lo = (uint32_t)x;
   const uint32_t b = csub(csub(lo, 2 * two_q), two_q);                      // [0, 2q)
-  return csub(csub(a + b, two_q), q);                                        // [0, 4q) -> [0, q)
+  return csub(a + b, two_q);                                                 // [0, 4q) -> [0, 2q)
 }
+__device__ __forceinline__ uint32_t red64(uint64_t x, const LimbConst& lc) { return csub(red64_2q(x, lc), lc.q); }
 
 __device__ __forceinline__ void ct_bfly(uint32_t& X, uint32_t& Y, uint32_t w, uint32_t wsh,
                                         uint32_t q, uint32_t two_q) {
@@ -110,7 +119,108 @@ __device__ __forceinline__ void gs_bfly(uint32_t& X, uint32_t& Y, uint32_t w, ui
   Y = y;
 }
 
-__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
+// Padded shared-memory position of coefficient i: rows of 32 at a stride of 36 words.
+constexpr int ROW = 36;
+__host__ __device__ __forceinline__ constexpr int pad(int i) { return i + ((i >> 5) << 2); }
+// 32-bit words of one padded polynomial of n coefficients
+__host__ __device__ constexpr int padded_words(int n) { return n + n / 8; }
+
+// A padded row (32 consecutive coefficients starting at p, 16-byte aligned)
+// to registers and back as eight 128-bit accesses.
+__device__ __forceinline__ void lds_row(const uint32_t* p, uint32_t* v) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint4 x = reinterpret_cast<const uint4*>(p)[j];
+    v[4 * j] = x.x, v[4 * j + 1] = x.y, v[4 * j + 2] = x.z, v[4 * j + 3] = x.w;
+  }
+}
+__device__ __forceinline__ void sts_row(uint32_t* p, const uint32_t* v) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    reinterpret_cast<uint4*>(p)[j] = make_uint4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+}
+
+// NG consecutive words (NG = 1, 2 or 4, p aligned to 4*NG bytes) as one access.
+template <int NG, bool GLOBAL>
+__device__ __forceinline__ void ld_n(const uint32_t* p, uint32_t* v) {
+  if constexpr (NG == 4) {
+    const uint4 x = GLOBAL ? __ldg(reinterpret_cast<const uint4*>(p)) : *reinterpret_cast<const uint4*>(p);
+    v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+  } else if constexpr (NG == 2) {
+    const uint2 x = GLOBAL ? __ldg(reinterpret_cast<const uint2*>(p)) : *reinterpret_cast<const uint2*>(p);
+    v[0] = x.x, v[1] = x.y;
+  } else {
+    v[0] = GLOBAL ? __ldg(p) : *p;
+  }
+}
+template <int NG>
+__device__ __forceinline__ void st_n(uint32_t* p, const uint32_t* v) {
+  if constexpr (NG == 4) *reinterpret_cast<uint4*>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+  else if constexpr (NG == 2) *reinterpret_cast<uint2*>(p) = make_uint2(v[0], v[1]);
+  else *p = v[0];
+}
+
+// Streaming (evict-first) global store of NG consecutive words.
+template <int NG>
+__device__ __forceinline__ void stcs_n(uint32_t* p, const uint32_t* v) {
+  if constexpr (NG == 4) __stcs(reinterpret_cast<uint4*>(p), make_uint4(v[0], v[1], v[2], v[3]));
+  else if constexpr (NG == 2) __stcs(reinterpret_cast<uint2*>(p), make_uint2(v[0], v[1]));
+  else __stcs(p, v[0]);
+}
+
+// Epilogues of the inverse transform receive NG adjacent final values at a
+// time: through `epi.put<NG>(v, u)` when the epilogue has that vector form,
+// else as NG calls `epi(v[j], u + j)`.
+template <class E, class = void> struct has_put : std::false_type {};
+template <class E>
+struct has_put<E, std::void_t<decltype(std::declval<E&>().template put<1>((const uint32_t*)nullptr, 0))>>
+    : std::true_type {};
+
+template <int NG, class E>
+__device__ __forceinline__ void epi_put(E& epi, const uint32_t* v, int u) {
+  if constexpr (has_put<E>::value) {
+    epi.template put<NG>(v, u);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NG; ++j) epi(v[j], u + j);
+  }
+}
+
+// The store that ends every fused convolution item: o[u] = v, plus
+// Delta * r[u] when a mask r is given, reduced to [0, q), as streaming stores.
+// v is in [0, 2q) and the Shoup product in [0, 2q), so the sum stays below 4q;
+// without a mask one conditional subtraction of q suffices.
+struct MaskStore {
+  uint32_t* o;
+  const uint32_t* r;  // nullptr: no mask
+  const LimbConst& lc;
+  template <int NG>
+  __device__ __forceinline__ void put(const uint32_t* v, int u) const {
+    uint32_t x[NG];
+#pragma unroll
+    for (int j = 0; j < NG; ++j) x[j] = v[j];
+    if (r) {
+      uint32_t m[NG];
+      ld_n<NG, true>(r + u, m);
+#pragma unroll
+      for (int j = 0; j < NG; ++j) x[j] = csub(csub(x[j] + shoup_mul(m[j], lc.delta, lc.delta_sh, lc.q), lc.two_q), lc.q);
+    } else {
+#pragma unroll
+      for (int j = 0; j < NG; ++j) x[j] = csub(x[j], lc.q);
+    }
+    stcs_n<NG>(o + u, x);
+  }
+};
+
+// Twiddle m of stage st for block blk of a pass that entered d stages
+// earlier: table entry (1 << st) + (blk << d) + m.  For d >= 1 that index is
+// even for even m, so twiddles m and m ^ 1 come from one 16-byte load.
+__device__ __forceinline__ uint2 tw_at(const uint2* __restrict__ tw, int st, int blk, int d, int m) {
+  const int i = (1 << st) + (blk << d);
+  if (d == 0) return __ldg(tw + i + m);
+  const uint4 t = __ldg(reinterpret_cast<const uint4*>(tw + i + (m & ~1)));
+  return (m & 1) ? make_uint2(t.z, t.w) : make_uint2(t.x, t.y);
+}
 
 template <int LOGN> struct Plan;
 template <> struct Plan<11> { static constexpr int R1 = 3, R2 = 3; };
@@ -128,60 +238,61 @@ template <int LOGN> constexpr int minb_one_poly() { return 1024 >> (LOGN - 5); }
 template <int LOGN> struct Geo {
   static constexpr int N = 1 << LOGN;
   static constexpr int T = N / 32;                 // threads per polynomial
-  static constexpr int SMEM_WORDS = N + N / 32;    // one padded polynomial
+  static constexpr int SMEM_WORDS = padded_words(N);  // one padded polynomial
 };
 
-// Group gid of the pass over stages [S0, S0+R): element k sits at
-// coefficient base + k*TL; in padded shared memory at pb + k*PSTEP.
+// Row-strided pass over stages [S0, S0+R) (TL = N >> (S0+R) >= 32): group
+// gid holds coefficients base + k*TL, k < 2^R.  Thread tid of the T = N/32
+// threads takes the NG = 32 / 2^R adjacent groups NG*tid .. NG*tid + NG-1:
+// one block, NG adjacent columns, i.e. element k of all its groups is one
+// NG-word access at pb + k*PSTEP in padded shared memory.
 template <int LOGN, int S0, int R>
 struct PassGeo {
   static constexpr int N = 1 << LOGN;
   static constexpr int TL = N >> (S0 + R);
-  static constexpr int PSTEP = TL >= 32 ? TL + TL / 32 : 1;
-  static_assert(TL == 1 || TL % 32 == 0, "pass plan keeps passes bank-conflict free");
-  static_assert(TL != 1 || R == 5, "contiguous groups are 32 wide");
-  __device__ __forceinline__ static void of(int gid, int& blk, int& base, int& pb) {
-    if (TL >= 32) {
-      blk = gid / TL;
-      base = blk * (N >> S0) + gid % TL;
-      pb = base + (base >> 5);
-    } else {
-      blk = gid;
-      base = blk * 32;
-      pb = blk * 33;
-    }
+  static constexpr int NG = 32 >> R;
+  static constexpr int PSTEP = TL + TL / 8;
+  static_assert(TL % 32 == 0, "row-strided passes only; the contiguous one is pass32");
+  static_assert(NG >= 1 && NG <= 4, "radix 8, 16 or 32");
+  __device__ __forceinline__ static void of(int tid, int& blk, int& base, int& pb) {
+    const int gid = NG * tid;
+    blk = gid / TL;
+    base = blk * (N >> S0) + gid % TL;
+    pb = pad(base);
   }
 };
 
-// Forward pass over stages [S0, S0+R).  SRC_G: read the group from global
+// Forward pass over stages [S0, S0+R).  SRC_G: read the groups from global
 // memory `g` (natural order) instead of shared memory.  T: threads sharing
-// this polynomial.
+// this polynomial.  v[k*NG + j] is element k of column j.
 template <int LOGN, int T, int S0, int R, bool SRC_G>
 __device__ __forceinline__ void fwd_pass(uint32_t* __restrict__ s, const uint32_t* __restrict__ g,
                                          const uint2* __restrict__ tw, uint32_t q, uint32_t two_q,
                                          int tid) {
   using PG = PassGeo<LOGN, S0, R>;
-  constexpr int RAD = 1 << R, NG = (PG::N / RAD) / T;
+  constexpr int RAD = 1 << R, NG = PG::NG;
+  static_assert(NG * T * RAD == PG::N, "one set of groups per thread");
+  int blk, base, pb;
+  PG::of(tid, blk, base, pb);
+  uint32_t v[RAD * NG];
 #pragma unroll
-  for (int gi = 0; gi < NG; ++gi) {
-    int blk, base, pb;
-    PG::of(tid + gi * T, blk, base, pb);
-    uint32_t v[RAD];
-#pragma unroll
-    for (int k = 0; k < RAD; ++k) v[k] = SRC_G ? __ldg(g + base + k * PG::TL) : s[pb + k * PG::PSTEP];
-#pragma unroll
-    for (int d = 0; d < R; ++d) {
-      const int half = RAD >> (d + 1);
-#pragma unroll
-      for (int k = 0; k < RAD; ++k) {
-        if (k & half) continue;
-        const uint2 w = __ldg(tw + (1 << (S0 + d)) + (blk << d) + (k >> (R - d)));
-        ct_bfly(v[k], v[k + half], w.x, w.y, q, two_q);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < RAD; ++k) s[pb + k * PG::PSTEP] = v[k];
+  for (int k = 0; k < RAD; ++k) {
+    if (SRC_G) ld_n<NG, true>(g + base + k * PG::TL, v + k * NG);
+    else ld_n<NG, false>(s + pb + k * PG::PSTEP, v + k * NG);
   }
+#pragma unroll
+  for (int d = 0; d < R; ++d) {
+    const int half = RAD >> (d + 1);
+#pragma unroll
+    for (int k = 0; k < RAD; ++k) {
+      if (k & half) continue;
+      const uint2 w = tw_at(tw, S0 + d, blk, d, k >> (R - d));
+#pragma unroll
+      for (int j = 0; j < NG; ++j) ct_bfly(v[k * NG + j], v[(k + half) * NG + j], w.x, w.y, q, two_q);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RAD; ++k) st_n<NG>(s + pb + k * PG::PSTEP, v + k * NG);
 }
 
 // Inverse pass over stages [S0, S0+R), applied from the highest stage down.
@@ -194,38 +305,40 @@ template <int LOGN, int T, int S0, int R, bool LAST, class Epi, bool SCALE = tru
 __device__ __forceinline__ void inv_pass(uint32_t* __restrict__ s, const uint2* __restrict__ tw,
                                          const LimbConst& lc, int tid, Epi& epi) {
   using PG = PassGeo<LOGN, S0, R>;
-  constexpr int RAD = 1 << R, NG = (PG::N / RAD) / T;
+  constexpr int RAD = 1 << R, NG = PG::NG;
+  static_assert(NG * T * RAD == PG::N, "one set of groups per thread");
   const uint32_t q = lc.q, two_q = lc.two_q;
+  int blk, base, pb;
+  PG::of(tid, blk, base, pb);
+  uint32_t v[RAD * NG];
 #pragma unroll
-  for (int gi = 0; gi < NG; ++gi) {
-    int blk, base, pb;
-    PG::of(tid + gi * T, blk, base, pb);
-    uint32_t v[RAD];
+  for (int k = 0; k < RAD; ++k) ld_n<NG, false>(s + pb + k * PG::PSTEP, v + k * NG);
 #pragma unroll
-    for (int k = 0; k < RAD; ++k) v[k] = s[pb + k * PG::PSTEP];
+  for (int d = R - 1; d >= 0; --d) {
+    const int half = RAD >> (d + 1);
 #pragma unroll
-    for (int d = R - 1; d >= 0; --d) {
-      const int half = RAD >> (d + 1);
+    for (int k = 0; k < RAD; ++k) {
+      if (k & half) continue;
+      if (LAST && SCALE && S0 + d == 0) {
 #pragma unroll
-      for (int k = 0; k < RAD; ++k) {
-        if (k & half) continue;
-        if (LAST && SCALE && S0 + d == 0) {
-          uint32_t X = v[k], Y = v[k + half];
-          v[k] = shoup_mul(X + Y, lc.n_inv, lc.n_inv_sh, q);
-          v[k + half] = shoup_mul(X - Y + two_q, lc.last_w, lc.last_w_sh, q);
-        } else {
-          const uint2 w = __ldg(tw + (1 << (S0 + d)) + (blk << d) + (k >> (R - d)));
-          gs_bfly(v[k], v[k + half], w.x, w.y, q, two_q);
+        for (int j = 0; j < NG; ++j) {
+          const uint32_t X = v[k * NG + j], Y = v[(k + half) * NG + j];
+          v[k * NG + j] = shoup_mul(X + Y, lc.n_inv, lc.n_inv_sh, q);
+          v[(k + half) * NG + j] = shoup_mul(X - Y + two_q, lc.last_w, lc.last_w_sh, q);
         }
+      } else {
+        const uint2 w = tw_at(tw, S0 + d, blk, d, k >> (R - d));
+#pragma unroll
+        for (int j = 0; j < NG; ++j) gs_bfly(v[k * NG + j], v[(k + half) * NG + j], w.x, w.y, q, two_q);
       }
     }
-    if (LAST) {
+  }
+  if (LAST) {
 #pragma unroll
-      for (int k = 0; k < RAD; ++k) epi(v[k], base + k * PG::TL);
-    } else {
+    for (int k = 0; k < RAD; ++k) epi_put<NG>(epi, v + k * NG, base + k * PG::TL);
+  } else {
 #pragma unroll
-      for (int k = 0; k < RAD; ++k) s[pb + k * PG::PSTEP] = v[k];
-    }
+    for (int k = 0; k < RAD; ++k) st_n<NG>(s + pb + k * PG::PSTEP, v + k * NG);
   }
 }
 
@@ -274,12 +387,12 @@ __device__ __forceinline__ void ntt_forward_to_smem(uint32_t* s, const uint32_t*
   __syncthreads();
   {
     uint32_t v[32];
-    const int pb = tid * 33;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = s[pb + k];
+    uint32_t* p = s + tid * ROW;
+    lds_row(p, v);
     pass32<false>(v, tg, T, tid, lc.q, lc.two_q);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) s[pb + k] = csub(csub(v[k], lc.two_q), lc.q);  // [0, 4q) -> [0, q)
+    for (int k = 0; k < 32; ++k) v[k] = csub(csub(v[k], lc.two_q), lc.q);  // [0, 4q) -> [0, q)
+    sts_row(p, v);
   }
 }
 
@@ -296,12 +409,10 @@ __device__ __forceinline__ void intt_from_smem_bar(uint32_t* s, const uint32_t* 
   const uint4* tg = reinterpret_cast<const uint4*>(tw_l + TwLayout<LOGN>::PAIRS_WORDS) + TW_INV * 16 * T;
   {
     uint32_t v[32];
-    const int pb = tid * 33;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = s[pb + k];
+    uint32_t* p = s + tid * ROW;
+    lds_row(p, v);
     pass32<true>(v, tg, T, tid, lc.q, lc.two_q);
-#pragma unroll
-    for (int k = 0; k < 32; ++k) s[pb + k] = v[k];
+    sts_row(p, v);
   }
   bar();
   inv_pass<LOGN, T, R1, R2, false, Epi, SCALE>(s, f, lc, tid, epi);

@@ -40,11 +40,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
   ntt_forward_to_smem<LOGN>(sm, x, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, tid);
   __syncthreads();
   for (int v = tid; v < N / 4; v += T) {
-    uint4 o;
-    o.x = sm[pad(4 * v + 0)];
-    o.y = sm[pad(4 * v + 1)];
-    o.z = sm[pad(4 * v + 2)];
-    o.w = sm[pad(4 * v + 3)];
+    const uint4 o = *reinterpret_cast<const uint4*>(sm + pad(4 * v));  // 4 slots of one row
     reinterpret_cast<uint4*>(y)[v] = o;
   }
 }
@@ -116,12 +112,11 @@ __device__ __forceinline__ void conv_item(const uint32_t* __restrict__ w_hat, co
         }
       }
     }
-    const int pu = pad(4 * v);  // the 4 slots share one 32-word row
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      s0[pu + j] = red64(a0[j], lc);
-      s1[pu + j] = red64(a1[j], lc);
-    }
+    const int pu = pad(4 * v);  // the 4 slots share one row: one 128-bit store per component
+    *reinterpret_cast<uint4*>(s0 + pu) =
+        make_uint4(red64_2q(a0[0], lc), red64_2q(a0[1], lc), red64_2q(a0[2], lc), red64_2q(a0[3], lc));
+    *reinterpret_cast<uint4*>(s1 + pu) =
+        make_uint4(red64_2q(a1[0], lc), red64_2q(a1[1], lc), red64_2q(a1[2], lc), red64_2q(a1[3], lc));
   }
   __syncthreads();
 
@@ -132,11 +127,7 @@ __device__ __forceinline__ void conv_item(const uint32_t* __restrict__ w_hat, co
   const uint32_t* rr = (r && h == 0) ? r + oct * N : nullptr;
   // the encoded weights carry N^-1, so the transform skips that scaling
   intt_from_smem_unscaled<LOGN>(h ? s1 : s0, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, lt,
-                                [&](uint32_t v, int u) {
-    uint32_t x = v;
-    if (rr) x += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, lc.q);
-    __stcs(op + u, csub(csub(x, lc.two_q), lc.q));
-  });
+                                MaskStore{op, rr, lc});
 }
 
 // Fused contraction + inverse NTT (+ mask).  Grid (B*bands, Cout, L).
@@ -425,7 +416,7 @@ cudaError_t launch_ntt_fwd(int logn, int rows, const uint32_t* src, int src_per,
                            const uint32_t* tw, const CtxConst& cc, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   const int N = 1 << logn;
-  const size_t smem = (size_t)(N + N / 32) * 4;
+  const size_t smem = (size_t)padded_words(N) * 4;
   FL_DISPATCH(logn, (k_ntt_fwd<LG><<<rows, N / 32, smem, st>>>(src, src_per, src_stride, dst, dst_per,
                                                                 dst_stride, limb_div, tw, cc)));
   return cudaGetLastError();
@@ -435,7 +426,7 @@ cudaError_t launch_ntt_inv(int logn, int rows, uint32_t* data, const uint32_t* t
                            cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   const int N = 1 << logn;
-  const size_t smem = (size_t)(N + N / 32) * 4;
+  const size_t smem = (size_t)padded_words(N) * 4;
   FL_DISPATCH(logn, (k_ntt_inv<LG><<<rows, N / 32, smem, st>>>(data, tw, cc)));
   return cudaGetLastError();
 }
@@ -463,7 +454,7 @@ cudaError_t launch_conv_intt(int logn, int B, const ConvDims& cd, const uint32_t
                              const uint32_t* c_hat, uint32_t* out, const uint32_t* r,
                              const uint32_t* tw, const CtxConst& cc, cudaStream_t st, bool pdl) {
   const int N = 1 << logn;
-  const size_t smem = (size_t)2 * (N + N / 32) * 4;
+  const size_t smem = (size_t)2 * padded_words(N) * 4;
   dim3 grid(B * cd.bands, cd.Cout, cc.L);
   cudaError_t e = cudaSuccess;
   if (r) {
@@ -513,7 +504,7 @@ cudaError_t launch_pmul_intt(int logn, int mode, int n, uint32_t* ws, uint32_t* 
                              const uint32_t* tw, const CtxConst& cc, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const int N = 1 << logn;
-  const size_t smem = (size_t)(N + N / 32) * 4;
+  const size_t smem = (size_t)padded_words(N) * 4;
   dim3 grid(n, cc.L);
   if (mode == MODE_DEC) {
     FL_DISPATCH(logn, (k_pmul_intt<LG, MODE_DEC><<<grid, N / 32, smem, st>>>(ws, ct, sk, x, e, gd, tw, cc)));

@@ -68,12 +68,12 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
     __syncthreads();
     if (tid < T) {
       uint32_t v[32];
-      const int pb = tid * 33;
-#pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] = sw[pb + k];
+      uint32_t* p = sw + tid * ROW;
+      lds_row(p, v);
       pass32<false>(v, tg, T, tid, q, lc.two_q);
 #pragma unroll
-      for (int k = 0; k < 32; ++k) sw[pb + k] = csub(csub(v[k], lc.two_q), q);  // [0, q)
+      for (int k = 0; k < 32; ++k) v[k] = csub(csub(v[k], lc.two_q), q);  // [0, q)
+      sts_row(p, v);
     }
     __syncthreads();
     const uint4* X0 = reinterpret_cast<const uint4*>(C + (size_t)g * ct_words);
@@ -96,11 +96,7 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
   const size_t oct = (size_t)b * gd.n_out + (size_t)i * gd.bands + band;
   uint32_t* op = out + oct * ct_words + (size_t)h * L * N + (size_t)l * N;
   const uint32_t* rr = (r && h == 0) ? r + oct * N : nullptr;
-  intt_from_smem_unscaled<LOGN>(h ? s1 : s0, tw_l, lc, lt, [&](uint32_t v, int u) {
-    uint32_t x = v;
-    if (rr) x += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, q);
-    __stcs(op + u, csub(csub(x, lc.two_q), q));
-  });
+  intt_from_smem_unscaled<LOGN>(h ? s1 : s0, tw_l, lc, lt, MaskStore{op, rr, lc});
 }
 
 template <int LOGN>
@@ -124,7 +120,7 @@ cudaError_t launch_conv_otf(int logn, int B, const GeomDims& gd, const int8_t* w
                             cudaStream_t st) {
   if (B == 0) return cudaSuccess;
   const int N = 1 << logn;
-  const size_t smem = (size_t)3 * (N + N / 32) * 4;
+  const size_t smem = (size_t)3 * padded_words(N) * 4;
   dim3 grid(B * gd.bands, gd.Cout, cc.L);
   switch (logn) {
     case 11: k_conv_otf<11><<<grid, N / 16, smem, st>>>(w, c_hat, out, r, gd, tw, cc); break;

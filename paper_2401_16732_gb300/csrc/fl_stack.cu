@@ -344,11 +344,7 @@ __global__ void __launch_bounds__(PT + PAR * ((1 << LOGN) / 32), MINB)
       for (int v = ct; v < N / 2; v += CTN) {
         const int h = v >= N / 4, vq = v - h * (N / 4);
         const uint4 y = __ldcg(reinterpret_cast<const uint4*>(o0 + (size_t)h * L * N) + vq);
-        uint32_t* sp = polys + (size_t)h * SW + pad(4 * vq);
-        sp[0] = y.x;
-        sp[1] = y.y;
-        sp[2] = y.z;
-        sp[3] = y.w;
+        *reinterpret_cast<uint4*>(polys + (size_t)h * SW + pad(4 * vq)) = y;
       }
       named_sync(BAR_CONSUMER, CTN);
       const uint32_t* twl = tw + (size_t)x.l * TwLayout<LOGN>::LIMB_WORDS;
@@ -361,11 +357,7 @@ __global__ void __launch_bounds__(PT + PAR * ((1 << LOGN) / 32), MINB)
         uint32_t* sp = polys + (size_t)h * SW;
         if (hs) named_sync(BAR_CONSUMER, CTN);
         // the encoded weights carry N^-1, so the transform skips that scaling
-        auto epi = [&](uint32_t v, int u) {
-          uint32_t y = v;
-          if (rr) y += shoup_mul(__ldg(rr + u), lc.delta, lc.delta_sh, lc.q);
-          __stcs(op + u, csub(csub(y, lc.two_q), lc.q));
-        };
+        MaskStore epi{op, rr, lc};
         auto bar = [] { named_sync(BAR_CONSUMER, CTN); };
         intt_from_smem_bar<LOGN, decltype(epi), decltype(bar), false>(sp, twl, lc, lt, epi, bar);
       }
@@ -481,11 +473,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, 1024 >> (LOGN - 5))
   ntt_forward_to_smem<LOGN>(sm, x, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, tid);
   __syncthreads();
   for (int v = tid; v < N / 4; v += T) {
-    uint4 o;
-    o.x = sm[pad(4 * v + 0)];
-    o.y = sm[pad(4 * v + 1)];
-    o.z = sm[pad(4 * v + 2)];
-    o.w = sm[pad(4 * v + 3)];
+    const uint4 o = *reinterpret_cast<const uint4*>(sm + pad(4 * v));  // 4 slots of one row
     reinterpret_cast<uint4*>(y)[v] = o;
   }
 }
@@ -511,7 +499,7 @@ cudaError_t launch_ntt_multi(int logn, const NttSegs& segs, const uint32_t* tw, 
   const int rows = segs.row_begin[segs.n];
   if (rows == 0) return cudaSuccess;
   const int N = 1 << logn;
-  const size_t smem = (size_t)(N + N / 32) * 4;
+  const size_t smem = (size_t)padded_words(N) * 4;
   switch (logn) {
     case 11: k_ntt_fwd_multi<11><<<rows, N / 32, smem, st>>>(segs, tw, cc); break;
     case 12: k_ntt_fwd_multi<12><<<rows, N / 32, smem, st>>>(segs, tw, cc); break;

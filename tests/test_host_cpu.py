@@ -102,3 +102,31 @@ def test_bench_algorithmic_bytes_count_every_buffer_once(oracle):
     words = L * g.Cout * g.G * N + B * g.n_in * 2 * L * N + B * g.n_out * 2 * L * N + B * g.n_out * N
     assert bench.layer_bytes(g, B, L, N) == 4 * words
     assert bench.intt_butterflies(g, B, L, N) == B * g.n_out * 2 * L * (N // 2) * int(math.log2(N))
+
+
+def test_clock_record_uses_the_timed_region_reads():
+    """bench.py's clock record: NVML reads taken while the timed steps run
+    are preferred; the reasons the record must flag come from their bits."""
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    reads = iter([(2070.0, 0), (1965.0, 0x4), (2070.0, 0x1)])
+
+    class Ev:
+        n = 0
+
+        def query(self):
+            Ev.n += 1
+            return Ev.n == 3
+
+    cs = bench.ClockSampler.__new__(bench.ClockSampler)
+    cs.samples, cs.win = [], []
+    cs.nvml = types.SimpleNamespace(read=lambda: next(reads), max_mhz=2070.0)
+    cs.poll_until(Ev())
+    s = cs.summary()
+    assert s["samples_timed_region"] == 3 and s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]  # 0x1 (idle) is not a throttle reason
+    cs.win = [(1500.0, 0x8 | 0x40)]
+    assert cs.summary()["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    cs.nvml, cs.win = None, []
+    assert cs.summary()["reasons"] == ["no nvidia-smi samples"]  # neither source: said so, no number
