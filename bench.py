@@ -41,7 +41,7 @@ ALU_BFLY_PEAK = 152 * 4 * 16 * 2.07e9 / 4
 DIRECT_MAC_PEAK = 152 * 4 * 16 * 2.07e9
 # DRAM bytes (read + write) of one step's launches of the dominant kernel, from
 # one ncu capture of the same command (profiles/); a kernel change voids them.
-TRAFFIC = {("x2x", "round2"): 1.071e9}
+TRAFFIC = {("resnet18", "queue"): 3.354e9, ("x2x", "round1"): 1.032e9, ("x2x", "round2"): 1.071e9}
 
 
 def peaks():
@@ -404,7 +404,7 @@ def run_gpu(args, wl, rank, world, local_rank):
     elif args.stack_kernel == "auto":
         from paper_2401_16732_gb300.autotune import tune_stack
         tuned = tune_stack(ctx, [{"g": lay["g"], "ct_in": lay["ct"], "r": lay["r"]} for lay in layers], arr, ws,
-                           stream=stream, cache=None)
+                           stream=stream, cache=None, graph=True)  # the timed step is one graph replay
     else:
         ctx.stack_kernel = {"per_layer": flashgpu.FL_STACK_PER_LAYER, "persistent": flashgpu.FL_STACK_PERSISTENT,
                             "queue": flashgpu.FL_STACK_QUEUE}[args.stack_kernel]

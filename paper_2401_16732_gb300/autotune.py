@@ -18,22 +18,38 @@ KERNELS = ((flashgpu.FL_STACK_PER_LAYER, "per_layer"), (flashgpu.FL_STACK_PERSIS
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "flashgpu_autotune.json")
 
 
-def _key(ctx, specs) -> str:
+def _key(ctx, specs, graph) -> str:
     shapes = [(sp["g"].Cin, sp["g"].Cout, sp["g"].H, sp["g"].W, sp["g"].k, sp["g"].stride, sp["g"].pad,
                int(sp["ct_in"].shape[0]), sp.get("r") is not None) for sp in specs]
     dev = torch.cuda.get_device_name(ctx.device)
-    raw = json.dumps([dev, ctx.N, ctx.L, shapes])
+    raw = json.dumps([dev, ctx.N, ctx.L, shapes, "graph replays" if graph else "whole stack call"])
     return hashlib.sha256(raw.encode()).hexdigest()[:24]
 
 
-def _time(ctx, arr, ws, stream, reps):
+def _time(ctx, arr, ws, stream, reps, graph):
+    """Best of reps+1 timed stack calls (eager), or the mean of 4*reps
+    back-to-back replays of the call captured as a CUDA graph."""
     torch.cuda.synchronize()
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            ctx.he_conv2d_stack(arr, ws, stream=stream, stage="all")
+        for _ in range(2):
+            g.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(4 * reps):
+                g.replay()
+            e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / (4 * reps)
     best = None
     for _ in range(reps + 1):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx.he_conv2d_stack(arr, ws, stream=stream, stage="run")
+        ctx.he_conv2d_stack(arr, ws, stream=stream, stage="all")
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
@@ -41,11 +57,17 @@ def _time(ctx, arr, ws, stream, reps):
     return best
 
 
-def tune_stack(ctx: flashgpu.Context, specs, arr, ws, stream=None, reps: int = 3, cache: str | None = DEFAULT_CACHE):
+def tune_stack(ctx: flashgpu.Context, specs, arr, ws, stream=None, reps: int = 3, cache: str | None = DEFAULT_CACHE,
+               graph: bool = False):
     """Time every stack kernel on the stack `arr` (inputs already in place),
-    set the fastest on `ctx` and return {"kernel": name, "ms": {...}}."""
+    set the fastest on `ctx` and return {"kernel": name, "ms": {...}}.  Each
+    timing covers the whole stack call, input NTT included: how the fused
+    kernel follows the NTT (programmatic dependent launch) is part of what
+    differs between the kernels.  graph=True times the call the way a caller
+    that captures it in a CUDA graph runs it (replays back to back), where
+    host launch latency no longer adds to small stacks."""
     stream = stream or torch.cuda.current_stream()
-    key = _key(ctx, specs)
+    key = _key(ctx, specs, graph)
     table = {}
     if cache and os.path.exists(cache):
         try:
@@ -60,7 +82,7 @@ def tune_stack(ctx: flashgpu.Context, specs, arr, ws, stream=None, reps: int = 3
     ms = {}
     for kid, name in KERNELS:
         ctx.stack_kernel = kid
-        ms[name] = _time(ctx, arr, ws, stream, reps)
+        ms[name] = _time(ctx, arr, ws, stream, reps, graph)
         if ctx.stack_error(ws, stream=stream):
             ms[name] = float("inf")
     best = min(ms, key=ms.get)

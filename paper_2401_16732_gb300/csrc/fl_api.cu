@@ -700,8 +700,9 @@ static int stack_impl(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, v
   unsigned long long* ctl = (unsigned long long*)workspace_dev;
   cudaError_t e;
   // queue head and error word: zeroed before the input NTT, so that the
-  // queue kernel can follow the NTT directly as a programmatic dependent
-  if ((stages & 2) && ctx->stack_kernel == FL_STACK_QUEUE &&
+  // queue kernel (or a single per-layer launch) follows the NTT directly as a
+  // programmatic dependent; the persistent kernel's launcher zeroes its own
+  if ((stages & 2) && ctx->stack_kernel != FL_STACK_PERSISTENT &&
       (e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
     return cuda_fail(e, "control reset");
   if ((stages & 1) && (rc = launched(fl::launch_ntt_multi(ctx->logN, segs, ctx->tw, ctx->cc, st), "stack input ntt")))
@@ -714,8 +715,6 @@ static int stack_impl(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, v
   // per-layer fused launches; the error word stays 0 (these kernels never
   // wait).  The layers are independent, so they fan out over the context's
   // auxiliary streams and join back into `st`.
-  if ((e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
-    return cuda_fail(e, "control reset");
   const int fan = a.n_layers < kAuxStreams ? a.n_layers : kAuxStreams;
   if (fan > 1) {
     if ((e = cudaEventRecord(ctx->fork_ev, st)) != cudaSuccess) return cuda_fail(e, "fork");

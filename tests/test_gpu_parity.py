@@ -419,6 +419,35 @@ def test_stack_keeps_inline_tensors_alive(fg):
     c.stack_kernel = fg.FL_STACK_PER_LAYER
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_autotune_sets_the_fastest_kernel(fg, graph):
+    """The autotuner times every stack kernel (eager calls or graph replays),
+    leaves the fastest set on the context, and the stack then still gives the
+    single-layer result."""
+    from paper_2401_16732_gb300.autotune import KERNELS, tune_stack
+    N, L = 4096, 2
+    c = ctx(fg, N, L)
+    g = c.geom(16, 16, 16, 16, 3, 1, 1)
+    wh = c.encode_weights(g, dev(synth.weights(93, (16, 16, 3, 3)), torch.int8))
+    ct = dev(synth.raw_ciphertexts(93, c.primes, (1, g.n_in, 2, L, N)))
+    r = dev(synth.masks(93, (1, g.n_out, N), T))
+    want = c.he_conv2d(g, wh, ct, r=r)
+    outs = [torch.zeros_like(want) for _ in range(2)]
+    arr = c.stack_layers([{"g": g, "w_hat": wh, "ct_in": ct, "r": r, "out": o} for o in outs])
+    ws = c.stack_workspace(arr)
+    res = tune_stack(c, [{"g": g, "ct_in": ct, "r": r}] * 2, arr, ws, cache=None, graph=graph)
+    assert set(res["ms"]) == {name for _, name in KERNELS} and all(v > 0 for v in res["ms"].values())
+    assert res["kernel"] == min(res["ms"], key=res["ms"].get)
+    assert c.stack_kernel == dict((name, k) for k, name in KERNELS)[res["kernel"]]
+    for o in outs:
+        o.zero_()
+    c.he_conv2d_stack(arr, ws)
+    assert c.stack_error(ws) == 0
+    for o in outs:
+        assert torch.equal(o, want)
+    c.stack_kernel = fg.FL_STACK_PER_LAYER
+
+
 @pytest.mark.parametrize("kernel", ["queue", "per_layer"])
 def test_graph_replay_matches_eager(fg, oracle, kernel):
     """A stack (one call: input NTT, then the conv kernel as a programmatic
