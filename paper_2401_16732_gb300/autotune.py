@@ -31,17 +31,19 @@ def _time(ctx, arr, ws, stream, reps, graph):
     back-to-back replays of the call captured as a CUDA graph."""
     torch.cuda.synchronize()
     if graph:
+        # graphs are captured on a side stream (never the default stream)
+        st = stream if stream != torch.cuda.default_stream(stream.device) else torch.cuda.Stream(stream.device)
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=stream):
-            ctx.he_conv2d_stack(arr, ws, stream=stream, stage="all")
-        for _ in range(2):
-            g.replay()
+        with torch.cuda.graph(g, stream=st):
+            ctx.he_conv2d_stack(arr, ws, stream=st, stage="all")
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            e0.record(stream)
+        with torch.cuda.stream(st):
+            for _ in range(2):
+                g.replay()
+            e0.record(st)
             for _ in range(4 * reps):
                 g.replay()
-            e1.record(stream)
+            e1.record(st)
         e1.synchronize()
         return e0.elapsed_time(e1) / (4 * reps)
     best = None
