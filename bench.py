@@ -93,46 +93,55 @@ def oracle_sample(wl, seed, budget_s):
     """Time Algorithm 1 (oracle route O2, OpenMP over output channels) on a
     bounded sample of (layer, output channel) jobs of one image: passes over
     the layers, each taking the next min(cores, Cout) output channels of every
-    layer, until `budget_s` is spent or every channel is done; the inner loop
-    is the same for every multiply-add, so the whole workload's time follows
-    from the measured multiply-add rate.  Returns (extrapolated seconds per
-    step, seconds spent, sample description)."""
+    layer, until `budget_s` is spent; a workload that finishes well within
+    the budget is run again whole.  The inner loop is the same for every
+    multiply-add, so the whole workload's time follows from the measured
+    multiply-add rate.  Returns (extrapolated seconds per step, seconds spent,
+    sample description)."""
     import oracle
     primes = oracle.find_primes(wl.N, wl.L)
     threads = oracle.num_threads()
-    spent, done, chans = 0.0, 0, 0
+    spent, done, chans, rounds = 0.0, 0, 0, 0
     inputs, layers_seen = {}, set()
-    for p in range(max(sh[1] for sh in wl.layers)):
-        progressed = False
-        for li, shape in enumerate(wl.layers):
-            Cin, Cout, H, W, k, s, pd = shape
-            n = min(threads, Cout)
-            c0 = p * n
-            if c0 >= Cout:
-                continue
-            c1 = min(Cout, c0 + n)
-            job = o2_macs(wl, shape) * (c1 - c0) // Cout
-            if done and spent + job / (done / spent) > budget_s:
-                continue
-            if li not in inputs:
-                geo = oracle.geometry(wl.N, *shape)
-                inputs[li] = (geo, synth.weights(seed, (Cout, Cin, k, k), li),
-                              synth.raw_ciphertexts(seed, primes, (geo.n_in, 2, wl.L, wl.N), li))
-            geo, w, ct = inputs[li]
-            t0 = time.perf_counter()
-            oracle.conv_alg1(ct, w, geo, primes, c0, c1)
-            spent += time.perf_counter() - t0
-            done += job
-            chans += c1 - c0
-            layers_seen.add(li)
-            progressed = True
-        if not progressed:
+    while True:
+        whole = True  # every job of the workload ran in this round
+        for p in range(max(sh[1] for sh in wl.layers)):
+            progressed = False
+            for li, shape in enumerate(wl.layers):
+                Cin, Cout, H, W, k, s, pd = shape
+                n = min(threads, Cout)
+                c0 = p * n
+                if c0 >= Cout:
+                    continue
+                c1 = min(Cout, c0 + n)
+                job = o2_macs(wl, shape) * (c1 - c0) // Cout
+                if done and spent + job / (done / spent) > budget_s:
+                    whole = False
+                    continue
+                if li not in inputs:
+                    geo = oracle.geometry(wl.N, *shape)
+                    inputs[li] = (geo, synth.weights(seed, (Cout, Cin, k, k), li),
+                                  synth.raw_ciphertexts(seed, primes, (geo.n_in, 2, wl.L, wl.N), li))
+                geo, w, ct = inputs[li]
+                t0 = time.perf_counter()
+                oracle.conv_alg1(ct, w, geo, primes, c0, c1)
+                spent += time.perf_counter() - t0
+                done += job
+                chans += c1 - c0
+                layers_seen.add(li)
+                progressed = True
+            if not progressed:
+                break
+        rounds += 1
+        if not whole or spent * (rounds + 1) / rounds > budget_s:
             break
     rate = done / spent
     total = sum(o2_macs(wl, sh) for sh in wl.layers) * wl.B
+    runs = f", the whole workload {rounds} times" if rounds > 1 else ""
     desc = (f"Algorithm 1 (oracle O2, OpenMP over output channels, {threads} threads) on {chans} output channels "
-            f"from {len(layers_seen)} of {len(wl.layers)} layers of one image ({spent:.1f} s, {rate / 1e9:.2f} G "
-            f"multiply-adds/s), extrapolated by multiply-add count to all channels, layers and B={wl.B}")
+            f"from {len(layers_seen)} of {len(wl.layers)} layers of one image{runs} ({spent:.1f} s, "
+            f"{rate / 1e9:.2f} G multiply-adds/s), extrapolated by multiply-add count to all channels, layers and "
+            f"B={wl.B}")
     return total / rate, spent, desc
 
 
