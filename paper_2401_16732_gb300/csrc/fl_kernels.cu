@@ -71,7 +71,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
 // One output item: image/band bb, output channel i, limb l.  2 * N/32
 // threads, two padded polynomials of shared memory at `sm`.  r may be null
 // (no mask).
-template <int LOGN>
+template <int LOGN, bool WALK>
 __device__ __forceinline__ void conv_item(const uint32_t* __restrict__ w_hat, const uint32_t* __restrict__ c_hat,
                                           uint32_t* __restrict__ out, const uint32_t* __restrict__ r,
                                           const ConvDims& cd, int bb, int i, int l, const uint32_t* __restrict__ tw,
@@ -87,28 +87,69 @@ __device__ __forceinline__ void conv_item(const uint32_t* __restrict__ w_hat, co
   const uint32_t* C = c_hat + ((size_t)b * cd.n_in + (size_t)band * cd.G) * ct_words + (size_t)l * N;
 
   // contraction: each thread owns 4 consecutive slots of both components, so
-  // every weight word is loaded once and used twice
+  // every weight word is loaded once and used twice; the 64-bit accumulators
+  // are folded after every 16 terms.  Two forms of the same loop, identical
+  // in result: WALK advances the operand pointers by additions, the other
+  // indexes from fixed bases.  They differ only in what the compiler makes of
+  // them under the 64-register cap; each kernel takes the one that measures
+  // faster in it (WALK in k_conv_intt, where it also halves the spills).
+  const int G = cd.G;
 #pragma unroll 1
   for (int v = tid; v < N / 4; v += T2) {
     uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
-#pragma unroll 2
-    for (int g = 0; g < cd.G; ++g) {
-      const uint4 w = __ldg(W + (size_t)g * (N / 4) + v);
-      const uint4 x0 = __ldg(reinterpret_cast<const uint4*>(C + g * ct_words) + v);
-      const uint4 x1 = __ldg(reinterpret_cast<const uint4*>(C + g * ct_words + (size_t)L * N) + v);
-      a0[0] += (uint64_t)w.x * x0.x;
-      a0[1] += (uint64_t)w.y * x0.y;
-      a0[2] += (uint64_t)w.z * x0.z;
-      a0[3] += (uint64_t)w.w * x0.w;
-      a1[0] += (uint64_t)w.x * x1.x;
-      a1[1] += (uint64_t)w.y * x1.y;
-      a1[2] += (uint64_t)w.z * x1.z;
-      a1[3] += (uint64_t)w.w * x1.w;
-      if (((g + 1) & 15) == 0 && g + 1 < cd.G) {
+    if (WALK) {
+      const size_t ct4 = ct_words / 4;
+      const uint4* wp = W + v;
+      const uint4* xp0 = reinterpret_cast<const uint4*>(C) + v;
+      const uint4* xp1 = reinterpret_cast<const uint4*>(C + (size_t)L * N) + v;
+#pragma unroll 1
+      for (int g0 = 0; g0 < G; g0 += 16) {
+        if (g0) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          a0[j] = red64(a0[j], lc);
-          a1[j] = red64(a1[j], lc);
+          for (int j = 0; j < 4; ++j) {
+            a0[j] = red64(a0[j], lc);
+            a1[j] = red64(a1[j], lc);
+          }
+        }
+        const int g1 = min(G, g0 + 16);
+#pragma unroll 2
+        for (int g = g0; g < g1; ++g) {
+          const uint4 w = __ldg(wp);
+          const uint4 x0 = __ldg(xp0);
+          const uint4 x1 = __ldg(xp1);
+          wp += N / 4;
+          xp0 += ct4;
+          xp1 += ct4;
+          a0[0] += (uint64_t)w.x * x0.x;
+          a0[1] += (uint64_t)w.y * x0.y;
+          a0[2] += (uint64_t)w.z * x0.z;
+          a0[3] += (uint64_t)w.w * x0.w;
+          a1[0] += (uint64_t)w.x * x1.x;
+          a1[1] += (uint64_t)w.y * x1.y;
+          a1[2] += (uint64_t)w.z * x1.z;
+          a1[3] += (uint64_t)w.w * x1.w;
+        }
+      }
+    } else {
+#pragma unroll 2
+      for (int g = 0; g < cd.G; ++g) {
+        const uint4 w = __ldg(W + (size_t)g * (N / 4) + v);
+        const uint4 x0 = __ldg(reinterpret_cast<const uint4*>(C + g * ct_words) + v);
+        const uint4 x1 = __ldg(reinterpret_cast<const uint4*>(C + g * ct_words + (size_t)L * N) + v);
+        a0[0] += (uint64_t)w.x * x0.x;
+        a0[1] += (uint64_t)w.y * x0.y;
+        a0[2] += (uint64_t)w.z * x0.z;
+        a0[3] += (uint64_t)w.w * x0.w;
+        a1[0] += (uint64_t)w.x * x1.x;
+        a1[1] += (uint64_t)w.y * x1.y;
+        a1[2] += (uint64_t)w.z * x1.z;
+        a1[3] += (uint64_t)w.w * x1.w;
+        if (((g + 1) & 15) == 0 && g + 1 < cd.G) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            a0[j] = red64(a0[j], lc);
+            a1[j] = red64(a1[j], lc);
+          }
         }
       }
     }
@@ -142,7 +183,7 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
                 const uint32_t* __restrict__ tw, CtxConst cc) {
   extern __shared__ uint32_t sm[];
   pdl_wait();  // the NTT-domain inputs come from the previous grid in the stream
-  conv_item<LOGN>(w_hat, c_hat, out, MASK ? r : nullptr, cd, blockIdx.x, blockIdx.y, blockIdx.z, tw, cc, sm);
+  conv_item<LOGN, true>(w_hat, c_hat, out, MASK ? r : nullptr, cd, blockIdx.x, blockIdx.y, blockIdx.z, tw, cc, sm);
 }
 
 // The same items for every layer of a stack, pulled from one queue by
@@ -167,7 +208,7 @@ __global__ void __launch_bounds__(2 * ((1 << LOGN) / 32), minb_two_polys<LOGN>()
     const Item x = decode(a, pos);
     const StackLayer& y = a.layer[x.li];
     const ConvDims cd{y.Cout, y.G, y.n_in, y.n_out, y.bands};
-    conv_item<LOGN>(y.w_hat, y.c_hat, y.out, y.r, cd, x.bb, x.i, x.l, tw, cc, sm);
+    conv_item<LOGN, false>(y.w_hat, y.c_hat, y.out, y.r, cd, x.bb, x.i, x.l, tw, cc, sm);
   }
 }
 
