@@ -39,6 +39,9 @@ ALU_BFLY_PEAK = 152 * 4 * 16 * 2.07e9 / 4
 # Direct form: one signed 32x32->64-bit multiply-add per lane per clock on the
 # 16-lane integer multiply pipe (an upper bound).
 DIRECT_MAC_PEAK = 152 * 4 * 16 * 2.07e9
+# mma.sync m16n8k32 u8 x u8 -> s32 multiply-adds/s measured on this GPU by the
+# tensor-core probe (profiles/tc_rates_gb300.md)
+TC_U8_PEAK = 7.9e13
 # DRAM bytes (read + write) of one step's launches of the dominant kernel, from
 # one ncu capture of the same command (profiles/); a kernel change voids them.
 TRAFFIC = {("resnet18", "queue"): 3.354e9, ("x2x", "round1"): 1.032e9, ("x2x", "round2"): 1.071e9}
@@ -393,7 +396,7 @@ def run_gpu(args, wl, rank, world, local_rank):
         a = synth.device_uniform_residues(seed, ctx.primes, (B, g.n_in, L, N), li, device=dev)
         e = synth.device_cbd_noise(seed, (B, g.n_in, N), li, device=dev)
         w_dev = to_dev(w, torch.int8)
-        lay = {"g": g, "w": w_dev, "w_hat": ctx.encode_weights(g, w_dev) if args.form == "ntt" else None,
+        lay = {"g": g, "w": w_dev, "w_hat": ctx.encode_weights(g, w_dev) if args.form in ("ntt", "tc") else None,
                "ct": ctx.encrypt(sk, g, to_dev(x), a, e),
                "r": synth.device_masks(seed, (B, g.n_out, N), T_PLAIN, li, device=dev),
                "out": torch.empty((B, g.n_out, 2, L, N), dtype=torch.int32, device=dev)}
@@ -405,9 +408,9 @@ def run_gpu(args, wl, rank, world, local_rank):
                                  "out": lay["out"]} for lay in layers])
         ws = ctx.stack_workspace(arr)
     torch.cuda.synchronize()
-    if args.form in ("direct", "otf"):
+    if args.form in ("direct", "otf", "tc"):
         tuned = {"kernel": args.form, "ms": None}
-        if args.form == "otf":
+        if args.form in ("otf", "tc"):
             for lay in layers:
                 lay["ws"] = ctx.workspace(lay["g"], B)
     elif args.stack_kernel == "auto":
@@ -433,6 +436,18 @@ def run_gpu(args, wl, rank, world, local_rank):
                 events[1].record(stream)
             for lay, o in zip(layers, outs):
                 ctx.he_conv2d_direct(lay["g"], lay["w"], lay["ct"], out=o, r=lay["r"], stream=stream)
+            if events is not None:
+                events[2].record(stream)
+            return
+        if args.form == "tc":
+            # per layer: input NTT, byte-split tensor-core contraction into the
+            # output buffer (NTT domain), in-place inverse NTT + mask of every
+            # output row (the stages are not separated here: events[1] == events[0])
+            if events is not None:
+                events[1].record(stream)
+            for lay, o in zip(layers, outs):
+                ctx.he_conv2d_tc(lay["g"], lay["w_hat"], lay["ct"], out=o, workspace=lay["ws"], r=lay["r"],
+                                 stream=stream)
             if events is not None:
                 events[2].record(stream)
             return
@@ -464,7 +479,8 @@ def run_gpu(args, wl, rank, world, local_rank):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         step()
-    launches_per_step = {"persistent": 2, "queue": 2, "direct": len(layers), "otf": 2 * len(layers)}.get(
+    launches_per_step = {"persistent": 2, "queue": 2, "direct": len(layers), "otf": 2 * len(layers),
+                         "tc": 3 * len(layers)}.get(
         tuned["kernel"], 1 + len(layers))
 
     def barrier():
@@ -659,6 +675,20 @@ def run_gpu(args, wl, rank, world, local_rank):
                 "kernel_ms_per_step": kern["conv"], "algorithmic_butterflies_per_step": bfly + wbfly,
                 "weight_ntt_butterflies_per_step": wbfly, "hbm_bytes_per_step": obytes,
                 "encoded_weight_bytes_avoided": sum(L * g.Cout * g.G * N * 4 for g in geoms)}
+        kname = roof["kernel"]
+    if tuned["kernel"] == "tc":
+        # the per-slot products as exact u8 digit products on the warp-level
+        # integer MMA (16 per modular multiply-add), against the rate the
+        # tensor-core probe measured for that instruction on this GPU; the
+        # output inverse NTTs run in a second kernel
+        digit_macs = 16 * macs
+        rate = digit_macs / kern_s
+        roof = {"bound": "tensor", "achieved": rate / 1e12, "peak": TC_U8_PEAK / 1e12, "unit": "T u8-MAC/s",
+                "frac": rate / TC_U8_PEAK, "traffic": None,
+                "peak_source": "measured: mma.sync m16n8k32 u8 throughput probe (python -m paper_2401_16732_gb300.tcprobe)",
+                "kernel": "per layer: k_conv_tc (byte-split mma.sync contraction) + k_intt_mask_rows",
+                "kernel_ms_per_step": kern["conv"], "algorithmic_digit_macs_per_step": digit_macs,
+                "other_roofline": dict(alu_line, achieved=achieved_bfly / 1e12, frac=achieved_bfly / ALU_BFLY_PEAK)}
         kname = roof["kernel"]
     line = {
         "metric": "encrypted conv layers/s", "value": value, "unit": "layers/s", "n_gpus": world,
@@ -901,9 +931,10 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--form", default="ntt", choices=["ntt", "direct", "otf"],
+    ap.add_argument("--form", default="ntt", choices=["ntt", "direct", "otf", "tc"],
                     help="ntt: the NTT route with encoded weights (default); direct: the paper's DRot + CMult form "
-                         "on the GPU; otf: the NTT route with weights rebuilt on the fly (no encoded weights)")
+                         "on the GPU; otf: the NTT route with weights rebuilt on the fly (no encoded weights); "
+                         "tc: the NTT route with the byte-split tensor-core contraction (not fused with the INTT)")
     ap.add_argument("--stack-kernel", default="auto", choices=["auto", "per_layer", "persistent", "queue"],
                     help="kernel for the contraction/INTT/mask stage (auto: time both, keep the faster)")
     args = ap.parse_args()

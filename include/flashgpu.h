@@ -212,6 +212,24 @@ int fl_he_conv2d_otf(fl_ctx *ctx, const fl_conv_geom *geom, int B, const int8_t 
 int fl_he_conv2d_direct(fl_ctx *ctx, const fl_conv_geom *geom, int B, const int8_t *w_dev,
                         const uint32_t *ct_in_dev, const uint32_t *r_dev, uint32_t *ct_out_dev, void *stream);
 
+/* Byte-split tensor-core form of the same convolution (the per-slot
+ * contraction of Algorithm 1's sum over input ciphertexts on the integer
+ * tensor cores).  It takes the same encoded weights, inputs, masks and
+ * workspace as fl_he_conv2d_mask, and gives a bit-identical result.  Every
+ * 30-bit residue is split into its four bytes; the per-slot products
+ * sum_g W[i][g] * X[g][col] become exact u8 x u8 -> s32 matrix products of
+ * the warp-level MMA, with the weight byte folded into the reduction
+ * dimension and the seven byte shifts into the column dimension, then
+ * recombined and reduced mod q_l on the CUDA cores.  Unlike the plain form it
+ * is not fused with the inverse NTT: a tensor-core tile spans 16 output
+ * channels of 8 slots, while the inverse NTT needs every slot of one output
+ * channel.  So the NTT-domain outputs go through ct_out_dev, and a second
+ * kernel transforms every output row in place and adds the mask.  Returns
+ * FL_ERR_ARG when L * ceil(2 * B * bands / 8) exceeds 65535. */
+int fl_he_conv2d_tc(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_hat_dev,
+                    const uint32_t *ct_in_dev, const uint32_t *r_dev, uint32_t *ct_out_dev,
+                    void *workspace_dev, size_t workspace_bytes, void *stream);
+
 /* ---- Many layers in one launch ---- */
 
 /* One layer of a stack: its geometry (host pointer), batch size, encoded

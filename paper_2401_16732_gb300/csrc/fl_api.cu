@@ -319,7 +319,8 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
   }
   if ((e = fl::launch_setup(logN)) != cudaSuccess || (e = fl::launch_stack_setup(logN)) != cudaSuccess ||
       (e = fl::launch_ntt_multi_setup(logN)) != cudaSuccess || (e = fl::launch_act_setup(logN)) != cudaSuccess ||
-      (e = fl::launch_direct_setup(logN)) != cudaSuccess || (e = fl::launch_otf_setup(logN)) != cudaSuccess) {
+      (e = fl::launch_direct_setup(logN)) != cudaSuccess || (e = fl::launch_otf_setup(logN)) != cudaSuccess ||
+      (e = fl::launch_tc_setup(logN)) != cudaSuccess) {
     delete c;
     return cuda_fail(e, "kernel set-up");
   }
@@ -603,6 +604,28 @@ int fl_he_conv2d_otf(fl_ctx* ctx, const fl_conv_geom* geom, int B, const int8_t*
   return launched(fl::launch_conv_otf(ctx->logN, B, dims_of(*geom), w_dev, (const uint32_t*)workspace_dev, ct_out_dev,
                                       r_dev, ctx->tw, ctx->cc, st),
                   "on-the-fly conv");
+}
+
+int fl_he_conv2d_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_hat_dev, const uint32_t* ct_in_dev,
+                    const uint32_t* r_dev, uint32_t* ct_out_dev, void* workspace_dev, size_t workspace_bytes,
+                    void* stream) {
+  int rc;
+  if ((rc = conv_checks(ctx, geom, B, workspace_bytes))) return rc;
+  if (B == 0) return FL_OK;
+  if ((rc = check_ptrs({w_hat_dev, ct_in_dev, ct_out_dev, workspace_dev}))) return rc;
+  if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
+  const long long cols = 2LL * B * geom->bands, chunks = (cols + 7) / 8;
+  if (ctx->L * chunks > 65535 || (geom->Cout + 15) / 16 > 65535)
+    return fail(FL_ERR_ARG, "batch too large for one tensor-core launch (%lld column groups)", chunks);
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = stage_ntt(ctx, geom, B, ct_in_dev, workspace_dev, st))) return rc;
+  if ((rc = launched(fl::launch_conv_tc(B, fl::ConvDims{geom->Cout, geom->G, geom->n_in, geom->n_out, geom->bands},
+                                        w_hat_dev, (const uint32_t*)workspace_dev, ct_out_dev, ctx->N, ctx->cc, st),
+                     "tensor-core contraction")))
+    return rc;
+  return launched(fl::launch_intt_mask_rows(ctx->logN, (long long)B * geom->n_out * 2 * ctx->L, ct_out_dev, r_dev,
+                                            ctx->tw, ctx->cc, st),
+                  "output inverse ntt");
 }
 
 int fl_he_conv2d_direct(fl_ctx* ctx, const fl_conv_geom* geom, int B, const int8_t* w_dev, const uint32_t* ct_in_dev,

@@ -135,6 +135,13 @@ cudaError_t launch_conv_otf(int logn, int B, const GeomDims& gd, const int8_t* w
                             cudaStream_t st);
 
 // direct form (fl_direct.cu)
+// byte-split tensor-core contraction (fl_tc.cu): NTT-domain outputs, then
+// the in-place inverse NTT of every output row with the mask
+cudaError_t launch_tc_setup(int logn);
+cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_hat, const uint32_t* c_hat, uint32_t* y_hat,
+                           int N, const CtxConst& cc, cudaStream_t st);
+cudaError_t launch_intt_mask_rows(int logn, long long rows, uint32_t* y, const uint32_t* r, const uint32_t* tw,
+                                  const CtxConst& cc, cudaStream_t st);
 cudaError_t launch_direct_setup(int logn);
 cudaError_t launch_direct(int logn, int B, const GeomDims& g, const int8_t* w, const uint32_t* ct, uint32_t* out,
                           const uint32_t* r, const CtxConst& cc, cudaStream_t st);

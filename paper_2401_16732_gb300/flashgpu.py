@@ -63,6 +63,7 @@ _SIGS = {
     "fl_he_conv2d": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_mask_to_share": ([_vp, _i, _vp, _vp, _vp], _i),
     "fl_he_conv2d_direct": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp], _i),
+    "fl_he_conv2d_tc": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_mod_switch": ([_vp, _i, _vp, _i, _vp, _vp], _i),
     "fl_he_conv2d_otf": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_he_conv2d_mask": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
@@ -348,6 +349,18 @@ class Context:
         out = self._new(B, g.n_out, 2, self.L, self.N) if out is None else out
         _check(_lib.fl_he_conv2d_direct(self.h, ctypes.byref(g), B, _ptr(w), _ptr(ct_in), _ptr(r), _ptr(out),
                                         _stream(stream)))
+        return out
+
+    def he_conv2d_tc(self, g, w_hat, ct_in, out=None, workspace=None, r=None, stream=None) -> torch.Tensor:
+        """Byte-split tensor-core form: the same ciphertexts as he_conv2d (plus
+        the mask when r is given) from the same encoded weights."""
+        B = ct_in.shape[0]
+        _dev_u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
+        out = self._new(B, g.n_out, 2, self.L, self.N) if out is None else out
+        workspace = self.workspace(g, B) if workspace is None else workspace
+        _check(_lib.fl_he_conv2d_tc(self.h, ctypes.byref(g), B, _ptr(w_hat), _ptr(ct_in), _ptr(r), _ptr(out),
+                                    _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                    _stream(stream)))
         return out
 
     def mod_switch(self, ct, L_out: int, out=None, stream=None) -> torch.Tensor:

@@ -127,3 +127,62 @@ def test_otf_weights_bit_exact(fg, oracle, N, L, shape, B):
             sl = slice(i * g.bands, (i + 1) * g.bands)
             assert (y[b, sl] == want).all()
             assert (ym[b, sl] == oracle.mask(want, r[b, sl], c.primes)).all()
+
+
+# ------------------------------------------------------------------ byte-split tensor-core contraction
+TC_CASES = CASES + [
+    (2048, 2, (8, 40, 6, 6, 3, 1, 1), 9),        # 18 columns: three column groups, the last ragged; 3 row tiles
+    (4096, 3, (96, 17, 8, 8, 3, 1, 1), 3),       # several K steps, Cout 17
+]
+
+
+@pytest.mark.parametrize("N,L,shape,B", TC_CASES)
+def test_tc_form_bit_exact(fg, oracle, N, L, shape, B):
+    """The tensor-core form gives the plain form's ciphertexts from the same
+    encoded weights, with and without the mask, and matches the oracle's
+    Algorithm 1 on sampled output channels."""
+    c = ctx(fg, N, L)
+    g = c.geom(*shape)
+    geo = oracle.geometry(N, *shape)
+    w = synth.weights(14, (g.Cout, g.Cin, g.k, g.k))
+    ct = synth.raw_ciphertexts(14, c.primes, (B, g.n_in, 2, L, N))
+    r = synth.masks(14, (B, g.n_out, N), T)
+    dw, dct, dr = dev(w, torch.int8), dev(ct), dev(r)
+    wh = c.encode_weights(g, dw)
+    ym = u32(c.he_conv2d_tc(g, wh, dct, r=dr))
+    y = u32(c.he_conv2d_tc(g, wh, dct))
+    assert (ym == u32(c.he_conv2d(g, wh, dct, r=dr))).all()
+    assert (y == u32(c.he_conv2d(g, wh, dct))).all()
+    assert (u32(dct) == ct).all()
+    for b in (0, B - 1):
+        for i in ([0, g.Cout - 1] if g.Cout > 1 else [0]):
+            want = oracle.conv_alg1(ct[b], w, geo, c.primes, i, i + 1)
+            sl = slice(i * g.bands, (i + 1) * g.bands)
+            assert (y[b, sl] == want).all()
+            assert (ym[b, sl] == oracle.mask(want, r[b, sl], c.primes)).all()
+
+
+def test_tc_form_extreme_digits(fg):
+    """Weights and inputs whose three low bytes are all 255 (the largest digit
+    products) and G = 20, so every tensor-core partial sum is at its bound:
+    the tensor-core form still equals the plain form."""
+    N, L = 2048, 2
+    c = ctx(fg, N, L)
+    g = c.geom(160, 20, 14, 14, 3, 1, 1)  # 8 channels of 16 x 16 padded rows per ciphertext
+    assert g.G == 20
+    big = [((q >> 24) << 24) - 1 for q in c.primes]  # bytes ff ff ff, then the top byte minus one
+    wh = torch.empty((L, g.Cout, g.G, N), dtype=torch.int32, device="cuda")
+    ct = torch.empty((1, g.n_in, 2, L, N), dtype=torch.int32, device="cuda")
+    for l, v in enumerate(big):
+        wh[l] = int(np.uint32(v).view(np.int32))
+        ct[:, :, :, l] = int(np.uint32(v).view(np.int32))
+    r = dev(synth.masks(15, (1, g.n_out, N), T))
+    assert torch.equal(c.he_conv2d_tc(g, wh, ct, r=r), c.he_conv2d(g, wh, ct, r=r))
+
+
+def test_tc_form_empty_batch(fg):
+    c = ctx(fg, 2048, 2)
+    g = c.geom(3, 4, 8, 8, 3, 1, 1)
+    wh = c.encode_weights(g, torch.zeros((4, 3, 3, 3), dtype=torch.int8, device="cuda"))
+    empty = torch.empty((0, g.n_in, 2, 2, 2048), dtype=torch.int32, device="cuda")
+    assert c.he_conv2d_tc(g, wh, empty, workspace=torch.empty(16, dtype=torch.int32, device="cuda")).shape[0] == 0
