@@ -225,7 +225,9 @@ int fl_he_conv2d_direct(fl_ctx *ctx, const fl_conv_geom *geom, int B, const int8
  * channels of 8 slots, while the inverse NTT needs every slot of one output
  * channel.  So the NTT-domain outputs go through ct_out_dev, and a second
  * kernel transforms every output row in place and adds the mask.  Returns
- * FL_ERR_ARG when L * ceil(2 * B * bands / 8) exceeds 65535. */
+ * FL_ERR_SHAPE when the weights of 16 output channels for all G input
+ * ciphertexts of 8 slots do not fit one CTA's shared memory (G above about
+ * 190). */
 int fl_he_conv2d_tc(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_hat_dev,
                     const uint32_t *ct_in_dev, const uint32_t *r_dev, uint32_t *ct_out_dev,
                     void *workspace_dev, size_t workspace_bytes, void *stream);

@@ -138,6 +138,7 @@ cudaError_t launch_conv_otf(int logn, int B, const GeomDims& gd, const int8_t* w
 // byte-split tensor-core contraction (fl_tc.cu): NTT-domain outputs, then
 // the in-place inverse NTT of every output row with the mask
 cudaError_t launch_tc_setup(int logn);
+size_t conv_tc_smem_bytes(int G);  // shared memory of the contraction for G input ciphertexts
 cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_hat, const uint32_t* c_hat, uint32_t* y_hat,
                            int N, const CtxConst& cc, cudaStream_t st);
 cudaError_t launch_intt_mask_rows(int logn, long long rows, uint32_t* y, const uint32_t* r, const uint32_t* tw,

@@ -18,9 +18,10 @@
 // the weight residues themselves, and a B fragment register is a
 // byte-reversed, shifted window of an input residue.
 //
-//   k_conv_tc          one CTA per (8 slots, 16 output channels, limb,
-//                      8 columns); one warp per slot; writes the NTT-domain
-//                      outputs, reduced to [0, q)
+//   k_conv_tc          one CTA per (8-32 slots, 16 output channels, limb):
+//                      weights staged once, then every group of 8 columns;
+//                      each warp takes its slots in turn over all K steps;
+//                      writes the NTT-domain outputs, reduced to [0, q)
 //   k_intt_mask_rows   in-place inverse NTT of every output row, + Delta*r
 //                      on component 0 (the encoded weights carry N^-1, so the
 //                      transform is the unscaled one)
@@ -32,12 +33,13 @@
 namespace fl {
 
 namespace {
-constexpr int TC_SLOTS = 8;        // slots per CTA, one per warp
 constexpr int TC_ROWS = 16;        // output channels per CTA (the MMA's M)
-constexpr int TC_COLS = 8;         // (image/band, component) columns per CTA
+constexpr int TC_COLS = 8;         // (image/band, component) columns per column group
 constexpr int TC_GK = 8;           // input ciphertexts per K step: 8 x 4 weight bytes = 32
 constexpr int TC_N = 7 * TC_COLS;  // (column, shift) pairs: 56, i.e. 7 n-tiles of 8
-constexpr int TC_THREADS = 32 * TC_SLOTS;
+constexpr int TC_WARPS = 8;
+constexpr int TC_THREADS = 32 * TC_WARPS;
+constexpr int TC_WROW = 24;        // row stride of a staged weight: 16 rows + 8 words of padding
 
 // Bytes [x_s, x_(s-1), x_(s-2), x_(s-3)] of x (x_j its byte j; 0 outside 0..3):
 // rows (g, a = 0..3) of B's column (col, s).
@@ -52,98 +54,144 @@ __device__ __forceinline__ void mma_u8(int (&c)[4], const uint32_t (&a)[4], uint
       : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
+
+// Dynamic shared memory of k_conv_tc<SPW> for Gp = G rounded up to 8, in words:
+//   Wst [U][Gp][24]    weights of the CTA's 16 output channels (rows 16..23 padding)
+//   Xst [U][Gp][8]     inputs of one column group
+//   Ys  [8][16][57]    one slot's seven shift sums per warp
+//   Ot  [16][8][U + 4] reduced NTT-domain outputs of the column group
+// with U = 8 * SPW slots.  The weight layout puts the 32 lanes' A-fragment
+// words (g = 8k + t, row = grp or grp + 8) in 32 different banks.
+__host__ __device__ constexpr size_t tc_smem_words(int spw, int gp) {
+  return (size_t)8 * spw * gp * TC_WROW + (size_t)8 * spw * gp * TC_COLS + (size_t)TC_WARPS * TC_ROWS * (TC_N + 1) +
+         (size_t)TC_ROWS * TC_COLS * (8 * spw + 4);
+}
 }  // namespace
 
-// Grid (N / 8, ceil(Cout / 16), L * ceil(2 * B * bands / 8)).
+// Grid (N / U, ceil(Cout / 16), L), U = 8 * SPW slots per CTA; every CTA
+// loops over the column groups of 8 (image/band, component) columns, with
+// its weights staged once.  Warp w takes slots w*SPW .. w*SPW + SPW - 1 in
+// turn, each over all K steps.
+template <int SPW>
 __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const uint32_t* __restrict__ w_hat,
                                                          const uint32_t* __restrict__ c_hat,
                                                          uint32_t* __restrict__ y_hat, ConvDims cd, int B, int N,
                                                          CtxConst cc) {
-  __shared__ uint32_t Wst[TC_ROWS][TC_GK][TC_SLOTS];
-  __shared__ uint32_t Xst[TC_GK][TC_COLS][TC_SLOTS];
-  __shared__ int Ys[TC_SLOTS][TC_ROWS][TC_N + 1];
-  __shared__ uint32_t Ot[TC_ROWS][TC_COLS][TC_SLOTS];
+  constexpr int U = 8 * SPW, U4 = U / 4, UP = U + 4;  // UP: padded row of Ot
+  extern __shared__ __align__(16) uint32_t tsm[];
+  const int Gp = (cd.G + TC_GK - 1) / TC_GK * TC_GK;
+  uint32_t* Wst = tsm;                                            // [U][Gp][24]
+  uint32_t* Xst = Wst + (size_t)U * Gp * TC_WROW;                 // [U][Gp][8]
+  int* Ys = reinterpret_cast<int*>(Xst + (size_t)U * Gp * TC_COLS);  // [8][16][57]
+  uint32_t* Ot = reinterpret_cast<uint32_t*>(Ys + TC_WARPS * TC_ROWS * (TC_N + 1));  // [16][8][UP]
   const int L = cc.L;
-  const int u0 = blockIdx.x * TC_SLOTS, i0 = blockIdx.y * TC_ROWS;
-  const int l = blockIdx.z % L, chunk = blockIdx.z / L;
+  const int u0 = blockIdx.x * U, i0 = blockIdx.y * TC_ROWS, l = blockIdx.z;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, grp = lane >> 2, t = lane & 3;
-  const int ncols = min(TC_COLS, 2 * B * cd.bands - chunk * TC_COLS);  // >= 1 by the grid
-  const int ntiles = (7 * ncols + 7) / 8;
   const size_t ct_words = (size_t)2 * L * N;
   const LimbConst lc = cc.limb[l];
+  const uint32_t c40 = red64((uint64_t)lc.r32 << 8, lc);  // 2^40 mod q
+  const int cols = 2 * B * cd.bands;
 
-  int acc[7][4];
-#pragma unroll
-  for (int j = 0; j < 7; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0;
+  // weights: Wst[uu][g][ii] = W[l][i0 + ii][g][u0 + uu], zero outside the layer
+  for (int e = tid; e < TC_ROWS * Gp * U4; e += TC_THREADS) {
+    const int ii = e % TC_ROWS, g = (e / TC_ROWS) % Gp, q4 = e / (TC_ROWS * Gp);
+    const int i = i0 + ii;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    if (i < cd.Cout && g < cd.G)
+      w = __ldg(reinterpret_cast<const uint4*>(w_hat + (((size_t)l * cd.Cout + i) * cd.G + g) * N + u0) + q4);
+    uint32_t* d = Wst + ((size_t)(4 * q4) * Gp + g) * TC_WROW + ii;
+    d[0] = w.x;
+    d[(size_t)Gp * TC_WROW] = w.y;
+    d[(size_t)2 * Gp * TC_WROW] = w.z;
+    d[(size_t)3 * Gp * TC_WROW] = w.w;
+  }
 
-  for (int g0 = 0; g0 < cd.G; g0 += TC_GK) {
-    __syncthreads();  // the previous K step's operands are no longer read
-    for (int e = tid; e < TC_ROWS * TC_GK * TC_SLOTS; e += TC_THREADS) {
-      const int uu = e % TC_SLOTS, gg = (e / TC_SLOTS) % TC_GK, ii = e / (TC_SLOTS * TC_GK);
-      const int i = i0 + ii, g = g0 + gg;
-      Wst[ii][gg][uu] =
-          (i < cd.Cout && g < cd.G) ? __ldg(w_hat + (((size_t)l * cd.Cout + i) * cd.G + g) * N + u0 + uu) : 0u;
-    }
-    for (int e = tid; e < TC_GK * TC_COLS * TC_SLOTS; e += TC_THREADS) {
-      const int uu = e % TC_SLOTS, cl = (e / TC_SLOTS) % TC_COLS, gg = e / (TC_SLOTS * TC_COLS);
-      const int g = g0 + gg, col = chunk * TC_COLS + cl;
-      uint32_t x = 0;
+  for (int chunk = 0; chunk * TC_COLS < cols; ++chunk) {
+    const int ncols = min(TC_COLS, cols - chunk * TC_COLS);
+    const int ntiles = (7 * ncols + 7) / 8;
+    __syncthreads();  // the weights are staged; the previous group's Xst and Ot are no longer read
+    // inputs: Xst[uu][g][cl] = X[g][column chunk*8 + cl][u0 + uu], zero outside
+    for (int e = tid; e < TC_COLS * Gp * U4; e += TC_THREADS) {
+      const int cl = e % TC_COLS, g = (e / TC_COLS) % Gp, q4 = e / (TC_COLS * Gp);
+      uint4 x = make_uint4(0, 0, 0, 0);
       if (g < cd.G && cl < ncols) {
-        const int bb = col >> 1, c = col & 1, b = bb / cd.bands, band = bb % cd.bands;
-        x = __ldg(c_hat + ((size_t)b * cd.n_in + (size_t)band * cd.G + g) * ct_words + (size_t)c * L * N +
-                  (size_t)l * N + u0 + uu);
+        const int col = chunk * TC_COLS + cl, bb = col >> 1, c = col & 1, b = bb / cd.bands, band = bb % cd.bands;
+        x = __ldg(reinterpret_cast<const uint4*>(c_hat + ((size_t)b * cd.n_in + (size_t)band * cd.G + g) * ct_words +
+                                                 (size_t)c * L * N + (size_t)l * N + u0) +
+                  q4);
       }
-      Xst[gg][cl][uu] = x;
+      uint32_t* d = Xst + ((size_t)(4 * q4) * Gp + g) * TC_COLS + cl;
+      d[0] = x.x;
+      d[(size_t)Gp * TC_COLS] = x.y;
+      d[(size_t)2 * Gp * TC_COLS] = x.z;
+      d[(size_t)3 * Gp * TC_COLS] = x.w;
     }
     __syncthreads();
-    // A fragment: rows grp, grp+8; K columns 4t..4t+3 (g = t) and 16+4t.. (g = 4+t)
-    const uint32_t a[4] = {Wst[grp][t][warp], Wst[grp + 8][t][warp], Wst[grp][4 + t][warp],
-                           Wst[grp + 8][4 + t][warp]};
+    int* ys = Ys + warp * TC_ROWS * (TC_N + 1);
+#pragma unroll 1
+    for (int sl = 0; sl < SPW; ++sl) {
+      const int uu = warp * SPW + sl;
+      const uint32_t* ws = Wst + (size_t)uu * Gp * TC_WROW;
+      const uint32_t* xs = Xst + (size_t)uu * Gp * TC_COLS;
+      int acc[7][4];
 #pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      if (j < ntiles) {  // warp-uniform
-        // B fragment: column n = 8j + grp of the tile, K rows as for A
-        const int n = 8 * j + grp, cl = n / 7, s = n % 7;
-        mma_u8(acc[j], a, digit_window(Xst[t][cl][warp], s), digit_window(Xst[4 + t][cl][warp], s));
+      for (int j = 0; j < 7; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0;
+#pragma unroll 1
+      for (int g0 = 0; g0 < Gp; g0 += TC_GK) {
+        // A fragment: rows grp, grp+8; K columns 4t..4t+3 (g = g0+t) and 16+4t.. (g = g0+4+t)
+        const uint32_t* w0 = ws + (g0 + t) * TC_WROW;
+        const uint32_t* w1 = ws + (g0 + 4 + t) * TC_WROW;
+        const uint32_t a[4] = {w0[grp], w0[grp + 8], w1[grp], w1[grp + 8]};
+        const uint32_t* x0 = xs + (g0 + t) * TC_COLS;
+        const uint32_t* x1 = xs + (g0 + 4 + t) * TC_COLS;
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+          if (j < ntiles) {  // warp-uniform
+            // B fragment: column n = 8j + grp of the tile, K rows as for A
+            const int n = 8 * j + grp, cl = n / 7, s = n % 7;
+            mma_u8(acc[j], a, digit_window(x0[cl], s), digit_window(x1[cl], s));
+          }
+        }
       }
-    }
-  }
-
-  // accumulators -> Ys[slot][row][n]: c0, c1 at row grp, c2, c3 at row grp + 8; n = 8j + 2t + {0, 1}
+      // accumulators -> ys[row][n]: c0, c1 at row grp, c2, c3 at row grp + 8; n = 8j + 2t + {0, 1}
 #pragma unroll
-  for (int j = 0; j < 7; ++j) {
-    if (j < ntiles) {
-      Ys[warp][grp][8 * j + 2 * t] = acc[j][0];
-      Ys[warp][grp][8 * j + 2 * t + 1] = acc[j][1];
-      Ys[warp][grp + 8][8 * j + 2 * t] = acc[j][2];
-      Ys[warp][grp + 8][8 * j + 2 * t + 1] = acc[j][3];
-    }
-  }
-  __syncwarp();
-  // recombine Y = sum_s 2^(8s) Y_s mod q: Y_0..Y_4 by shifts below 2^64, then
-  // (Y_5 + 2^8 Y_6) * (2^40 mod q)
-  const uint32_t c40 = red64((uint64_t)lc.r32 << 8, lc);
-  for (int p = lane; p < TC_ROWS * TC_COLS; p += 32) {
-    const int ii = p / TC_COLS, cl = p % TC_COLS;
-    uint32_t y = 0;
-    if (cl < ncols) {
-      const int* ys = &Ys[warp][ii][7 * cl];
-      uint64_t lo = 0;
+      for (int j = 0; j < 7; ++j) {
+        if (j < ntiles) {
+          ys[grp * (TC_N + 1) + 8 * j + 2 * t] = acc[j][0];
+          ys[grp * (TC_N + 1) + 8 * j + 2 * t + 1] = acc[j][1];
+          ys[(grp + 8) * (TC_N + 1) + 8 * j + 2 * t] = acc[j][2];
+          ys[(grp + 8) * (TC_N + 1) + 8 * j + 2 * t + 1] = acc[j][3];
+        }
+      }
+      __syncwarp();
+      // Y = sum_s 2^(8s) Y_s mod q: Y_0..Y_4 by shifts below 2^64, then
+      // (Y_5 + 2^8 Y_6) * (2^40 mod q)
+      for (int p = lane; p < TC_ROWS * TC_COLS; p += 32) {
+        const int ii = p / TC_COLS, cl = p % TC_COLS;
+        uint32_t y = 0;
+        if (cl < ncols) {
+          const int* v = ys + ii * (TC_N + 1) + 7 * cl;
+          uint64_t lo = 0;
 #pragma unroll
-      for (int s = 0; s < 5; ++s) lo += (uint64_t)(uint32_t)ys[s] << (8 * s);
-      const uint64_t hi = (uint64_t)(uint32_t)ys[5] + ((uint64_t)(uint32_t)ys[6] << 8);
-      y = csub(red64(lo, lc) + red64((uint64_t)red64(hi, lc) * c40, lc), lc.q);
+          for (int s = 0; s < 5; ++s) lo += (uint64_t)(uint32_t)v[s] << (8 * s);
+          const uint64_t hi = (uint64_t)(uint32_t)v[5] + ((uint64_t)(uint32_t)v[6] << 8);
+          y = csub(red64(lo, lc) + red64((uint64_t)red64(hi, lc) * c40, lc), lc.q);
+        }
+        Ot[(ii * TC_COLS + cl) * UP + uu] = y;
+      }
+      __syncwarp();  // ys is rewritten by the next slot
     }
-    Ot[ii][cl][warp] = y;
-  }
-  __syncthreads();
-  for (int e = tid; e < TC_ROWS * TC_COLS * TC_SLOTS; e += TC_THREADS) {
-    const int uu = e % TC_SLOTS, cl = (e / TC_SLOTS) % TC_COLS, ii = e / (TC_SLOTS * TC_COLS);
-    const int i = i0 + ii, col = chunk * TC_COLS + cl;
-    if (i < cd.Cout && cl < ncols) {
-      const int bb = col >> 1, c = col & 1, b = bb / cd.bands, band = bb % cd.bands;
-      const size_t oct = (size_t)b * cd.n_out + (size_t)i * cd.bands + band;
-      y_hat[(oct * 2 + c) * L * N + (size_t)l * N + u0 + uu] = Ot[ii][cl][uu];
+    __syncthreads();
+    // rows (i, column) of the group: U consecutive slots each, as 16-byte stores
+    for (int e = tid; e < TC_ROWS * TC_COLS * U4; e += TC_THREADS) {
+      const int q4 = e % U4, cl = (e / U4) % TC_COLS, ii = e / (U4 * TC_COLS);
+      const int i = i0 + ii;
+      if (i < cd.Cout && cl < ncols) {
+        const int col = chunk * TC_COLS + cl, bb = col >> 1, c = col & 1, b = bb / cd.bands, band = bb % cd.bands;
+        const size_t oct = (size_t)b * cd.n_out + (size_t)i * cd.bands + band;
+        reinterpret_cast<uint4*>(y_hat + (oct * 2 + c) * L * N + (size_t)l * N + u0)[q4] =
+            reinterpret_cast<const uint4*>(Ot + (ii * TC_COLS + cl) * UP)[q4];
+      }
     }
   }
 }
@@ -169,15 +217,40 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
                                 MaskStore{p, (r && c == 0) ? r + oct * N : nullptr, lc});
 }
 
+// Slots per warp for a layer: 4 while the staged operands fit in 200 KB of
+// shared memory (two CTAs per SM for small G), then 2, then 1.
+static int tc_spw(int G) {
+  const int gp = (G + TC_GK - 1) / TC_GK * TC_GK;
+  for (int spw = 4; spw > 1; spw /= 2)
+    if (tc_smem_words(spw, gp) * 4 <= 200 * 1024) return spw;
+  return 1;
+}
+
+size_t conv_tc_smem_bytes(int G) {
+  const int gp = (G + TC_GK - 1) / TC_GK * TC_GK;
+  return tc_smem_words(tc_spw(G), gp) * 4;
+}
+
+template <int SPW>
+static cudaError_t conv_tc(int B, const ConvDims& cd, const uint32_t* w_hat, const uint32_t* c_hat, uint32_t* y_hat,
+                           int N, const CtxConst& cc, cudaStream_t st) {
+  const int gp = (cd.G + TC_GK - 1) / TC_GK * TC_GK;
+  const size_t smem = tc_smem_words(SPW, gp) * 4;
+  const dim3 grid(N / (8 * SPW), (cd.Cout + TC_ROWS - 1) / TC_ROWS, cc.L);
+  k_conv_tc<SPW><<<grid, TC_THREADS, smem, st>>>(w_hat, c_hat, y_hat, cd, B, N, cc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_hat, const uint32_t* c_hat, uint32_t* y_hat,
                            int N, const CtxConst& cc, cudaStream_t st) {
-  const long long cols = 2LL * B * cd.bands;
-  if (cols == 0 || cd.Cout == 0) return cudaSuccess;
-  const long long chunks = (cols + TC_COLS - 1) / TC_COLS;
-  const dim3 grid(N / TC_SLOTS, (cd.Cout + TC_ROWS - 1) / TC_ROWS, (unsigned)(cc.L * chunks));
-  if (grid.y > 65535 || cc.L * chunks > 65535) return cudaErrorInvalidConfiguration;
-  k_conv_tc<<<grid, TC_THREADS, 0, st>>>(w_hat, c_hat, y_hat, cd, B, N, cc);
-  return cudaGetLastError();
+  if (B == 0 || cd.Cout == 0) return cudaSuccess;
+  if ((cd.Cout + TC_ROWS - 1) / TC_ROWS > 65535 || conv_tc_smem_bytes(cd.G) > 227 * 1024)
+    return cudaErrorInvalidConfiguration;
+  switch (tc_spw(cd.G)) {
+    case 4: return conv_tc<4>(B, cd, w_hat, c_hat, y_hat, N, cc, st);
+    case 2: return conv_tc<2>(B, cd, w_hat, c_hat, y_hat, N, cc, st);
+    default: return conv_tc<1>(B, cd, w_hat, c_hat, y_hat, N, cc, st);
+  }
 }
 
 template <int LOGN>
@@ -187,6 +260,12 @@ static cudaError_t intt_rows_setup() {
 }
 
 cudaError_t launch_tc_setup(int logn) {
+  // the contraction kernels may use up to the per-CTA maximum of dynamic shared memory
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) ||
+      (e = cudaFuncSetAttribute(k_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) ||
+      (e = cudaFuncSetAttribute(k_conv_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)))
+    return e;
   switch (logn) {
     case 11: return intt_rows_setup<11>();
     case 12: return intt_rows_setup<12>();
