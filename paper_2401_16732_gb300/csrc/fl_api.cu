@@ -614,7 +614,7 @@ int fl_he_conv2d_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t
   if (B == 0) return FL_OK;
   if ((rc = check_ptrs({w_hat_dev, ct_in_dev, ct_out_dev, workspace_dev}))) return rc;
   if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
-  if (fl::conv_tc_smem_bytes(geom->G) > 227 * 1024)
+  if (fl::conv_tc_smem_bytes(geom->G) > 226 * 1024)
     return fail(FL_ERR_SHAPE, "G=%d input ciphertexts exceed the tensor-core form's shared memory", geom->G);
   if ((geom->Cout + 15) / 16 > 65535) return fail(FL_ERR_SHAPE, "Cout=%d", geom->Cout);
   cudaStream_t st = (cudaStream_t)stream;

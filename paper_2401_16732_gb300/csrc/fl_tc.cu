@@ -40,6 +40,7 @@ constexpr int TC_N = 7 * TC_COLS;  // (column, shift) pairs: 56, i.e. 7 n-tiles 
 constexpr int TC_WARPS = 8;
 constexpr int TC_THREADS = 32 * TC_WARPS;
 constexpr int TC_WROW = 24;        // row stride of a staged weight: 16 rows + 8 words of padding
+constexpr int TC_MAX_DYN_SMEM = 226 * 1024;  // dynamic shared memory limit, 1 KB below the CTA maximum
 
 // Bytes [x_s, x_(s-1), x_(s-2), x_(s-3)] of x (x_j its byte j; 0 outside 0..3):
 // rows (g, a = 0..3) of B's column (col, s).
@@ -92,39 +93,56 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const uint32_t* __restri
   const uint32_t c40 = red64((uint64_t)lc.r32 << 8, lc);  // 2^40 mod q
   const int cols = 2 * B * cd.bands;
 
-  // weights: Wst[uu][g][ii] = W[l][i0 + ii][g][u0 + uu], zero outside the layer
-  for (int e = tid; e < TC_ROWS * Gp * U4; e += TC_THREADS) {
-    const int ii = e % TC_ROWS, g = (e / TC_ROWS) % Gp, q4 = e / (TC_ROWS * Gp);
+  // weights: Wst[uu][g][ii] = W[l][i0 + ii][g][u0 + uu], zero outside the
+  // layer.  Each thread owns one (row, 4-slot group) and walks g; no index
+  // division by a runtime value.
+  {
+    constexpr int WP = TC_ROWS * U4, WS = TC_THREADS / WP;
+    const int ii = tid % TC_ROWS, q4 = (tid / TC_ROWS) % U4, gs = tid / WP;
     const int i = i0 + ii;
-    uint4 w = make_uint4(0, 0, 0, 0);
-    if (i < cd.Cout && g < cd.G)
-      w = __ldg(reinterpret_cast<const uint4*>(w_hat + (((size_t)l * cd.Cout + i) * cd.G + g) * N + u0) + q4);
-    uint32_t* d = Wst + ((size_t)(4 * q4) * Gp + g) * TC_WROW + ii;
-    d[0] = w.x;
-    d[(size_t)Gp * TC_WROW] = w.y;
-    d[(size_t)2 * Gp * TC_WROW] = w.z;
-    d[(size_t)3 * Gp * TC_WROW] = w.w;
+    const uint4* src = reinterpret_cast<const uint4*>(w_hat + ((size_t)l * cd.Cout + (i < cd.Cout ? i : 0)) * cd.G * N + u0) + q4;
+    uint32_t* d = Wst + (size_t)(4 * q4) * Gp * TC_WROW + ii;
+    for (int g = gs; g < Gp; g += WS) {
+      uint4 w = make_uint4(0, 0, 0, 0);
+      if (i < cd.Cout && g < cd.G) w = __ldg(src + (size_t)g * (N / 4));
+      d[g * TC_WROW] = w.x;
+      d[(Gp + g) * TC_WROW] = w.y;
+      d[(2 * Gp + g) * TC_WROW] = w.z;
+      d[(3 * Gp + g) * TC_WROW] = w.w;
+    }
   }
+  __shared__ long long colbase[TC_COLS];  // output offset of each column of the group, row i0 excluded
+  const size_t rowstride = (size_t)cd.bands * 2 * L * N;  // between output channels i and i + 1
 
   for (int chunk = 0; chunk * TC_COLS < cols; ++chunk) {
     const int ncols = min(TC_COLS, cols - chunk * TC_COLS);
     const int ntiles = (7 * ncols + 7) / 8;
+    const unsigned rc = (65536u + ncols - 1) / ncols;  // (p * rc) >> 16 == p / ncols for p < 128
     __syncthreads();  // the weights are staged; the previous group's Xst and Ot are no longer read
-    // inputs: Xst[uu][g][cl] = X[g][column chunk*8 + cl][u0 + uu], zero outside
-    for (int e = tid; e < TC_COLS * Gp * U4; e += TC_THREADS) {
-      const int cl = e % TC_COLS, g = (e / TC_COLS) % Gp, q4 = e / (TC_COLS * Gp);
-      uint4 x = make_uint4(0, 0, 0, 0);
-      if (g < cd.G && cl < ncols) {
-        const int col = chunk * TC_COLS + cl, bb = col >> 1, c = col & 1, b = bb / cd.bands, band = bb % cd.bands;
-        x = __ldg(reinterpret_cast<const uint4*>(c_hat + ((size_t)b * cd.n_in + (size_t)band * cd.G + g) * ct_words +
-                                                 (size_t)c * L * N + (size_t)l * N + u0) +
-                  q4);
+    // inputs: Xst[uu][g][cl] = X[g][column chunk*8 + cl][u0 + uu], zero
+    // outside; each thread owns one (column, 4-slot group) and walks g
+    {
+      constexpr int XP = TC_COLS * U4, XS = TC_THREADS / XP;
+      const int cl = tid % TC_COLS, q4 = (tid / TC_COLS) % U4, gs = tid / XP;
+      const int col = chunk * TC_COLS + cl, bb = col >> 1, c = col & 1;
+      const int b = bb / cd.bands, band = bb - b * cd.bands;  // one division per thread and group
+      const bool ok = cl < ncols;
+      const uint4* src = reinterpret_cast<const uint4*>(
+          c_hat + (ok ? ((size_t)b * cd.n_in + (size_t)band * cd.G) * ct_words + (size_t)c * L * N : 0) +
+          (size_t)l * N + u0) + q4;
+      uint32_t* d = Xst + (size_t)(4 * q4) * Gp * TC_COLS + cl;
+      for (int g = gs; g < Gp; g += XS) {
+        uint4 x = make_uint4(0, 0, 0, 0);
+        if (ok && g < cd.G) x = __ldg(src + (size_t)g * (ct_words / 4));
+        d[g * TC_COLS] = x.x;
+        d[(Gp + g) * TC_COLS] = x.y;
+        d[(2 * Gp + g) * TC_COLS] = x.z;
+        d[(3 * Gp + g) * TC_COLS] = x.w;
       }
-      uint32_t* d = Xst + ((size_t)(4 * q4) * Gp + g) * TC_COLS + cl;
-      d[0] = x.x;
-      d[(size_t)Gp * TC_COLS] = x.y;
-      d[(size_t)2 * Gp * TC_COLS] = x.z;
-      d[(size_t)3 * Gp * TC_COLS] = x.w;
+      if (tid < TC_COLS)
+        colbase[cl] = ok ? (long long)(((size_t)b * cd.n_out + band) * 2 * L * N + (size_t)c * L * N + (size_t)l * N +
+                                       u0 + (size_t)i0 * rowstride)
+                         : 0;
     }
     __syncthreads();
     int* ys = Ys + warp * TC_ROWS * (TC_N + 1);
@@ -164,20 +182,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const uint32_t* __restri
         }
       }
       __syncwarp();
-      // Y = sum_s 2^(8s) Y_s mod q: Y_0..Y_4 by shifts below 2^64, then
-      // (Y_5 + 2^8 Y_6) * (2^40 mod q)
-      for (int p = lane; p < TC_ROWS * TC_COLS; p += 32) {
-        const int ii = p / TC_COLS, cl = p % TC_COLS;
-        uint32_t y = 0;
-        if (cl < ncols) {
-          const int* v = ys + ii * (TC_N + 1) + 7 * cl;
-          uint64_t lo = 0;
+      // Y = sum_s 2^(8s) Y_s mod q for the 16 x ncols outputs (lanes on valid
+      // pairs only): Y_0..Y_4 by shifts, plus ((Y_5 + 2^8 Y_6) mod q) *
+      // (2^40 mod q), one reduction.  With Y_s < 4 * 192 * 255^2 < 2^26 (G at
+      // most 192, the shared-memory limit) the first part stays below 2^59
+      // and the second below 2^60.
+      for (int p = lane; p < TC_ROWS * ncols; p += 32) {
+        const int ii = (int)(((unsigned)p * rc) >> 16), cl = p - ii * ncols;  // p / ncols, p < 128
+        const int* v = ys + ii * (TC_N + 1) + 7 * cl;
+        uint64_t lo = 0;
 #pragma unroll
-          for (int s = 0; s < 5; ++s) lo += (uint64_t)(uint32_t)v[s] << (8 * s);
-          const uint64_t hi = (uint64_t)(uint32_t)v[5] + ((uint64_t)(uint32_t)v[6] << 8);
-          y = csub(red64(lo, lc) + red64((uint64_t)red64(hi, lc) * c40, lc), lc.q);
-        }
-        Ot[(ii * TC_COLS + cl) * UP + uu] = y;
+        for (int s = 0; s < 5; ++s) lo += (uint64_t)(uint32_t)v[s] << (8 * s);
+        const uint64_t hi = (uint64_t)(uint32_t)v[5] + ((uint64_t)(uint32_t)v[6] << 8);
+        Ot[(ii * TC_COLS + cl) * UP + uu] = red64(lo + (uint64_t)red64(hi, lc) * c40, lc);
       }
       __syncwarp();  // ys is rewritten by the next slot
     }
@@ -185,13 +202,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const uint32_t* __restri
     // rows (i, column) of the group: U consecutive slots each, as 16-byte stores
     for (int e = tid; e < TC_ROWS * TC_COLS * U4; e += TC_THREADS) {
       const int q4 = e % U4, cl = (e / U4) % TC_COLS, ii = e / (U4 * TC_COLS);
-      const int i = i0 + ii;
-      if (i < cd.Cout && cl < ncols) {
-        const int col = chunk * TC_COLS + cl, bb = col >> 1, c = col & 1, b = bb / cd.bands, band = bb % cd.bands;
-        const size_t oct = (size_t)b * cd.n_out + (size_t)i * cd.bands + band;
-        reinterpret_cast<uint4*>(y_hat + (oct * 2 + c) * L * N + (size_t)l * N + u0)[q4] =
+      if (i0 + ii < cd.Cout && cl < ncols)
+        reinterpret_cast<uint4*>(y_hat + colbase[cl] + (size_t)ii * rowstride)[q4] =
             reinterpret_cast<const uint4*>(Ot + (ii * TC_COLS + cl) * UP)[q4];
-      }
     }
   }
 }
@@ -217,12 +230,12 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
                                 MaskStore{p, (r && c == 0) ? r + oct * N : nullptr, lc});
 }
 
-// Slots per warp for a layer: 4 while the staged operands fit in 200 KB of
-// shared memory (two CTAs per SM for small G), then 2, then 1.
+// Slots per warp for a layer: the most (4, 2) that still lets two CTAs share
+// an SM (113 KB of shared memory each), else 1.
 static int tc_spw(int G) {
   const int gp = (G + TC_GK - 1) / TC_GK * TC_GK;
   for (int spw = 4; spw > 1; spw /= 2)
-    if (tc_smem_words(spw, gp) * 4 <= 200 * 1024) return spw;
+    if (tc_smem_words(spw, gp) * 4 <= 113 * 1024) return spw;
   return 1;
 }
 
@@ -244,7 +257,7 @@ static cudaError_t conv_tc(int B, const ConvDims& cd, const uint32_t* w_hat, con
 cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_hat, const uint32_t* c_hat, uint32_t* y_hat,
                            int N, const CtxConst& cc, cudaStream_t st) {
   if (B == 0 || cd.Cout == 0) return cudaSuccess;
-  if ((cd.Cout + TC_ROWS - 1) / TC_ROWS > 65535 || conv_tc_smem_bytes(cd.G) > 227 * 1024)
+  if ((cd.Cout + TC_ROWS - 1) / TC_ROWS > 65535 || conv_tc_smem_bytes(cd.G) > TC_MAX_DYN_SMEM)
     return cudaErrorInvalidConfiguration;
   switch (tc_spw(cd.G)) {
     case 4: return conv_tc<4>(B, cd, w_hat, c_hat, y_hat, N, cc, st);
@@ -260,11 +273,12 @@ static cudaError_t intt_rows_setup() {
 }
 
 cudaError_t launch_tc_setup(int logn) {
-  // the contraction kernels may use up to the per-CTA maximum of dynamic shared memory
+  // the contraction kernels may use up to the per-CTA maximum of shared
+  // memory less 1 KB kept for their static part (the column offsets)
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) ||
-      (e = cudaFuncSetAttribute(k_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) ||
-      (e = cudaFuncSetAttribute(k_conv_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)))
+  if ((e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_DYN_SMEM)) ||
+      (e = cudaFuncSetAttribute(k_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_DYN_SMEM)) ||
+      (e = cudaFuncSetAttribute(k_conv_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_DYN_SMEM)))
     return e;
   switch (logn) {
     case 11: return intt_rows_setup<11>();
