@@ -186,3 +186,18 @@ def test_tc_form_empty_batch(fg):
     wh = c.encode_weights(g, torch.zeros((4, 3, 3, 3), dtype=torch.int8, device="cuda"))
     empty = torch.empty((0, g.n_in, 2, 2, 2048), dtype=torch.int32, device="cuda")
     assert c.he_conv2d_tc(g, wh, empty, workspace=torch.empty(16, dtype=torch.int32, device="cuda")).shape[0] == 0
+
+
+def test_tc_form_refuses_g_beyond_shared_memory(fg):
+    """G = 200 input ciphertexts do not fit one CTA's shared memory in the
+    tensor-core form: refused on the host before any launch; the plain form
+    still takes the layer."""
+    N, L = 2048, 1
+    c = ctx(fg, N, L)
+    g = c.geom(1600, 1, 14, 14, 3, 1, 1)  # 8 channels of 16 x 16 padded rows per ciphertext
+    assert g.G == 200
+    wh = torch.zeros((L, g.Cout, g.G, N), dtype=torch.int32, device="cuda")
+    ct = torch.zeros((1, g.n_in, 2, L, N), dtype=torch.int32, device="cuda")
+    with pytest.raises(fg.FlashError, match="shared memory"):
+        c.he_conv2d_tc(g, wh, ct)
+    assert int(c.he_conv2d(g, wh, ct).abs().sum()) == 0
