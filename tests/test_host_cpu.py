@@ -130,3 +130,22 @@ def test_clock_record_uses_the_timed_region_reads():
     assert cs.summary()["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
     cs.nvml, cs.win = None, []
     assert cs.summary()["reasons"] == ["no nvidia-smi samples"]  # neither source: said so, no number
+
+
+def test_reference_arm_prints_one_contract_line(oracle):
+    """bench.py --impl reference (the oracle on the host cores) prints one
+    JSON line with the keys the benchmark contract asks of that arm."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "single",
+                          "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "layers/s" and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
