@@ -253,6 +253,19 @@ def run_reference_x2x(args):
 # ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
+def gpu_uuid(device_index):
+    """'GPU-<uuid>' of a CUDA device as NVML and nvidia-smi name it, or None."""
+    try:
+        import torch
+        u = getattr(torch.cuda.get_device_properties(device_index), "uuid", None)
+        if u is None:
+            return None
+        u = str(u)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
 class NvmlClock:
     """SM clock and clock-event reasons of one GPU, read through NVML (the
     driver's management library; read-only queries, nothing is set)."""
@@ -260,14 +273,17 @@ class NvmlClock:
     REASONS = ((0x4, "sw_power_cap"), (0x8, "hw_slowdown"), (0x20, "sw_thermal_slowdown"),
                (0x40, "hw_thermal_slowdown"))
 
-    def __init__(self, index):
+    def __init__(self, index, uuid=None):
         import ctypes
         self.ct = ctypes
         self.lib = ctypes.CDLL("libnvidia-ml.so.1")
         if self.lib.nvmlInit_v2() != 0:
             raise OSError("nvmlInit failed")
         self.h = ctypes.c_void_p()
-        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+        # by UUID when known (NVML numbers every GPU of the machine, whatever
+        # CUDA_VISIBLE_DEVICES selects), else by index
+        if not (uuid and self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) == 0) and \
+                self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
             raise OSError("no NVML handle")
         self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
             self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
@@ -293,12 +309,13 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index):
-        self.dev = device_index
+        uuid = gpu_uuid(device_index)
+        self.dev = uuid or device_index  # nvidia-smi --id takes either
         self.proc = None
         self.samples = []
         self.win = []
         try:
-            self.nvml = NvmlClock(device_index)
+            self.nvml = NvmlClock(device_index, uuid)
         except Exception:
             self.nvml = None
 
