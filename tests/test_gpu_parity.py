@@ -386,6 +386,40 @@ def test_stack_equals_single_layer_and_oracle(fg, oracle, N, L, layers, kernel):
     c.stack_kernel = fg.FL_STACK_PER_LAYER
 
 
+@pytest.mark.parametrize("kernel", ["per_layer", "persistent", "queue"])
+def test_stack_at_the_layer_limit(fg, kernel):
+    """FL_STACK_MAX_LAYERS (64) layers of four alternating shapes, some
+    masked, some with B = 0, in one stack call: every output equals the
+    single-layer call; one layer more is refused before any launch."""
+    N, L = 2048, 2
+    c = ctx(fg, N, L)
+    c.stack_kernel = {"per_layer": fg.FL_STACK_PER_LAYER, "persistent": fg.FL_STACK_PERSISTENT,
+                      "queue": fg.FL_STACK_QUEUE}[kernel]
+    shapes = [(3, 4, 8, 8, 3, 1, 1), (8, 5, 10, 10, 1, 2, 0), (20, 3, 6, 6, 3, 1, 1), (4, 17, 12, 12, 3, 2, 1)]
+    geoms = [c.geom(*sh) for sh in shapes]
+    whs = [c.encode_weights(g, dev(synth.weights(96, (g.Cout, g.Cin, g.k, g.k), k), torch.int8))
+           for k, g in enumerate(geoms)]
+    specs, want = [], []
+    for li in range(fg.FL_STACK_MAX_LAYERS):
+        g, wh = geoms[li % 4], whs[li % 4]
+        B = (li % 3) if li % 7 else 0
+        ct = dev(synth.raw_ciphertexts(97, c.primes, (B, g.n_in, 2, L, N), li))
+        r = dev(synth.masks(97, (B, g.n_out, N), T, li)) if li % 2 else None
+        out = torch.full((B, g.n_out, 2, L, N), -1, dtype=torch.int32, device="cuda")
+        specs.append({"g": g, "w_hat": wh, "ct_in": ct, "r": r, "out": out})
+        want.append(c.he_conv2d(g, wh, ct, r=r) if B else out.clone())
+    arr = c.stack_layers(specs)
+    ws = c.stack_workspace(arr)
+    c.he_conv2d_stack(arr, ws)
+    assert c.stack_error(ws) == 0
+    for sp, w in zip(specs, want):
+        assert torch.equal(sp["out"], w)
+    over = c.stack_layers(specs + specs[:1])
+    with pytest.raises(fg.FlashError, match="n_layers"):
+        c.he_conv2d_stack(over, ws)
+    c.stack_kernel = fg.FL_STACK_PER_LAYER
+
+
 def test_stack_empty(fg):
     c = ctx(fg, 4096, 2)
     arr = c.stack_layers([])
