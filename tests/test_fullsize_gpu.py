@@ -1,0 +1,67 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times: the whole ResNet-18 CIFAR conv stack (20 layers, N = 8192, L = 3) as
+one stack call (input NTT of every layer, then the fused contraction /
+inverse NTT / mask kernel) captured in a CUDA graph and replayed.  At B = 1
+it runs on the queue kernel, at B = 64 on per-layer launches, the kernels the
+autotuner keeps for these workloads.  Sampled outputs, two output channels of
+every layer for the last image, are compared bit for bit with the oracle's
+Algorithm 1 plus the mask."""
+import numpy as np
+import pytest
+
+from paper_2401_16732_gb300 import synth
+from paper_2401_16732_gb300.workloads import WORKLOADS
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+T = 65537
+
+
+@pytest.fixture(scope="module")
+def fg():
+    from paper_2401_16732_gb300 import flashgpu
+    return flashgpu
+
+
+@pytest.mark.parametrize("config,kernel", [("resnet18", "queue"), ("resnet18-b64", "per_layer")])
+def test_full_stack_in_the_bench_configuration(fg, oracle, config, kernel):
+    wl = WORKLOADS[config]
+    N, L, B = wl.N, wl.L, wl.B
+    c = fg.Context(N, L)
+    c.stack_kernel = {"queue": fg.FL_STACK_QUEUE, "per_layer": fg.FL_STACK_PER_LAYER}[kernel]
+    specs, filters = [], []
+    for li, shape in enumerate(wl.layers):
+        g = c.geom(*shape)
+        w = synth.weights(5, (g.Cout, g.Cin, g.k, g.k), li)
+        specs.append({"g": g, "w_hat": c.encode_weights(g, torch.from_numpy(w).to(torch.int8).cuda()),
+                      "ct_in": synth.device_uniform_residues(5, c.primes, (B, g.n_in, 2, L, N), li),
+                      "r": synth.device_masks(5, (B, g.n_out, N), T, li),
+                      "out": torch.empty((B, g.n_out, 2, L, N), dtype=torch.int32, device="cuda")})
+        filters.append((shape, w))
+    arr = c.stack_layers(specs)
+    ws = c.stack_workspace(arr)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        c.he_conv2d_stack(arr, ws, stream=stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        c.he_conv2d_stack(arr, ws, stream=stream)
+    for sp in specs:
+        sp["out"].fill_(-1)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        graph.replay()
+    stream.synchronize()
+    assert c.stack_error(ws) == 0
+    b = B - 1
+    for li, (sp, (shape, w)) in enumerate(zip(specs, filters)):
+        g = sp["g"]
+        geo = oracle.geometry(N, *shape)
+        ct_b = sp["ct_in"][b].cpu().numpy().view(np.uint32)
+        r_b = sp["r"][b].cpu().numpy().view(np.uint32)
+        got = sp["out"][b].cpu().numpy().view(np.uint32)
+        for i in sorted({li % g.Cout, g.Cout - 1}):
+            sl = slice(i * g.bands, (i + 1) * g.bands)
+            want = oracle.mask(oracle.conv_alg1(ct_b, w, geo, c.primes, i, i + 1), r_b[sl], c.primes)
+            assert (got[sl] == want).all(), (config, li, i)
