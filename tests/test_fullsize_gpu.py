@@ -1,11 +1,12 @@
-"""Parity at the benchmark's full sizes, in the launch configuration bench.py
-times: the whole ResNet-18 CIFAR conv stack (20 layers, N = 8192, L = 3) as
+"""Parity at the benchmark's full sizes, in the launch configurations bench.py
+times.  The whole ResNet-18 CIFAR conv stack (20 layers, N = 8192, L = 3) as
 one stack call (input NTT of every layer, then the fused contraction /
 inverse NTT / mask kernel) captured in a CUDA graph and replayed.  At B = 1
 it runs on the queue kernel, at B = 64 on per-layer launches, the kernels the
 autotuner keeps for these workloads.  Sampled outputs, two output channels of
 every layer for the last image, are compared bit for bit with the oracle's
-Algorithm 1 plus the mask."""
+Algorithm 1 plus the mask.  The x^2 + x server rounds run over the 1808
+activation ciphertexts of bench.py's x2x workload."""
 import numpy as np
 import pytest
 
@@ -65,3 +66,31 @@ def test_full_stack_in_the_bench_configuration(fg, oracle, config, kernel):
             sl = slice(i * g.bands, (i + 1) * g.bands)
             want = oracle.mask(oracle.conv_alg1(ct_b, w, geo, c.primes, i, i + 1), r_b[sl], c.primes)
             assert (got[sl] == want).all(), (config, li, i)
+
+
+def test_x2x_rounds_at_the_bench_size(fg, oracle):
+    """The x^2 + x server rounds over the benchmark's 1808 activation
+    ciphertexts (every packed input of ResNet-18 CIFAR's convolutions but the
+    stem, B = 16, N = 8192, L = 3), launched as bench.py does; the first, a
+    middle and the last ciphertext against the oracle's two rounds."""
+    wl = WORKLOADS["resnet18"]
+    N, L = wl.N, wl.L
+    c = fg.Context(N, L)
+    n = 16 * sum(c.geom(*sh).n_in for sh in wl.layers[1:])
+    assert n == 1808
+    r, v = synth.device_masks(6, (n, N), T, 1), synth.device_masks(6, (n, N), T, 2)
+    prep = c.x2x_prepare(r, v)
+    ct_z, ct_x, ct_y = (synth.device_uniform_residues(6, c.primes, (n, 2, L, N), k) for k in (3, 4, 5))
+    stream = torch.cuda.Stream()
+    out1, out2 = torch.empty_like(ct_z), torch.empty_like(ct_z)
+    torch.cuda.synchronize()  # inputs and prepared rows come from the default stream
+    c.x2x_round1(prep, ct_z, out1, stream=stream)
+    c.x2x_round2(prep, ct_x, ct_y, out2, stream=stream)
+    stream.synchronize()
+
+    def h(t, k):
+        return t[k:k + 1].cpu().numpy().view(np.uint32)
+
+    for k in (0, n // 2, n - 1):
+        assert (h(out1, k) == oracle.x2x_server_round1(h(ct_z, k), h(r, k), h(v, k), c.primes)).all(), k
+        assert (h(out2, k) == oracle.x2x_server_round2(h(ct_x, k), h(ct_y, k), h(r, k), h(v, k), c.primes)).all(), k
