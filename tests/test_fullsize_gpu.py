@@ -1,7 +1,7 @@
 """Parity at the benchmark's full sizes, in the launch configurations bench.py
-times.  The whole ResNet-18 CIFAR conv stack (20 layers, N = 8192, L = 3) as
-one stack call (input NTT of every layer, then the fused contraction /
-inverse NTT / mask kernel) captured in a CUDA graph and replayed.  At B = 1
+times.  The whole ResNet-18 CIFAR conv stack (20 layers, N = 8192, L = 3)
+runs as one stack call (input NTT of every layer, then the fused contraction
+/ inverse NTT / mask kernel) captured in a CUDA graph and replayed.  At B = 1
 it runs on the queue kernel, at B = 64 on per-layer launches, the kernels the
 autotuner keeps for these workloads.  Sampled outputs, two output channels of
 every layer for the last image, are compared bit for bit with the oracle's
