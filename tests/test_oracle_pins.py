@@ -472,3 +472,40 @@ def test_pmult_lifts_plaintexts_centred(oracle):
             a = ct[0, c, l].astype(np.int64)
             want = np.concatenate([[(q - a[-1]) % q], a[:-1]])
             assert (shifted[0, c, l] == want).all()
+
+
+def test_plaintext_addition_and_ciphertext_subtraction_are_homomorphic(oracle):
+    """decrypt(add_plain(Enc(m1), m2)) = m1 + m2 mod t and
+    decrypt(sub_ct(Enc(m1), Enc(m2))) = m1 - m2 mod t (fresh noise stays far
+    inside the decryption bound).  Delta = floor(q/t) satisfies
+    Delta * t + (q mod t) = q, so every residue Delta_l * t + (q mod t) is 0
+    mod q_l."""
+    N, L = 256, 2
+    primes = oracle.find_primes(N, L)
+    s = synth.secret_key(81, N)
+    m1, m2 = synth.masks(81, (1, N), T, 1), synth.masks(81, (1, N), T, 2)
+    ct1 = oracle.encrypt(s, synth.uniform_residues(81, primes, (1, L, N), 1), synth.cbd_noise(81, (1, N), 1), m1,
+                         primes)
+    ct2 = oracle.encrypt(s, synth.uniform_residues(81, primes, (1, L, N), 2), synth.cbd_noise(81, (1, N), 2), m2,
+                         primes)
+    m1, m2 = m1.astype(np.int64), m2.astype(np.int64)
+    assert (oracle.decrypt(s, oracle.add_plain(ct1, m2, primes), primes) == (m1 + m2) % T).all()
+    assert (oracle.decrypt(s, oracle.sub_ct(ct1, ct2, primes), primes) == (m1 - m2) % T).all()
+    q = math.prod(primes)
+    for d, ql in zip(oracle.delta_residues(primes, T), primes):
+        assert (d * T + q % T) % ql == 0
+
+
+def test_centred_lift(oracle):
+    """lift_centered sends [0, t) to its representatives in (-t/2, t/2],
+    written mod q: each is congruent to its input mod t and the ends of the
+    range map to 0, t//2, -(t//2) and -1."""
+    q = oracle.find_primes(2048, 1)[0]
+    m = np.array([0, 1, T // 2, T // 2 + 1, T - 1])
+    got = oracle.lift_centered(m, q).astype(np.int64)
+    ints = np.where(got > q // 2, got - q, got)
+    assert list(ints) == [0, 1, T // 2, -(T // 2), -1]
+    r = synth.masks(82, (4096,), T).astype(np.int64)
+    li = oracle.lift_centered(r, q).astype(np.int64)
+    li = np.where(li > q // 2, li - q, li)
+    assert (np.abs(li) <= T // 2).all() and ((li - r) % T == 0).all()
