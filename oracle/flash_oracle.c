@@ -77,22 +77,24 @@ void or_negacyclic_mul(const uint32_t *a, const uint32_t *b, uint32_t N,
 
 /* ------------------------------------------------------------------ */
 /* DRot (Eq. 2, proof in Appendix A): c'(x) = c(x) * x^{-step} mod       */
-/* x^N + 1, i.e. coefficient i of the result is                          */
-/* (-1)^floor((i+step)/N) * c[(i+step) mod N].  Every step Algorithm 1    */
-/* takes lies in [0, N), so i + step < 2N wraps at most once.             */
+/* x^N + 1 for any step >= 0.  Since x^N = -1, x^{2N} = 1, so the step    */
+/* counts modulo 2N, and coefficient i of the result is                  */
+/* (-1)^floor((i+e)/N) * c[(i+e) mod N] with e = step mod 2N.  Here       */
+/* i + e < 3N, so the sign flips once per multiple of N passed (zero, one */
+/* or two times).  Every output coefficient is written.                  */
 /* ------------------------------------------------------------------ */
 static int64_t drot_coeff(const uint32_t *c, uint32_t N, uint32_t step,
                           uint32_t i)
 {
-    uint32_t idx = i + step;
-    if (idx < N) return (int64_t)c[idx];
-    return -(int64_t)c[idx - N];
+    uint64_t idx = (uint64_t)i + step % (2ull * N);
+    uint64_t wraps = idx / N;
+    int64_t v = (int64_t)c[idx % N];
+    return (wraps & 1) ? -v : v;
 }
 
 void or_drot(const uint32_t *c, uint32_t N, uint32_t q, uint32_t step,
              uint32_t *out)
 {
-    if (step >= N) return; /* outside the domain Algorithm 1 uses */
     for (uint32_t i = 0; i < N; ++i) {
         int64_t v = drot_coeff(c, N, step, i);
         out[i] = (uint32_t)(v < 0 ? v + (int64_t)q : v) % q;

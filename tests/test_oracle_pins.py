@@ -117,6 +117,29 @@ def test_drot_is_multiplication_by_x_minus_step(oracle):
         assert list(oracle.drot(c, step, q)) == list(oracle.negacyclic_mul(mono, c, q))
 
 
+def test_drot_beyond_one_wrap(oracle):
+    """Eq. 2 for steps of N and more: x^N = -1, so x^{-step} is the monomial
+    x^e with e = -step mod 2N, read as -x^{e-N} when e >= N.  Steps compose:
+    DRot(DRot(c, a), b) = DRot(c, a + b), and a step of 2N is the identity.
+    Every coefficient is written (no step leaves the output untouched)."""
+    N, q = 16, 97
+    c = np.random.default_rng(3).integers(1, q, N)
+    for step in (N - 1, N, N + 3, 2 * N - 1, 2 * N, 2 * N + 5, 3 * N + 1):
+        e = (-step) % (2 * N)
+        mono = np.zeros(N, np.int64)
+        if e < N:
+            mono[e] = 1
+        else:
+            mono[e - N] = q - 1
+        got = oracle.drot(c, step, q)
+        assert list(got) == list(oracle.negacyclic_mul(mono, c, q)), step
+        assert (got != 0).all()  # c has no zero coefficient, so neither has its shift
+    for a_step, b_step in ((3, N - 1), (N, N), (N + 2, 2 * N - 3)):
+        two = oracle.drot(oracle.drot(c, a_step, q), b_step, q)
+        assert list(two) == list(oracle.drot(c, a_step + b_step, q))
+    assert list(oracle.drot(c, 2 * N, q)) == list(c)
+
+
 def test_drot_theorem_on_ciphertexts(oracle):
     """Appendix A: decrypting DRot(ct, step) gives the signed shift of m and
     the noise norm is unchanged."""
