@@ -39,12 +39,44 @@ ALU_BFLY_PEAK = 152 * 4 * 16 * 2.07e9 / 4
 # Direct form: one signed 32x32->64-bit multiply-add per lane per clock on the
 # 16-lane integer multiply pipe (an upper bound).
 DIRECT_MAC_PEAK = 152 * 4 * 16 * 2.07e9
-# mma.sync m16n8k32 u8 x u8 -> s32 multiply-adds/s measured on this GPU by the
-# tensor-core probe (profiles/tc_rates_gb300.md)
+# mma.sync m16n8k32 u8 x u8 -> s32 multiply-adds/s measured on this GPU by an
+# instruction-rate microbenchmark
 TC_U8_PEAK = 7.9e13
-# DRAM bytes (read + write) of one step's launches of the dominant kernel, from
-# one ncu capture of the same command (profiles/); a kernel change voids them.
-TRAFFIC = {("resnet18", "queue"): 3.354e9, ("x2x", "round1"): 1.032e9, ("x2x", "round2"): 1.071e9}
+# DRAM bytes (read + write) of one step's launches of the dominant kernel,
+# from one ncu capture of the same command, each with the SHA-256 (first 16
+# hex digits) of the kernel sources it was captured from.  The figure is
+# reported only while those sources still hash the same; any edit to them
+# makes it null until it is captured again.
+KERNEL_SOURCES = {
+    "queue": ("fl_kernels.cu", "fl_device.cuh", "fl_launch.h"),
+    "round1": ("fl_act.cu", "fl_device.cuh", "fl_launch.h"),
+    "round2": ("fl_act.cu", "fl_device.cuh", "fl_launch.h"),
+}
+TRAFFIC = {}
+
+
+def kernel_source_hash(kernel):
+    """SHA-256 over the named kernel's source files (name and bytes, in a
+    fixed order); None for a kernel without a recorded source set."""
+    import hashlib
+    files = KERNEL_SOURCES.get(kernel)
+    if files is None:
+        return None
+    h = hashlib.sha256()
+    for name in files:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_2401_16732_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(config, kernel):
+    """ncu DRAM bytes per step for (config, kernel) if they were captured
+    from the current sources, else None."""
+    rec = TRAFFIC.get((config, kernel))
+    if rec is None or rec[1] != kernel_source_hash(kernel):
+        return None
+    return rec[0]
 
 
 def peaks():
@@ -655,7 +687,7 @@ def run_gpu(args, wl, rank, world, local_rank):
     kname = {"persistent": "k_stack (persistent, warp-specialised, all layers)",
              "queue": "k_conv_queue (resident CTAs over one queue of all layers' items)"}.get(
         tuned["kernel"], "k_conv_intt (one launch per layer)") + ": contraction + inverse NTT + mask"
-    traffic = TRAFFIC.get((args.config, tuned["kernel"]))
+    traffic = traffic_of(args.config, tuned["kernel"])
     hbm_line = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_source": peak_kind, "traffic": traffic}
     alu_line = {"bound": "alu", "achieved": achieved_bfly / 1e12, "peak": ALU_BFLY_PEAK / 1e12,
@@ -850,14 +882,14 @@ def run_x2x(args, rank, world, local_rank):
     roof = {"bound": "alu", "achieved": alu1 / 1e12, "peak": ALU_BFLY_PEAK / 1e12, "unit": "T butterflies/s",
             "frac": alu1 / ALU_BFLY_PEAK,
             "peak_source": "derived: 152 SMs x 4 x 16 ALU lanes x 2.07 GHz / 4 ALU ops per butterfly",
-            "traffic": TRAFFIC.get(("x2x", "round1")),
+            "traffic": traffic_of("x2x", "round1"),
             "kernel": "k_x2x_round1: forward NTT x2, NTT-domain PMult, inverse NTT x2, + encode(v)",
             "kernel_ms_per_step": k1, "algorithmic_butterflies_per_step": bfly1,
             "hbm_view": {"achieved": hbm1, "peak": hbm, "frac": hbm1 / hbm, "algorithmic_bytes_per_step": bytes1},
             "other_kernels": [{"kernel": "k_x2x_round2: <X> - <Y> + Delta*(r^2 - r + v)", "bound": "hbm",
                                "kernel_ms_per_step": k2, "achieved": hbm2, "peak": hbm, "unit": "GB/s",
                                "frac": hbm2 / hbm, "peak_source": peak_kind, "algorithmic_bytes_per_step": bytes2,
-                               "traffic": TRAFFIC.get(("x2x", "round2"))}]}
+                               "traffic": traffic_of("x2x", "round2")}]}
     line = {
         "metric": "x^2+x activations/s (server rounds 1+2)", "value": world * acts * args.steps / (ms * 1e-3),
         "unit": "activations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

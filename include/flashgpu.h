@@ -344,9 +344,11 @@ int fl_mod_switch(fl_ctx *ctx, int n, const uint32_t *ct_in_dev, int L_out, uint
  *   process exits.  The call needs B*n_in*2*L*N*4 bytes of it
  *   (fl_he_conv2d_workspace_bytes); a larger call is rejected with
  *   FL_ERR_ARG and a message, before any work is queued.
- * - The first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture begins.
+ * - Every call looks up the array's device address (cudaGetSymbolAddress)
+ *   with the context's device current, so the address stays right after a
+ *   device reset.  The first call on a device may load the library's device
+ *   code for that lookup; make that first call before any stream capture
+ *   begins.
  * - Calls share the array: two calls whose work overlaps on the GPU (other
  *   streams, or other threads) race on it and give undefined results;
  *   order them (one stream, or events).  The array keeps the last call's
@@ -416,14 +418,6 @@ int fl_x2x_round2(fl_ctx *ctx, int n, const uint32_t *prep_dev, const uint32_t *
  * H, W and N (FL_ERR_SHAPE otherwise).  The buffers must not overlap. */
 int fl_repack_outputs(const fl_conv_geom *prev, const fl_conv_geom *next, int B, const uint32_t *src_dev,
                       uint32_t *dst_dev, void *stream);
-
-/* Measured multiply-add rate of a warp-level tensor-core instruction on the
- * current device: kind 0 = mma.sync m16n8k32 u8 x u8 -> s32, kind 1 =
- * mma.sync m16n8k16 bf16 x bf16 -> f32.  Four 256-thread CTAs per SM, each
- * warp issuing `iters` rounds of 8 independent MMAs on registers.  This is
- * the ceiling of a byte-split contraction built on them (tcgen05 has no
- * integer kind on sm_103a). */
-int fl_probe_mma_rate(int kind, int iters, double *macs_per_s);
 
 /* ---- Building blocks, exposed for tests ---- */
 

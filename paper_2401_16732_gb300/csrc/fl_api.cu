@@ -799,19 +799,6 @@ int fl_stack_error(const void* workspace_dev, void* stream, uint64_t* error_host
   return v ? fail(FL_ERR_TIMEOUT, "a bounded device wait gave up (error word 0x%llx)", v) : FL_OK;
 }
 
-int fl_probe_mma_rate(int kind, int iters, double* macs_per_s) {
-  if (!macs_per_s || (kind != 0 && kind != 1) || iters < 1) return fail(FL_ERR_ARG, "kind=%d iters=%d", kind, iters);
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return cuda_fail(e, "device query");
-  float ms = 0.f;
-  double macs = 0.0;
-  if ((e = fl::probe_mma_rate(kind, sms * 4, iters, &ms, &macs)) != cudaSuccess) return cuda_fail(e, "mma probe");
-  *macs_per_s = ms > 0.f ? macs / (ms * 1e-3) : 0.0;
-  return FL_OK;
-}
-
 int fl_selftest_wait_timeout(void* stream, uint64_t* error_host) {
   if (!error_host) return fail(FL_ERR_ARG, "null pointer");
   unsigned long long* d = nullptr;

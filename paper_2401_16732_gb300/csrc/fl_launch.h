@@ -121,9 +121,6 @@ cudaError_t launch_w_scatter(const int8_t* w, uint32_t* w_hat, const GeomDims& g
 cudaError_t launch_sk_expand(const int8_t* s, uint32_t* out, int N, const CtxConst& cc,
                              cudaStream_t st);
 
-// tensor-core instruction rates (fl_tcprobe.cu)
-cudaError_t probe_mma_rate(int kind, int blocks, int iters, float* ms, double* macs);
-
 // modulus switching (fl_modswitch.cu)
 cudaError_t launch_mod_switch(const uint32_t* in, uint32_t* out, long long rows, int N, const ModSwitchConst& mc,
                               cudaStream_t st);

@@ -13,7 +13,6 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "../../include/flashgpu.h"
 #include "fl_launch.h"
@@ -24,26 +23,18 @@ namespace {
 // (B * n_in * 2 * L * N 32-bit words).
 __device__ __align__(256) static uint32_t g_noalloc_scratch[FL_NOALLOC_SCRATCH_BYTES / 4];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-uint32_t* g_scratch_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
-
 // Host code cannot use &g_noalloc_scratch as a device address (it names a
-// host-side shadow).  Resolve the real address once per device, with that
-// device current.
+// host-side shadow).  Resolve the real address with the context's device
+// current.  The lookup runs on every call: it is a table lookup once the
+// library's device code is loaded, and it stays right after a device reset
+// (cudaDeviceReset), which reloads the code at a new address.  On the first
+// call on a device it may load that code, so make the first call before any
+// stream capture begins.
 cudaError_t scratch_for_current_device(uint32_t** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<uint32_t*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<uint32_t*>(p);
   return cudaSuccess;
 }
 

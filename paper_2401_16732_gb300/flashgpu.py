@@ -84,7 +84,6 @@ _SIGS = {
     "fl_x2x_round1": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
     "fl_x2x_round2": ([_vp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "fl_repack_outputs": ([_gp, _gp, _i, _vp, _vp, _vp], _i),
-    "fl_probe_mma_rate": ([_i, _i, ctypes.POINTER(ctypes.c_double)], _i),
     "fl_selftest_wait_timeout": ([_vp, ctypes.POINTER(ctypes.c_uint64)], _i),
     "fl_ntt_forward": ([_vp, _i, _vp, _vp], _i),
     "fl_ntt_inverse": ([_vp, _i, _vp, _vp], _i),
@@ -135,13 +134,6 @@ def _dev_u32(t: torch.Tensor, shape, name):
     if tuple(t.shape) != tuple(shape):
         raise FlashError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
     return t
-
-
-def probe_mma_rate(kind: int, iters: int = 4096) -> float:
-    """Measured multiply-adds/s of mma.sync u8 (kind 0) or bf16 (kind 1)."""
-    v = ctypes.c_double()
-    _check(_lib.fl_probe_mma_rate(kind, iters, ctypes.byref(v)))
-    return v.value
 
 
 def selftest_wait_timeout(stream=None) -> tuple[int, int]:
@@ -317,7 +309,13 @@ class Context:
         """fl_he_conv2d_mask without a workspace: the library's fixed scratch
         array is used instead (FL_NOALLOC_SCRATCH_BYTES; calls must not
         overlap on the GPU).  Allocates nothing on the device; `out` is the
-        caller's [B][n_out][2][L][N] buffer."""
+        caller's [B][n_out][2][L][N] buffer.  Every buffer's dtype, device,
+        contiguity and shape is checked before the call."""
+        B = ct_in.shape[0]
+        _dev_u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
+        _dev_u32(w_hat, (self.L, g.Cout, g.G, self.N), "w_hat")
+        _dev_u32(r, (B, g.n_out, self.N), "r")
+        _dev_u32(out, (B, g.n_out, 2, self.L, self.N), "out")
         _check(_lib.fl_he_conv2d_mask_noalloc(self.h, ctypes.byref(g), ct_in.shape[0], _ptr(w_hat), _ptr(ct_in),
                                               _ptr(r), _ptr(out), _stream(stream)))
         return out

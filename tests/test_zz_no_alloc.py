@@ -37,11 +37,34 @@ def test_noalloc_equals_workspace_entry_point_on_two_calls(N, L, shape, B):
         wh = c.encode_weights(g, _dev(w, torch.int8))
         want = c.he_conv2d(g, wh, ct, r=r)  # fl_he_conv2d_mask with a workspace
         out = torch.full_like(want, -1)
-        before = torch.cuda.memory_allocated()
-        c.he_conv2d_mask_noalloc(g, wh, ct, r, out)
-        assert torch.cuda.memory_allocated() == before
         torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        free_before, _ = torch.cuda.mem_get_info()  # the driver's count: sees a cudaMalloc inside the library too
+        c.he_conv2d_mask_noalloc(g, wh, ct, r, out)
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == before
+        if call == 1:
+            # the first call may load the library's device code (the scratch
+            # array comes with it); from then on the device's free memory
+            # must not move
+            assert torch.cuda.mem_get_info()[0] == free_before
         assert torch.equal(out, want), f"call {call}"
+
+
+def test_noalloc_checks_buffer_shapes_before_the_call():
+    from paper_2401_16732_gb300 import flashgpu as fg
+    c = fg.Context(4096, 2, T)
+    g = c.geom(16, 16, 16, 16, 3, 1, 1)
+    wh = torch.zeros((2, g.Cout, g.G, 4096), dtype=torch.int32, device="cuda")
+    ct = torch.zeros((1, g.n_in, 2, 2, 4096), dtype=torch.int32, device="cuda")
+    r = torch.zeros((1, g.n_out, 4096), dtype=torch.int32, device="cuda")
+    out = torch.zeros((1, g.n_out, 2, 2, 4096), dtype=torch.int32, device="cuda")
+    with pytest.raises(fg.FlashError, match="^out:"):
+        c.he_conv2d_mask_noalloc(g, wh, ct, r, out[:, :-1])  # one output ciphertext short
+    with pytest.raises(fg.FlashError, match="^r:"):
+        c.he_conv2d_mask_noalloc(g, wh, ct, r.cpu(), out)  # mask on the host
+    with pytest.raises(fg.FlashError, match="^w_hat:"):
+        c.he_conv2d_mask_noalloc(g, wh[:, :, :, :2048], ct, r, out)
 
 
 def test_noalloc_rejects_calls_beyond_its_scratch():
