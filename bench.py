@@ -47,12 +47,16 @@ TC_U8_PEAK = 7.9e13
 # hex digits) of the kernel sources it was captured from.  The figure is
 # reported only while those sources still hash the same; any edit to them
 # makes it null until it is captured again.
-KERNEL_SOURCES = {
-    "queue": ("fl_kernels.cu", "fl_device.cuh", "fl_launch.h"),
-    "round1": ("fl_act.cu", "fl_device.cuh", "fl_launch.h"),
-    "round2": ("fl_act.cu", "fl_device.cuh", "fl_launch.h"),
+KERNEL_SOURCES = {  # the kernel's own file and the shared device header
+    "queue": ("fl_kernels.cu", "fl_device.cuh"),
+    "round1": ("fl_act.cu", "fl_device.cuh"),
+    "round2": ("fl_act.cu", "fl_device.cuh"),
 }
-TRAFFIC = {}
+TRAFFIC = {  # (config, kernel): (bytes per step, source hash at capture)
+    ("resnet18", "queue"): (3.354e9, "62ede15b38b67d2f"),
+    ("x2x", "round1"): (1.032e9, "a51b3f0fe9cceca3"),
+    ("x2x", "round2"): (1.071e9, "a51b3f0fe9cceca3"),
+}
 
 
 def kernel_source_hash(kernel):
@@ -689,7 +693,8 @@ def run_gpu(args, wl, rank, world, local_rank):
         tuned["kernel"], "k_conv_intt (one launch per layer)") + ": contraction + inverse NTT + mask"
     traffic = traffic_of(args.config, tuned["kernel"])
     hbm_line = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_source": peak_kind, "traffic": traffic}
+                "peak_source": peak_kind, "traffic": traffic,
+                "kernel_source_sha256_16": kernel_source_hash(tuned["kernel"])}
     alu_line = {"bound": "alu", "achieved": achieved_bfly / 1e12, "peak": ALU_BFLY_PEAK / 1e12,
                 "unit": "T butterflies/s", "frac": achieved_bfly / ALU_BFLY_PEAK,
                 "peak_source": "derived: 152 SMs x 4 x 16 ALU lanes x 2.07 GHz / 4 ALU ops per butterfly"}

@@ -3,9 +3,12 @@ times.  The whole ResNet-18 CIFAR conv stack (20 layers, N = 8192, L = 3)
 runs as one stack call (input NTT of every layer, then the fused contraction
 / inverse NTT / mask kernel) captured in a CUDA graph and replayed.  At B = 1
 it runs on the queue kernel, at B = 64 on per-layer launches, the kernels the
-autotuner keeps for these workloads.  Sampled outputs, two output channels of
-every layer for the last image, are compared bit for bit with the oracle's
-Algorithm 1 plus the mask.  The x^2 + x server rounds run over the 1808
+autotuner keeps for these workloads; the ResNet-50 ImageNet stack (53
+layers, N = 16384, L = 4, B = 8) runs on per-layer launches too.  The
+tensor-core form runs the batched stacks per layer as bench.py --form tc
+does.  Sampled outputs, two output channels of every layer for the last
+image, are compared bit for bit with the oracle's Algorithm 1 plus the
+mask.  The x^2 + x server rounds run over the 1808
 activation ciphertexts of bench.py's x2x workload."""
 import numpy as np
 import pytest
@@ -24,30 +27,67 @@ def fg():
     return flashgpu
 
 
-@pytest.mark.parametrize("config,kernel", [("resnet18", "queue"), ("resnet18-b64", "per_layer")])
-def test_full_stack_in_the_bench_configuration(fg, oracle, config, kernel):
-    wl = WORKLOADS[config]
+def _bench_layers(c, wl, seed):
+    """Every layer of a workload as bench.py sets it up: encoded weights,
+    fresh uniform-residue inputs and masks of the layer's shape, and output
+    buffers; returns the layer specs and the int8 filters."""
     N, L, B = wl.N, wl.L, wl.B
-    c = fg.Context(N, L)
-    c.stack_kernel = {"queue": fg.FL_STACK_QUEUE, "per_layer": fg.FL_STACK_PER_LAYER}[kernel]
     specs, filters = [], []
     for li, shape in enumerate(wl.layers):
         g = c.geom(*shape)
-        w = synth.weights(5, (g.Cout, g.Cin, g.k, g.k), li)
+        w = synth.weights(seed, (g.Cout, g.Cin, g.k, g.k), li)
         specs.append({"g": g, "w_hat": c.encode_weights(g, torch.from_numpy(w).to(torch.int8).cuda()),
-                      "ct_in": synth.device_uniform_residues(5, c.primes, (B, g.n_in, 2, L, N), li),
-                      "r": synth.device_masks(5, (B, g.n_out, N), T, li),
+                      "ct_in": synth.device_uniform_residues(seed, c.primes, (B, g.n_in, 2, L, N), li),
+                      "r": synth.device_masks(seed, (B, g.n_out, N), T, li),
                       "out": torch.empty((B, g.n_out, 2, L, N), dtype=torch.int32, device="cuda")})
         filters.append((shape, w))
-    arr = c.stack_layers(specs)
-    ws = c.stack_workspace(arr)
+    return specs, filters
+
+
+def _replay_once(step):
+    """Capture `step(stream)` in a CUDA graph (after one eager run) and
+    replay it once, as bench.py's timed step does."""
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        c.he_conv2d_stack(arr, ws, stream=stream)
+        step(stream)
     stream.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
-        c.he_conv2d_stack(arr, ws, stream=stream)
+        step(stream)
+    return stream, graph
+
+
+def _check_sampled(oracle, c, wl, specs, filters, channels):
+    """Output channels channels(li, Cout) of every layer, for the last image,
+    against the oracle's Algorithm 1 plus the mask, bit for bit.  Only those
+    rows leave the device."""
+    b = wl.B - 1
+    for li, (sp, (shape, w)) in enumerate(zip(specs, filters)):
+        g = sp["g"]
+        geo = oracle.geometry(wl.N, *shape)
+        ct_b = sp["ct_in"][b].cpu().numpy().view(np.uint32)
+        for i in channels(li, g):
+            sl = slice(i * g.bands, (i + 1) * g.bands)
+            r_b = sp["r"][b, sl].cpu().numpy().view(np.uint32)
+            got = sp["out"][b, sl].cpu().numpy().view(np.uint32)
+            want = oracle.mask(oracle.conv_alg1(ct_b, w, geo, c.primes, i, i + 1), r_b, c.primes)
+            assert (got == want).all(), (wl.name, li, i)
+
+
+def _two_channels(li, g):
+    return sorted({li % g.Cout, g.Cout - 1})
+
+
+@pytest.mark.parametrize("config,kernel", [("resnet18", "queue"), ("resnet18-b64", "per_layer"),
+                                           ("resnet50-b8", "per_layer")])
+def test_full_stack_in_the_bench_configuration(fg, oracle, config, kernel):
+    wl = WORKLOADS[config]
+    c = fg.Context(wl.N, wl.L)
+    c.stack_kernel = {"queue": fg.FL_STACK_QUEUE, "per_layer": fg.FL_STACK_PER_LAYER}[kernel]
+    specs, filters = _bench_layers(c, wl, 5)
+    arr = c.stack_layers(specs)
+    ws = c.stack_workspace(arr)
+    stream, graph = _replay_once(lambda st: c.he_conv2d_stack(arr, ws, stream=st))
     for sp in specs:
         sp["out"].fill_(-1)
     torch.cuda.synchronize()
@@ -55,17 +95,37 @@ def test_full_stack_in_the_bench_configuration(fg, oracle, config, kernel):
         graph.replay()
     stream.synchronize()
     assert c.stack_error(ws) == 0
-    b = B - 1
-    for li, (sp, (shape, w)) in enumerate(zip(specs, filters)):
-        g = sp["g"]
-        geo = oracle.geometry(N, *shape)
-        ct_b = sp["ct_in"][b].cpu().numpy().view(np.uint32)
-        r_b = sp["r"][b].cpu().numpy().view(np.uint32)
-        got = sp["out"][b].cpu().numpy().view(np.uint32)
-        for i in sorted({li % g.Cout, g.Cout - 1}):
-            sl = slice(i * g.bands, (i + 1) * g.bands)
-            want = oracle.mask(oracle.conv_alg1(ct_b, w, geo, c.primes, i, i + 1), r_b[sl], c.primes)
-            assert (got[sl] == want).all(), (config, li, i)
+    _check_sampled(oracle, c, wl, specs, filters, _two_channels)
+    del arr, ws, graph, specs
+
+
+@pytest.mark.parametrize("config", ["resnet18-b64", "resnet50-b8"])
+def test_tc_form_full_stack_in_the_bench_configuration(fg, oracle, config):
+    """The tensor-core form over a whole batched stack, as bench.py --form tc
+    runs it (per layer: input NTT, tensor-core contraction, inverse NTT +
+    mask; one CUDA graph per step), against the oracle on two output channels
+    of every layer.  ResNet-50's layers reach G = 52 input ciphertexts."""
+    wl = WORKLOADS[config]
+    c = fg.Context(wl.N, wl.L)
+    specs, filters = _bench_layers(c, wl, 7)
+    assert max(sp["g"].G for sp in specs) == (52 if config == "resnet50-b8" else 10)
+    for sp in specs:
+        sp["ws"] = c.workspace(sp["g"], wl.B)
+
+    def step(st):
+        for sp in specs:
+            c.he_conv2d_tc(sp["g"], sp["w_hat"], sp["ct_in"], out=sp["out"], workspace=sp["ws"], r=sp["r"],
+                           stream=st)
+
+    stream, graph = _replay_once(step)
+    for sp in specs:
+        sp["out"].fill_(-1)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        graph.replay()
+    stream.synchronize()
+    _check_sampled(oracle, c, wl, specs, filters, _two_channels)
+    del graph, specs
 
 
 def test_x2x_rounds_at_the_bench_size(fg, oracle):
