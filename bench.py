@@ -30,6 +30,7 @@ from paper_2401_16732_gb300.workloads import WORKLOADS  # noqa: E402
 
 T_PLAIN = 65537
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_TENSOR_FLOPS = 1.9e15
 L2_BYTES = 129e6
 # Integer-ALU roofline of the inverse NTT: a lazy Gentleman-Sande butterfly
 # with Shoup multiplication needs 4 ALU-pipe operations (sum, conditional
@@ -39,9 +40,6 @@ ALU_BFLY_PEAK = 152 * 4 * 16 * 2.07e9 / 4
 # Direct form: one signed 32x32->64-bit multiply-add per lane per clock on the
 # 16-lane integer multiply pipe (an upper bound).
 DIRECT_MAC_PEAK = 152 * 4 * 16 * 2.07e9
-# mma.sync m16n8k32 u8 x u8 -> s32 multiply-adds/s measured on this GPU by an
-# instruction-rate microbenchmark
-TC_U8_PEAK = 7.9e13
 # DRAM bytes (read + write) of one step's launches of the dominant kernel,
 # from one ncu capture of the same command, each with the SHA-256 (first 16
 # hex digits) of the kernel sources it was captured from.  The figure is
@@ -51,6 +49,8 @@ KERNEL_SOURCES = {  # the kernel's own file and the shared device header
     "queue": ("fl_kernels.cu", "fl_device.cuh"),
     "round1": ("fl_act.cu", "fl_device.cuh"),
     "round2": ("fl_act.cu", "fl_device.cuh"),
+    "tc": ("fl_tc.cu",),
+    "intt_rows": ("fl_tc.cu", "fl_device.cuh"),
 }
 TRAFFIC = {  # (config, kernel): (bytes per step, source hash at capture)
     ("resnet18", "queue"): (3.354e9, "62ede15b38b67d2f"),
@@ -91,6 +91,16 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def tensor_peak():
+    """Dense fp16 tensor FLOP/s: the measured bf16 burst figure (fp16 and
+    bf16 run at the same dense rate on the tensor cores), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1e12, "measured (bf16 burst; fp16 dense runs at the same rate)"
+    except Exception:
+        return FALLBACK_TENSOR_FLOPS, "fallback"
 
 
 def layer_bytes(g, B, L, N, masked=True):
@@ -449,7 +459,10 @@ def run_gpu(args, wl, rank, world, local_rank):
         a = synth.device_uniform_residues(seed, ctx.primes, (B, g.n_in, L, N), li, device=dev)
         e = synth.device_cbd_noise(seed, (B, g.n_in, N), li, device=dev)
         w_dev = to_dev(w, torch.int8)
-        lay = {"g": g, "w": w_dev, "w_hat": ctx.encode_weights(g, w_dev) if args.form in ("ntt", "tc") else None,
+        w_hat = ctx.encode_weights(g, w_dev) if args.form in ("ntt", "tc") else None
+        if args.form == "tc":  # the tensor-core form reads the weights in slot groups of 8
+            w_hat = ctx.tc_weights(g, w_hat)
+        lay = {"g": g, "w": w_dev, "w_hat": w_hat,
                "ct": ctx.encrypt(sk, g, to_dev(x), a, e),
                "r": synth.device_masks(seed, (B, g.n_out, N), T_PLAIN, li, device=dev),
                "out": torch.empty((B, g.n_out, 2, L, N), dtype=torch.int32, device=dev)}
@@ -465,7 +478,7 @@ def run_gpu(args, wl, rank, world, local_rank):
         tuned = {"kernel": args.form, "ms": None}
         if args.form in ("otf", "tc"):
             for lay in layers:
-                lay["ws"] = ctx.workspace(lay["g"], B)
+                lay["ws"] = (ctx.tc_workspace if args.form == "tc" else ctx.workspace)(lay["g"], B)
     elif args.stack_kernel == "auto":
         from paper_2401_16732_gb300.autotune import tune_stack
         tuned = tune_stack(ctx, [{"g": lay["g"], "ct_in": lay["ct"], "r": lay["r"]} for lay in layers], arr, ws,
@@ -481,7 +494,7 @@ def run_gpu(args, wl, rank, world, local_rank):
         # / `arr_` select another set of output buffers
         outs = outs or [lay["out"] for lay in layers]
         arr_ = arr if arr_ is None else arr_
-        if events is not None:
+        if events is not None and args.form != "tc":
             events[0].record(stream)
         if args.form == "direct":
             # the paper's DRot + CMult form on the GPU: one launch per layer, no NTT
@@ -493,16 +506,23 @@ def run_gpu(args, wl, rank, world, local_rank):
                 events[2].record(stream)
             return
         if args.form == "tc":
-            # per layer: input NTT, byte-split tensor-core contraction into the
-            # output buffer (NTT domain), in-place inverse NTT + mask of every
-            # output row (the stages are not separated here: events[1] == events[0])
-            if events is not None:
-                events[1].record(stream)
-            for lay, o in zip(layers, outs):
-                ctx.he_conv2d_tc(lay["g"], lay["w_hat"], lay["ct"], out=o, workspace=lay["ws"], r=lay["r"],
-                                 stream=stream)
-            if events is not None:
-                events[2].record(stream)
+            # per layer: input NTT, tensor-core contraction into the output
+            # buffer (NTT domain), in-place inverse NTT + mask of every output
+            # row; with `events`, each stage of each layer is bracketed
+            # (events[k] = 4 events per layer) and the stages are separate calls
+            for k, (lay, o) in enumerate(zip(layers, outs)):
+                if events is None:
+                    ctx.he_conv2d_tc(lay["g"], lay["w_hat"], lay["ct"], out=o, workspace=lay["ws"], r=lay["r"],
+                                     stream=stream)
+                    continue
+                ev = events[k]
+                ev[0].record(stream)
+                ctx.he_conv2d_ntt_inputs(lay["g"], lay["ct"], lay["ws"], stream=stream)
+                ev[1].record(stream)
+                ctx.he_conv2d_tc_from_ntt(lay["g"], B, lay["w_hat"], lay["ws"], o, stream=stream)
+                ev[2].record(stream)
+                ctx.intt_mask_outputs(lay["g"], o, r=lay["r"], stream=stream)
+                ev[3].record(stream)
             return
         if args.form == "otf":
             # input NTT + on-the-fly-weight kernel per layer (the two stages are
@@ -566,16 +586,28 @@ def run_gpu(args, wl, rank, world, local_rank):
 
     # ---- per-kernel durations (eager launches queued behind a GPU sleep so
     # that event timestamps bracket the kernels, not host launch latency) ----
-    kern = {"ntt": 0.0, "conv": 0.0}
+    kern = {"ntt": 0.0, "conv": 0.0, "tc": 0.0, "intt": 0.0}
     nrep = max(1, min(args.steps, 5))
     for _ in range(nrep):
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         with torch.cuda.stream(stream):
             torch.cuda._sleep(2_000_000)
+        if args.form == "tc":
+            evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in layers]
+            step(evs)
+            stream.synchronize()
+            for ev in evs:
+                kern["ntt"] += ev[0].elapsed_time(ev[1]) / nrep
+                kern["tc"] += ev[1].elapsed_time(ev[2]) / nrep
+                kern["intt"] += ev[2].elapsed_time(ev[3]) / nrep
+            kern["conv"] = kern["tc"] + kern["intt"]
+            continue
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         step(evs)
         stream.synchronize()
         kern["ntt"] += evs[0].elapsed_time(evs[1]) / nrep
         kern["conv"] += evs[1].elapsed_time(evs[2]) / nrep
+    if args.form == "tc" and ctx.tc_error(stream):
+        raise RuntimeError("a bounded wait of the tensor-core contraction ran out")
     err_word = ctx.stack_error(ws, stream=stream) if ws is not None else 0
     if err_word:
         raise RuntimeError(f"persistent kernel reported a timed-out wait (error word {err_word})")
@@ -731,18 +763,35 @@ def run_gpu(args, wl, rank, world, local_rank):
                 "encoded_weight_bytes_avoided": sum(L * g.Cout * g.G * N * 4 for g in geoms)}
         kname = roof["kernel"]
     if tuned["kernel"] == "tc":
-        # the per-slot products as exact u8 digit products on the warp-level
-        # integer MMA (16 per modular multiply-add), against the rate the
-        # tensor-core probe measured for that instruction on this GPU; the
-        # output inverse NTTs run in a second kernel
-        digit_macs = 16 * macs
-        rate = digit_macs / kern_s
-        roof = {"bound": "tensor", "achieved": rate / 1e12, "peak": TC_U8_PEAK / 1e12, "unit": "T u8-MAC/s",
-                "frac": rate / TC_U8_PEAK, "traffic": None,
-                "peak_source": "measured: mma.sync m16n8k32 u8 throughput probe (python -m paper_2401_16732_gb300.tcprobe)",
-                "kernel": "per layer: k_conv_tc (byte-split mma.sync contraction) + k_intt_mask_rows",
-                "kernel_ms_per_step": kern["conv"], "algorithmic_digit_macs_per_step": digit_macs,
-                "other_roofline": dict(alu_line, achieved=achieved_bfly / 1e12, frac=achieved_bfly / ALU_BFLY_PEAK)}
+        # two kernels per layer after the input NTT: the tensor-core
+        # contraction (NTT-domain outputs to HBM) and the in-place inverse NTT +
+        # mask of every output row; each is timed with its own events
+        tpk, tpk_src = tensor_peak()
+        digit_flops = 2 * 16 * macs  # 16 fp16 digit products per modular multiply-add
+        tc_bytes = sum(L * g.Cout * g.G * N * 4 + B * g.n_in * 2 * L * N * 4 + B * g.n_out * 2 * L * N * 4
+                       for g in geoms)  # weights + NTT inputs read, NTT-domain outputs written
+        intt_bytes = sum(2 * B * g.n_out * 2 * L * N * 4 + B * g.n_out * N * 4 for g in geoms)
+        tc_s, intt_s = kern["tc"] * 1e-3, kern["intt"] * 1e-3
+        tc_hbm = {"bound": "hbm", "achieved": tc_bytes / tc_s / 1e9, "peak": hbm, "unit": "GB/s",
+                  "frac": tc_bytes / tc_s / 1e9 / hbm, "peak_source": peak_kind}
+        tc_tensor = {"bound": "tensor", "achieved": digit_flops / tc_s / 1e12, "peak": tpk / 1e12, "unit": "TFLOP/s",
+                     "frac": digit_flops / tc_s / tpk, "peak_source": tpk_src}
+        tc_main, tc_other = (tc_hbm, tc_tensor) if tc_bytes / (hbm * 1e9) >= digit_flops / tpk else (tc_tensor, tc_hbm)
+        tc_line = dict(tc_main, kernel="k_conv_tc (tcgen05 kind::f16 digit products, tensor-memory accumulators)",
+                       kernel_ms_per_step=kern["tc"], algorithmic_bytes_per_step=tc_bytes,
+                       algorithmic_digit_flops_per_step=digit_flops, other_roofline=tc_other,
+                       traffic=traffic_of(args.config, "tc"), kernel_source_sha256_16=kernel_source_hash("tc"))
+        intt_hbm = {"bound": "hbm", "achieved": intt_bytes / intt_s / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": intt_bytes / intt_s / 1e9 / hbm, "peak_source": peak_kind}
+        intt_alu = dict(alu_line, achieved=bfly / intt_s / 1e12, frac=bfly / intt_s / ALU_BFLY_PEAK)
+        i_main, i_other = (intt_hbm, intt_alu) if intt_bytes / (hbm * 1e9) >= bfly / ALU_BFLY_PEAK else (intt_alu, intt_hbm)
+        intt_line = dict(i_main, kernel="k_intt_mask_rows (in-place inverse NTT + mask of every output row)",
+                         kernel_ms_per_step=kern["intt"], algorithmic_bytes_per_step=intt_bytes,
+                         algorithmic_butterflies_per_step=bfly, other_roofline=i_other,
+                         traffic=traffic_of(args.config, "intt_rows"),
+                         kernel_source_sha256_16=kernel_source_hash("intt_rows"))
+        roof, other_k = (tc_line, intt_line) if kern["tc"] >= kern["intt"] else (intt_line, tc_line)
+        roof = dict(roof, other_kernels=[other_k], ntt_inputs_ms_per_step=kern["ntt"])
         kname = roof["kernel"]
     line = {
         "metric": "encrypted conv layers/s", "value": value, "unit": "layers/s", "n_gpus": world,

@@ -212,25 +212,65 @@ int fl_he_conv2d_otf(fl_ctx *ctx, const fl_conv_geom *geom, int B, const int8_t 
 int fl_he_conv2d_direct(fl_ctx *ctx, const fl_conv_geom *geom, int B, const int8_t *w_dev,
                         const uint32_t *ct_in_dev, const uint32_t *r_dev, uint32_t *ct_out_dev, void *stream);
 
-/* Byte-split tensor-core form of the same convolution (the per-slot
- * contraction of Algorithm 1's sum over input ciphertexts on the integer
- * tensor cores).  It takes the same encoded weights, inputs, masks and
- * workspace as fl_he_conv2d_mask, and gives a bit-identical result.  Every
- * 30-bit residue is split into its four bytes; the per-slot products
- * sum_g W[i][g] * X[g][col] become exact u8 x u8 -> s32 matrix products of
- * the warp-level MMA, with the weight byte folded into the reduction
- * dimension and the seven byte shifts into the column dimension, then
- * recombined and reduced mod q_l on the CUDA cores.  Unlike the plain form it
- * is not fused with the inverse NTT: a tensor-core tile spans 16 output
- * channels of 8 slots, while the inverse NTT needs every slot of one output
- * channel.  So the NTT-domain outputs go through ct_out_dev, and a second
- * kernel transforms every output row in place and adds the mask.  Returns
- * FL_ERR_SHAPE when the weights of 16 output channels for all G input
- * ciphertexts of 8 slots do not fit one CTA's shared memory (G above about
- * 190). */
-int fl_he_conv2d_tc(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_hat_dev,
+/* Tensor-core form of the same convolution: the per-slot contraction of
+ * Algorithm 1's sum over input ciphertexts (evaluated in the NTT domain) on
+ * the 5th-generation tensor cores (tcgen05.mma kind::f16, accumulators in
+ * tensor memory).  It takes the same inputs and masks as fl_he_conv2d_mask,
+ * the encoded weights in the layout of fl_tc_weights and a workspace of
+ * fl_he_conv2d_tc_workspace_bytes, and gives a bit-identical result.
+ * - Exactness: every residue is split into four balanced base-256 digits in
+ *   [-128, 127], exact in fp16.  The inputs are first multiplied by 256^a mod
+ *   q_l (a = 0..3), so the product sum_g W X becomes four digit products
+ *   P_e (e = 0..3) per output, each an integer of magnitude at most
+ *   G * 2^16 accumulated in fp32; for G <= FL_TC_MAX_G every partial sum is
+ *   an exact integer.  The CUDA cores rebuild sum_e 256^e P_e mod q_l.
+ * - Tiling: a CTA holds 128 output channels x 16 (image/band, component)
+ *   columns x 8 slots of one limb in tensor memory; the K dimension runs
+ *   over (input ciphertext, weight digit) in steps of 16.
+ * - Weights: w_tc_dev holds the encoded weights of fl_encode_weights
+ *   re-laid by fl_tc_weights into slot groups of 8, so that each CTA reads
+ *   its weights as contiguous runs (fl_weights_bytes bytes, the same words).
+ * - Unlike the plain form it is not fused with the inverse NTT: a tile spans
+ *   128 output channels of 8 slots, while the inverse NTT needs every slot of
+ *   one output.  So the NTT-domain outputs go through ct_out_dev, and a
+ *   second kernel transforms every output row in place and adds the mask.
+ * - Every internal wait is bounded (2 s); a wait that runs out sets the
+ *   context's tensor-core error word (fl_tc_error).
+ * G > FL_TC_MAX_G: FL_ERR_SHAPE. */
+#define FL_TC_MAX_G 64
+/* Workspace of fl_he_conv2d_tc: the NTT images of the inputs (as for
+ * fl_he_conv2d), then their copy in slot groups of 4 ([L][N/4][B][n_in][2][4])
+ * that the contraction reads: 2 * B*n_in*2*L*N*4 bytes. */
+size_t fl_he_conv2d_tc_workspace_bytes(const fl_ctx *ctx, const fl_conv_geom *geom, int B);
+/* The encoded weights w_hat_dev [L][Cout][G][N] (fl_encode_weights) re-laid
+ * for fl_he_conv2d_tc: w_tc_dev [L][N/8][G][2][Cout][4], word
+ * [l][u/8][g][(u%8)/4][i][u%4] = w_hat[l][i][g][u].  fl_weights_bytes bytes;
+ * the buffers must not overlap.  Offline, like the encoding itself. */
+int fl_tc_weights(fl_ctx *ctx, const fl_conv_geom *geom, const uint32_t *w_hat_dev, uint32_t *w_tc_dev,
+                  void *stream);
+int fl_he_conv2d_tc(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_tc_dev,
                     const uint32_t *ct_in_dev, const uint32_t *r_dev, uint32_t *ct_out_dev,
                     void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/* The stages of fl_he_conv2d_tc after the input NTT, as separate calls
+ * (same results).  fl_he_conv2d_tc_from_ntt: the tensor-core contraction
+ * from a workspace (fl_he_conv2d_tc_workspace_bytes) whose first half
+ * fl_he_conv2d_ntt_inputs filled; it writes the slot-tiled copy of the
+ * inputs into the second half, and ct_out_dev receives
+ * the NTT-domain outputs (values in [0, 2 q_l)).  fl_intt_mask_outputs: the
+ * in-place inverse NTT of B * n_out such NTT-domain output ciphertexts
+ * (whose weights carried N^-1) plus Delta * r on c0 when r_dev is not NULL;
+ * the result is fl_he_conv2d_mask's. */
+int fl_he_conv2d_tc_from_ntt(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_tc_dev,
+                             void *workspace_dev, size_t workspace_bytes, uint32_t *ct_out_dev, void *stream);
+int fl_intt_mask_outputs(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *r_dev, uint32_t *ct_out_dev,
+                         void *stream);
+
+/* Synchronise `stream`, read the tensor-core form's error word into
+ * *error_host and clear it.  FL_OK when it is 0; FL_ERR_TIMEOUT when a
+ * bounded wait inside fl_he_conv2d_tc ran out (bit 0): that call's outputs
+ * are incomplete, and the context stays usable. */
+int fl_tc_error(fl_ctx *ctx, void *stream, uint64_t *error_host);
 
 /* ---- Many layers in one launch ---- */
 

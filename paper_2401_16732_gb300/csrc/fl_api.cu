@@ -33,12 +33,17 @@ struct fl_ctx {
   CtxConst cc;
   DecConst dc;
   uint32_t* tw;  // device twiddle tables, twiddle_limb_words(logN) words per limb
+  // error word of the tensor-core contraction's bounded waits (in the same
+  // allocation as the tables, after them)
+  unsigned long long* tc_err;
   // batch encoding over Z_t[x]/(x^N+1), present when t is prime and t = 1 mod 2N:
   // the tables of t follow the L limbs' tables in `tw`
   int batch;
   uint32_t psi_t;
   fl::LimbConst tc;
 };
+
+static_assert(FL_TC_MAX_G == fl::kTcMaxG, "header and kernel agree on the G bound");
 
 namespace {
 
@@ -332,11 +337,14 @@ int fl_ctx_create(int N, int L, uint32_t t, fl_ctx** out) {
     delete c;
     return fail(FL_ERR_OOM, "auxiliary streams / events");
   }
-  if ((e = cudaMalloc(&c->tw, host.size() * sizeof(uint32_t))) != cudaSuccess) {
+  const size_t tw_words = (host.size() + 3) / 4 * 4;  // the error word follows, 16-byte aligned
+  if ((e = cudaMalloc(&c->tw, (tw_words + 4) * sizeof(uint32_t))) != cudaSuccess) {
     delete c;
     return fail(FL_ERR_OOM, "twiddle tables: %s", cudaGetErrorString(e));
   }
-  if ((e = cudaMemcpy(c->tw, host.data(), host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
+  c->tc_err = reinterpret_cast<unsigned long long*>(c->tw + tw_words);
+  if ((e = cudaMemcpy(c->tw, host.data(), host.size() * sizeof(uint32_t), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(c->tc_err, 0, 16)) != cudaSuccess) {
     cudaFree(c->tw);
     delete c;
     return cuda_fail(e, "twiddle upload");
@@ -606,26 +614,100 @@ int fl_he_conv2d_otf(fl_ctx* ctx, const fl_conv_geom* geom, int B, const int8_t*
                   "on-the-fly conv");
 }
 
-int fl_he_conv2d_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_hat_dev, const uint32_t* ct_in_dev,
+size_t fl_he_conv2d_tc_workspace_bytes(const fl_ctx* ctx, const fl_conv_geom* geom, int B) {
+  return 2 * fl_he_conv2d_workspace_bytes(ctx, geom, B);
+}
+
+// Checks shared by the tensor-core entry points; the workspace holds the NTT
+// images of the inputs, then their slot-tiled copy.
+static int tc_checks(fl_ctx* ctx, const fl_conv_geom* geom, int B, size_t workspace_bytes) {
+  int rc;
+  if ((rc = conv_checks(ctx, geom, B, workspace_bytes))) return rc;
+  const size_t need = fl_he_conv2d_tc_workspace_bytes(ctx, geom, B);
+  if (workspace_bytes < need) return fail(FL_ERR_ARG, "workspace %zu bytes, need %zu", workspace_bytes, need);
+  if (geom->G > FL_TC_MAX_G)
+    return fail(FL_ERR_SHAPE, "G=%d input ciphertexts per band: above %d, the fp32 partial sums of the digit "
+                "products would no longer be exact", geom->G, FL_TC_MAX_G);
+  return FL_OK;
+}
+
+// slot-tiled copy of the NTT images (second half of the workspace), then the
+// tensor-core contraction; `pdl`: the contraction follows the copy as a
+// programmatic dependent launch
+static int stage_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_tc_dev, const void* ws,
+                    uint32_t* ct_out_dev, cudaStream_t st) {
+  const uint32_t* c_hat = (const uint32_t*)ws;
+  uint32_t* c_tc = (uint32_t*)ws + fl_he_conv2d_workspace_bytes(ctx, geom, B) / 4;
+  int rc;
+  if ((rc = launched(fl::launch_tc_inputs(c_hat, c_tc, B, geom->n_in, ctx->L, ctx->N, st), "tensor-core input layout")))
+    return rc;
+  return launched(fl::launch_conv_tc(B, fl::ConvDims{geom->Cout, geom->G, geom->n_in, geom->n_out, geom->bands},
+                                     w_tc_dev, c_tc, ct_out_dev, ctx->N, ctx->cc, ctx->tc_err, st, true),
+                  "tensor-core contraction");
+}
+
+int fl_he_conv2d_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_tc_dev, const uint32_t* ct_in_dev,
                     const uint32_t* r_dev, uint32_t* ct_out_dev, void* workspace_dev, size_t workspace_bytes,
                     void* stream) {
   int rc;
-  if ((rc = conv_checks(ctx, geom, B, workspace_bytes))) return rc;
+  if ((rc = tc_checks(ctx, geom, B, workspace_bytes))) return rc;
   if (B == 0) return FL_OK;
-  if ((rc = check_ptrs({w_hat_dev, ct_in_dev, ct_out_dev, workspace_dev}))) return rc;
+  if ((rc = check_ptrs({w_tc_dev, ct_in_dev, ct_out_dev, workspace_dev}))) return rc;
   if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
-  if (fl::conv_tc_smem_bytes(geom->G) > 226 * 1024)
-    return fail(FL_ERR_SHAPE, "G=%d input ciphertexts exceed the tensor-core form's shared memory", geom->G);
-  if ((geom->Cout + 15) / 16 > 65535) return fail(FL_ERR_SHAPE, "Cout=%d", geom->Cout);
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = stage_ntt(ctx, geom, B, ct_in_dev, workspace_dev, st))) return rc;
-  if ((rc = launched(fl::launch_conv_tc(B, fl::ConvDims{geom->Cout, geom->G, geom->n_in, geom->n_out, geom->bands},
-                                        w_hat_dev, (const uint32_t*)workspace_dev, ct_out_dev, ctx->N, ctx->cc, st),
-                     "tensor-core contraction")))
-    return rc;
+  if ((rc = stage_tc(ctx, geom, B, w_tc_dev, workspace_dev, ct_out_dev, st))) return rc;
   return launched(fl::launch_intt_mask_rows(ctx->logN, (long long)B * geom->n_out * 2 * ctx->L, ct_out_dev, r_dev,
-                                            ctx->tw, ctx->cc, st),
+                                            ctx->tw, ctx->cc, st, true),
                   "output inverse ntt");
+}
+
+int fl_he_conv2d_tc_from_ntt(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_tc_dev,
+                             void* workspace_dev, size_t workspace_bytes, uint32_t* ct_out_dev, void* stream) {
+  int rc;
+  if ((rc = tc_checks(ctx, geom, B, workspace_bytes))) return rc;
+  if (B == 0) return FL_OK;
+  if ((rc = check_ptrs({w_tc_dev, workspace_dev, ct_out_dev}))) return rc;
+  return stage_tc(ctx, geom, B, w_tc_dev, workspace_dev, ct_out_dev, (cudaStream_t)stream);
+}
+
+int fl_intt_mask_outputs(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* r_dev, uint32_t* ct_out_dev,
+                         void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_geom(ctx, geom))) return rc;
+  if (B < 0) return fail(FL_ERR_ARG, "B=%d", B);
+  if (B == 0) return FL_OK;
+  if ((rc = check_ptrs({ct_out_dev}))) return rc;
+  if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
+  if ((long long)B * geom->n_out * 2 * ctx->L > 0x7fffffffLL)
+    return fail(FL_ERR_ARG, "B=%d: too many output rows for one launch", B);
+  return launched(fl::launch_intt_mask_rows(ctx->logN, (long long)B * geom->n_out * 2 * ctx->L, ct_out_dev, r_dev,
+                                            ctx->tw, ctx->cc, (cudaStream_t)stream, false),
+                  "output inverse ntt");
+}
+
+int fl_tc_weights(fl_ctx* ctx, const fl_conv_geom* geom, const uint32_t* w_hat_dev, uint32_t* w_tc_dev, void* stream) {
+  int rc;
+  if ((rc = check_ctx(ctx)) || (rc = check_geom(ctx, geom))) return rc;
+  if ((rc = check_ptrs({w_hat_dev, w_tc_dev}))) return rc;
+  const size_t bytes = fl_weights_bytes(ctx, geom);
+  const uintptr_t a = (uintptr_t)w_hat_dev, b = (uintptr_t)w_tc_dev;
+  if (a < b + bytes && b < a + bytes) return fail(FL_ERR_ARG, "w_hat and w_tc overlap");
+  return launched(fl::launch_tc_weights(w_hat_dev, w_tc_dev, ctx->L, geom->Cout, geom->G, ctx->N, (cudaStream_t)stream),
+                  "tensor-core weight layout");
+}
+
+int fl_tc_error(fl_ctx* ctx, void* stream, uint64_t* error_host) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (!error_host) return fail(FL_ERR_ARG, "null error_host");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  unsigned long long v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, ctx->tc_err, sizeof v, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v) e = cudaMemset(ctx->tc_err, 0, sizeof v);
+  if (e != cudaSuccess) return cuda_fail(e, "error word");
+  *error_host = v;
+  return v ? fail(FL_ERR_TIMEOUT, "a bounded tensor-core wait gave up (error word 0x%llx)", v) : FL_OK;
 }
 
 int fl_he_conv2d_direct(fl_ctx* ctx, const fl_conv_geom* geom, int B, const int8_t* w_dev, const uint32_t* ct_in_dev,

@@ -131,15 +131,19 @@ cudaError_t launch_conv_otf(int logn, int B, const GeomDims& gd, const int8_t* w
                             uint32_t* out, const uint32_t* r, const uint32_t* tw, const CtxConst& cc,
                             cudaStream_t st);
 
-// direct form (fl_direct.cu)
-// byte-split tensor-core contraction (fl_tc.cu): NTT-domain outputs, then
-// the in-place inverse NTT of every output row with the mask
+// tensor-core contraction (fl_tc.cu): NTT-domain outputs in [0, 2q), then the
+// in-place inverse NTT of every output row with the mask.  kTcMaxG: the most
+// input ciphertexts per band whose digit products stay exact in fp32.
+constexpr int kTcMaxG = 64;
 cudaError_t launch_tc_setup(int logn);
-size_t conv_tc_smem_bytes(int G);  // shared memory of the contraction for G input ciphertexts
+size_t conv_tc_smem_bytes();
+cudaError_t launch_tc_weights(const uint32_t* w_hat, uint32_t* w_tc, int L, int Cout, int G, int N, cudaStream_t st);
+cudaError_t launch_tc_inputs(const uint32_t* c_hat, uint32_t* c_tc, int B, int n_in, int L, int N, cudaStream_t st);
 cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_hat, const uint32_t* c_hat, uint32_t* y_hat,
-                           int N, const CtxConst& cc, cudaStream_t st);
+                           int N, const CtxConst& cc, unsigned long long* err, cudaStream_t st, bool pdl);
 cudaError_t launch_intt_mask_rows(int logn, long long rows, uint32_t* y, const uint32_t* r, const uint32_t* tw,
-                                  const CtxConst& cc, cudaStream_t st);
+                                  const CtxConst& cc, cudaStream_t st, bool pdl);
+// direct form (fl_direct.cu)
 cudaError_t launch_direct_setup(int logn);
 cudaError_t launch_direct(int logn, int B, const GeomDims& g, const int8_t* w, const uint32_t* ct, uint32_t* out,
                           const uint32_t* r, const CtxConst& cc, cudaStream_t st);

@@ -1,30 +1,43 @@
-// Byte-split tensor-core form of the per-slot contraction (Algorithm 1's
-// sum over input ciphertexts, evaluated in the NTT domain), beside the plain
-// CUDA-core form of fl_kernels.cu.  sm_103a has no integer kind of tcgen05,
-// so the products run on the warp-level integer MMA
-// (mma.sync m16n8k32, u8 x u8 -> s32), which is exact by construction.
+// Tensor-core form of the per-slot contraction (Algorithm 1's sum over input
+// ciphertexts, evaluated in the NTT domain), beside the plain CUDA-core form
+// of fl_kernels.cu.  It runs on the 5th-generation tensor cores (tcgen05.mma
+// kind::f16, accumulators in tensor memory).  sm_103a has no integer kind of
+// tcgen05, so the integers are carried exactly in fp16 with fp32
+// accumulation.
 //
-// For limb l and slot u the contraction is a small integer matrix product
-//   Y[i][col] = sum_g W[i][g] * X[g][col]  (mod q_l),   col = (image, band, component).
-// Every residue (< 2^30) is split into its 4 bytes, W = sum_a W_a 2^(8a) and
-// X = sum_d X_d 2^(8d).  The weight byte index goes into K and the digit
-// shift s = a + d into N:
-//   A[i][(g, a)]       = W_a[i][g]
-//   B[(g, a)][(col, s)] = X_(s-a)[g][col]   (0 outside 0 <= s-a <= 3)
-//   Y_s[i][col]        = sum_(g, a) A * B = sum_g sum_(a+d=s) W_a X_d
-// and Y = sum_(s=0..6) 2^(8s) Y_s.  Every partial sum is at most
-// 4 * G * 255^2 < 2^31, so the s32 accumulation is exact.  With K = (g, a)
-// in the order of the residue's bytes, a thread's A fragment registers are
-// the weight residues themselves, and a B fragment register is a
-// byte-reversed, shifted window of an input residue.
+// For limb l and slot u the contraction is a small matrix product mod q_l:
+//   Y[i][col] = sum_g W[i][g] * X[g][col]   (mod q),  col = (image, band, component).
+// Balanced base-256 digits.  A residue v < 2^31 is v = sum_a d_a(v) 256^a with
+// d_a(v) = byte_a(v + 0x80808080) - 128 in [-128, 127]; every digit is exact in
+// fp16.  With X'_a = 256^a X mod q (a = 0..3):
+//   W X = sum_a d_a(W) 256^a X = sum_a d_a(W) X'_a  (mod q)
+//       = sum_e 256^e P_e,   P_e = sum_(g, a) d_a(W[g]) d_e(X'_a[g]).
+// So per slot one matrix product with K = (g, a) (4G) and N = (col, e) (4 per
+// column) gives four partial sums P_e per output.  |P_e| <= 4G * 128^2 =
+// G * 2^16 <= 2^22 for G <= 64, so every fp32 partial sum is an exact integer.
+// One more K column carries a bias 2048 * 6144 = 3 * 2^22 (both factors exact
+// in fp16), which puts every accumulator in [2^23, 2^24]: the fp32 bit pattern
+// minus 0x4B400000 is then P_e itself.
+// Recombination mod q on the CUDA cores: Y = sum_e 256^e P_e (|Y| < 2^46.1)
+// is known exactly mod 2^32 from the bit patterns; its quotient k =
+// round(Y / q) comes from an fp32 estimate of Y (error below 2^22.1, so k is
+// within 0.51 of Y / q), and Y - k q + q lies in [0, 2q), the input range of
+// the inverse NTT, computed exactly in 32-bit arithmetic.
 //
-//   k_conv_tc          one CTA per (8-32 slots, 16 output channels, limb):
-//                      weights staged once, then every group of 8 columns;
-//                      each warp takes its slots in turn over all K steps;
-//                      writes the NTT-domain outputs, reduced to [0, q)
-//   k_intt_mask_rows   in-place inverse NTT of every output row, + Delta*r
-//                      on component 0 (the encoded weights carry N^-1, so the
-//                      transform is the unscaled one)
+//   k_tc_weights   (offline) the encoded weights re-laid in slot groups of 8
+//   k_tc_inputs    the NTT images of the inputs re-laid in slot groups of 4
+//   k_conv_tc      one CTA per SM and (128 output channels, 16 columns, limb,
+//                  run of 16 groups of 4 slots), warp-specialised: 8 producer
+//                  warps (cp.async ring of raw residues -> fp16 digit tiles in
+//                  the canonical K-major layout, 4 stages), one MMA warp (4
+//                  MMAs M128 N64 K16 per K step, one per slot, into one of two
+//                  tensor-memory accumulator buffers), 8 epilogue warps
+//                  (tensor-memory loads, recombination, 32-byte stores of the
+//                  NTT-domain outputs in [0, 2q)); every hand-off an mbarrier
+//                  with a bounded wait
+//   k_intt_mask_rows   in-place inverse NTT of every output row, + Delta*r on
+//                  component 0 (the encoded weights carry N^-1, so the
+//                  transform is the unscaled one)
 #include <cuda_runtime.h>
 
 #include "fl_device.cuh"
@@ -33,184 +46,432 @@
 namespace fl {
 
 namespace {
-constexpr int TC_ROWS = 16;        // output channels per CTA (the MMA's M)
-constexpr int TC_COLS = 8;         // (image/band, component) columns per column group
-constexpr int TC_GK = 8;           // input ciphertexts per K step: 8 x 4 weight bytes = 32
-constexpr int TC_N = 7 * TC_COLS;  // (column, shift) pairs: 56, i.e. 7 n-tiles of 8
-constexpr int TC_WARPS = 8;
-constexpr int TC_THREADS = 32 * TC_WARPS;
-constexpr int TC_WROW = 24;        // row stride of a staged weight: 16 rows + 8 words of padding
-constexpr int TC_MAX_DYN_SMEM = 226 * 1024;  // dynamic shared memory limit, 1 KB below the CTA maximum
+constexpr int TC_M = 128;             // output channels per CTA (MMA M = tensor-memory lanes)
+constexpr int TC_CW = 16;             // columns per CTA; MMA N = 4 * 16 = 64 (column, digit e)
+constexpr int TC_NN = 4 * TC_CW;
+constexpr int TC_U = 4;               // slots per group: one accumulator buffer of 4 x 64 columns
+constexpr int TC_GS = 4;              // input ciphertexts per K step: 4 x 4 weight digits = K 16
+constexpr int TC_PROD_WARPS = 8;      // cp.async + digit conversion into the tile ring
+constexpr int TC_EPI_WARPS = 8;       // recombination, two per tensor-memory lane quadrant
+constexpr int TC_NPROD = 32 * TC_PROD_WARPS;
+constexpr int TC_MMA_WARP = TC_PROD_WARPS + TC_EPI_WARPS;  // one more warp issues the MMAs
+constexpr int TC_THREADS = 32 * (TC_MMA_WARP + 1);          // 416
+constexpr int TC_RING = 6;            // raw-residue ring depth, in K steps
+constexpr int TC_NS = 4;              // fp16 tile stages
+constexpr int TC_GPC = 16;            // slot groups per CTA: 64 slots, 256 bytes of every input row
+constexpr int TC_TMEM_COLS = 2 * TC_U * TC_NN;  // 512: two accumulator buffers
+static_assert(TC_GPC % 2 == 0, "the epilogue stores groups in pairs");
+// shared-memory layout (bytes)
+constexpr int RAWA_STEP = TC_GS * TC_M * 16;       // [g][row][4 slots]
+constexpr int RAWB_STEP = TC_CW * TC_GS * 16;      // [image/band][g][component][4 slots]
+constexpr int TILEA_SLOT = TC_M * 32;              // 128 rows x 16 halves
+constexpr int TILEB_SLOT = TC_NN * 32 + 16;        // 64 rows x 16 halves, +16 B against bank conflicts
+constexpr int STAGE_BYTES = TC_U * (TILEA_SLOT + TILEB_SLOT);
+constexpr int OFF_RAWA = 0;
+constexpr int OFF_RAWB = OFF_RAWA + TC_RING * RAWA_STEP;
+constexpr int OFF_TILE = (OFF_RAWB + TC_RING * RAWB_STEP + 1023) / 1024 * 1024;
+constexpr int OFF_HOLD = OFF_TILE + TC_NS * STAGE_BYTES;  // epilogue: even group's results [col][slot][thread]
+constexpr int TC_SMEM = OFF_HOLD + (TC_CW / 2) * TC_U * 32 * TC_EPI_WARPS * 4;
+// more than half of the SM's shared memory: one CTA per SM, which then owns
+// all of tensor memory
+static_assert(TC_SMEM > 116 * 1024 && TC_SMEM <= 220 * 1024, "one CTA per SM with room for the static part");
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // 2 s bound on every wait
+constexpr uint32_t FP_BIAS = 0x4B400000u;                 // bits of 3 * 2^22 in fp32
+constexpr uint16_t H_2048 = 0x6800, H_6144 = 0x6E00;      // fp16 2048, 6144
 
-// Bytes [x_s, x_(s-1), x_(s-2), x_(s-3)] of x (x_j its byte j; 0 outside 0..3):
-// rows (g, a = 0..3) of B's column (col, s).
-__device__ __forceinline__ uint32_t digit_window(uint32_t x, int s) {
-  const uint32_t r = __byte_perm(x, 0, 0x0123);  // x_3 x_2 x_1 x_0
-  return s <= 3 ? r >> (8 * (3 - s)) : r << (8 * (s - 3));
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor, no swizzle: start address,
+// leading byte offset (between core matrices along K), stride byte offset
+// (between 8-row groups along M or N), version bits 46-48 = 0b001.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
 }
-
-__device__ __forceinline__ void mma_u8(int (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+// instruction descriptor of kind::f16: D f32 (bits 4-5 = 1), A and B f16
+// (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
-      "mma.sync.aligned.m16n8k32.row.col.s32.u8.u8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-      : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// arrive on bar once every tcgen05 operation issued so far by this thread is done
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {  // one whole warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {  // the allocating warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes visible to the tensor core's (async-proxy) reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 8 consecutive tensor-memory columns of this thread's lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n}" ::"r"(su32(bar))
+               : "memory");
+}
+// Wait for the phase of the given parity; false after 2 s.  Each try_wait
+// suspends the warp in hardware for up to 20 us unless the phase completes
+// first, so waiting warps take no issue slots from the working ones.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  const unsigned long long t0 = gtimer();
+  for (unsigned polls = 0; polls < (1u << 20); ++polls) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(su32(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    if (done) return true;
+    if (gtimer() - t0 > TC_WAIT_NS) return false;
+  }
+  return false;
 }
 
-// Dynamic shared memory of k_conv_tc<SPW> for Gp = G rounded up to 8, in words:
-//   Wst [U][Gp][24]    weights of the CTA's 16 output channels (rows 16..23 padding)
-//   Xst [U][Gp][8]     inputs of one column group
-//   Ys  [8][16][57]    one slot's seven shift sums per warp
-//   Ot  [16][8][U + 4] reduced NTT-domain outputs of the column group
-// with U = 8 * SPW slots.  The weight layout puts the 32 lanes' A-fragment
-// words (g = 8k + t, row = grp or grp + 8) in 32 different banks.
-__host__ __device__ constexpr size_t tc_smem_words(int spw, int gp) {
-  return (size_t)8 * spw * gp * TC_WROW + (size_t)8 * spw * gp * TC_COLS + (size_t)TC_WARPS * TC_ROWS * (TC_N + 1) +
-         (size_t)TC_ROWS * TC_COLS * (8 * spw + 4);
+// 16-byte cp.async (src_bytes 0 fills the destination with zeros) with an
+// L2 eviction policy (createpolicy)
+__device__ __forceinline__ void cp16_pol(uint32_t dst, const void* src, uint32_t src_bytes, uint64_t pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(dst), "l"(src),
+               "r"(src_bytes), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// fp16 pair (byte_lo - 128, byte_hi - 128) from two biased bytes placed in
+// bytes 0 and 2 of t (bytes 1 and 3 are overwritten): 0x64xx is 1024 + xx
+__device__ __forceinline__ uint32_t digits2(uint32_t t) {
+  const uint32_t h = (t & 0x00FF00FFu) | 0x64006400u;
+  uint32_t r;
+  asm("sub.f16x2 %0, %1, %2;" : "=r"(r) : "r"(h), "r"(0x64806480u));  // - (1152, 1152)
+  return r;
+}
+// the four balanced digits of v (< 2^31) as fp16, in K order a = 0..3
+__device__ __forceinline__ uint2 digits4(uint32_t v) {
+  const uint32_t y = v + 0x80808080u;
+  // bytes (0, 1) into positions 0 and 2, then bytes (2, 3)
+  return make_uint2(digits2(__byte_perm(y, 0, 0x0100)), digits2(__byte_perm(y, 0, 0x0302)));
+}
+
+// Y - k q + q in [0, 2q) for Y = sum_e 256^e P_e, from the accumulator bit
+// patterns b[e] = bits(3 * 2^22 + P_e).  The fp32 estimate of Y sums the
+// biased accumulators (|error| < 2^23.1 at |sum| < 2^48) and subtracts the
+// biases' sum 3 * 2^22 * 0x01010101 (rounded: |error| <= 2^23; the
+// subtraction itself is exact), so k = round(Y / q) is within 0.52 of Y / q.
+// nq = -q mod 2^32; c = FP_BIAS * q + q - FP_BIAS * 0x01010101 mod 2^32 (the
+// biases of k and of the four P_e).
+__device__ __forceinline__ uint32_t recombine(const uint32_t* b, float qinv, uint32_t nq, uint32_t c) {
+  constexpr float kBiasSum = (float)(12582912.0 * 16843009.0);  // the exact integer, rounded once
+  const float y = fmaf(__uint_as_float(b[3]), 16777216.f,
+                       fmaf(__uint_as_float(b[2]), 65536.f, fmaf(__uint_as_float(b[1]), 256.f, __uint_as_float(b[0]))));
+  const uint32_t kb = __float_as_uint(fmaf(y - kBiasSum, qinv, 12582912.f));  // FP_BIAS + round(Y / q)
+  const uint32_t lo = b[0] + (b[1] << 8) + (b[2] << 16) + (b[3] << 24);     // Y + FP_BIAS * 0x01010101 mod 2^32
+  return kb * nq + lo + c;
 }
 }  // namespace
 
-// Grid (N / U, ceil(Cout / 16), L), U = 8 * SPW slots per CTA; every CTA
-// loops over the column groups of 8 (image/band, component) columns, with
-// its weights staged once.  Warp w takes slots w*SPW .. w*SPW + SPW - 1 in
-// turn, each over all K steps.
-template <int SPW>
-__global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const uint32_t* __restrict__ w_hat,
-                                                         const uint32_t* __restrict__ c_hat,
-                                                         uint32_t* __restrict__ y_hat, ConvDims cd, int B, int N,
-                                                         CtxConst cc) {
-  constexpr int U = 8 * SPW, U4 = U / 4, UP = U + 4;  // UP: padded row of Ot
-  extern __shared__ __align__(16) uint32_t tsm[];
-  const int Gp = (cd.G + TC_GK - 1) / TC_GK * TC_GK;
-  uint32_t* Wst = tsm;                                            // [U][Gp][24]
-  uint32_t* Xst = Wst + (size_t)U * Gp * TC_WROW;                 // [U][Gp][8]
-  int* Ys = reinterpret_cast<int*>(Xst + (size_t)U * Gp * TC_COLS);  // [8][16][57]
-  uint32_t* Ot = reinterpret_cast<uint32_t*>(Ys + TC_WARPS * TC_ROWS * (TC_N + 1));  // [16][8][UP]
-  const int L = cc.L;
-  const int u0 = blockIdx.x * U, i0 = blockIdx.y * TC_ROWS, l = blockIdx.z;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, grp = lane >> 2, t = lane & 3;
-  const size_t ct_words = (size_t)2 * L * N;
+// Grid (mtiles * nchunks, N / (4 * TC_GPC), L): blockIdx.x picks the 128
+// output channels and 16 columns (fastest, so CTAs sharing input slots run
+// together), blockIdx.y the run of TC_GPC groups of 4 slots, blockIdx.z the
+// limb.  Step t of the CTA is (group t / nch, K step t % nch) with nch =
+// G / 4 + 1 K steps per group, the last of which carries the bias column.
+// Warp roles (every hand-off an mbarrier with a bounded wait):
+//   producers (8 warps)  raw ring -> fp16 tile stage t % TC_NS, arrive tile_full
+//   MMA warp (1 thread)  tile_full -> 4 MMAs into accumulator buffer g % 2 ->
+//                        commit to tile_empty (and to acc_full after a group)
+//   epilogue (4 warps)   acc_full -> tensor-memory loads -> arrive acc_empty ->
+//                        recombination -> stores of the NTT-domain outputs
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_conv_tc(const uint32_t* __restrict__ w_tc, const uint32_t* __restrict__ c_hat, uint32_t* __restrict__ y_hat,
+              ConvDims cd, int B, int N, CtxConst cc, unsigned long long* err) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  __shared__ uint64_t tile_full[TC_NS], tile_empty[TC_NS], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort, p_abort[2];
+  __shared__ long long colout[TC_CW];  // output word offset of each column, output channel 0; -1 outside
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cols = 2 * B * cd.bands, mtiles = (cd.Cout + TC_M - 1) / TC_M;
+  const int i0 = (blockIdx.x % mtiles) * TC_M, col0 = (blockIdx.x / mtiles) * TC_CW;
+  const int l = blockIdx.z, grp0 = blockIdx.y * TC_GPC, L = cc.L, G = cd.G;
   const LimbConst lc = cc.limb[l];
-  const uint32_t c40 = red64((uint64_t)lc.r32 << 8, lc);  // 2^40 mod q
-  const int cols = 2 * B * cd.bands;
+  const size_t NL = (size_t)L * N, rowstride = (size_t)cd.bands * 2 * NL;
+  const int nch = G / TC_GS + 1, T = TC_GPC * nch;
+  const uint32_t sb = su32(tsm);
 
-  // weights: Wst[uu][g][ii] = W[l][i0 + ii][g][u0 + uu], zero outside the
-  // layer.  Each thread owns one (row, 4-slot group) and walks g; no index
-  // division by a runtime value.
-  {
-    constexpr int WP = TC_ROWS * U4, WS = TC_THREADS / WP;
-    const int ii = tid % TC_ROWS, q4 = (tid / TC_ROWS) % U4, gs = tid / WP;
-    const int i = i0 + ii;
-    const uint4* src = reinterpret_cast<const uint4*>(w_hat + ((size_t)l * cd.Cout + (i < cd.Cout ? i : 0)) * cd.G * N + u0) + q4;
-    uint32_t* d = Wst + (size_t)(4 * q4) * Gp * TC_WROW + ii;
-    for (int g = gs; g < Gp; g += WS) {
-      uint4 w = make_uint4(0, 0, 0, 0);
-      if (i < cd.Cout && g < cd.G) w = __ldg(src + (size_t)g * (N / 4));
-      d[g * TC_WROW] = w.x;
-      d[(Gp + g) * TC_WROW] = w.y;
-      d[(2 * Gp + g) * TC_WROW] = w.z;
-      d[(3 * Gp + g) * TC_WROW] = w.w;
+  if (warp == 0) tmem_alloc(&tmem_base, TC_TMEM_COLS);
+  if (tid == 0) {
+    for (int k = 0; k < TC_NS; ++k) {
+      mbar_init(&tile_full[k], TC_NPROD);
+      mbar_init(&tile_empty[k], 1);
     }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&acc_full[k], 1);
+      mbar_init(&acc_empty[k], 32 * TC_EPI_WARPS);
+    }
+    s_abort = p_abort[0] = p_abort[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __shared__ long long colbase[TC_COLS];  // output offset of each column of the group, row i0 excluded
-  const size_t rowstride = (size_t)cd.bands * 2 * L * N;  // between output channels i and i + 1
+  if (tid < TC_CW) {
+    const int colg = col0 + tid, bb = colg >> 1, b = bb / cd.bands, band = bb - b * cd.bands;
+    colout[tid] = colg < cols ? (long long)((((size_t)b * cd.n_out + band) * 2 + (colg & 1)) * NL + (size_t)l * N) : -1;
+  }
+  pdl_wait();  // the inputs come from the preceding forward NTT
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  pdl_trigger();
+  const uint32_t tbase = tmem_base;
 
-  for (int chunk = 0; chunk * TC_COLS < cols; ++chunk) {
-    const int ncols = min(TC_COLS, cols - chunk * TC_COLS);
-    const int ntiles = (7 * ncols + 7) / 8;
-    const unsigned rc = (65536u + ncols - 1) / ncols;  // (p * rc) >> 16 == p / ncols for p < 128
-    __syncthreads();  // the weights are staged; the previous group's Xst and Ot are no longer read
-    // inputs: Xst[uu][g][cl] = X[g][column chunk*8 + cl][u0 + uu], zero
-    // outside; each thread owns one (column, 4-slot group) and walks g
-    {
-      constexpr int XP = TC_COLS * U4, XS = TC_THREADS / XP;
-      const int cl = tid % TC_COLS, q4 = (tid / TC_COLS) % U4, gs = tid / XP;
-      const int col = chunk * TC_COLS + cl, bb = col >> 1, c = col & 1;
-      const int b = bb / cd.bands, band = bb - b * cd.bands;  // one division per thread and group
-      const bool ok = cl < ncols;
-      const uint4* src = reinterpret_cast<const uint4*>(
-          c_hat + (ok ? ((size_t)b * cd.n_in + (size_t)band * cd.G) * ct_words + (size_t)c * L * N : 0) +
-          (size_t)l * N + u0) + q4;
-      uint32_t* d = Xst + (size_t)(4 * q4) * Gp * TC_COLS + cl;
-      for (int g = gs; g < Gp; g += XS) {
-        uint4 x = make_uint4(0, 0, 0, 0);
-        if (ok && g < cd.G) x = __ldg(src + (size_t)g * (ct_words / 4));
-        d[g * TC_COLS] = x.x;
-        d[(Gp + g) * TC_COLS] = x.y;
-        d[(2 * Gp + g) * TC_COLS] = x.z;
-        d[(3 * Gp + g) * TC_COLS] = x.w;
-      }
-      if (tid < TC_COLS)
-        colbase[cl] = ok ? (long long)(((size_t)b * cd.n_out + band) * 2 * L * N + (size_t)c * L * N + (size_t)l * N +
-                                       u0 + (size_t)i0 * rowstride)
-                         : 0;
+  if (warp < TC_PROD_WARPS) {
+    // ------------------------------------------------------------ producers
+    const int pt = tid;  // 0..255
+    // Raw loads of each K step into ring slot t % TC_RING, 16-byte cp.async:
+    // A (slot-tiled weights w_tc[l][u / 8][g][(u % 8) / 4][i][4]): row pt & 127
+    // of the planes g = 2 (pt >> 7), + 1, so a warp reads 512 contiguous bytes;
+    // B (pt < 64; slot-tiled inputs c_tc[l][u / 4][b][ct][c][4]): image/band
+    // pt >> 3, ciphertext (pt >> 1) & 3, component pt & 1, so 8 threads read
+    // one 128-byte run.  Outside the layer the copies fill zeros.
+    const int a_row = pt & (TC_M - 1), a_gp = pt >> 7;
+    const bool a_ok = i0 + a_row < cd.Cout;
+    const size_t a_plane = (size_t)cd.Cout * 4;  // words of one (8-slot group, g, half) plane
+    const uint32_t* a_src = w_tc + (size_t)l * (N / 8) * G * 2 * a_plane + (size_t)(i0 + a_row) * 4;
+    const uint32_t a_dst = sb + OFF_RAWA + a_row * 16;
+    const int b_pair = pt >> 3, b_g = (pt >> 1) & 3, b_c = pt & 1;
+    bool b_ok = false;
+    const uint32_t* b_src = c_hat;
+    if (pt < TC_CW * TC_GS) {
+      const int colg = col0 + 2 * b_pair + b_c, bb = colg >> 1, b = bb / cd.bands, band = bb - b * cd.bands;
+      b_ok = colg < cols;
+      if (b_ok) b_src = c_hat + (((size_t)l * (N / 4) * B + b) * cd.n_in + (size_t)band * G) * 8 + b_c * 4;
     }
-    __syncthreads();
-    int* ys = Ys + warp * TC_ROWS * (TC_N + 1);
-#pragma unroll 1
-    for (int sl = 0; sl < SPW; ++sl) {
-      const int uu = warp * SPW + sl;
-      const uint32_t* ws = Wst + (size_t)uu * Gp * TC_WROW;
-      const uint32_t* xs = Xst + (size_t)uu * Gp * TC_COLS;
-      int acc[7][4];
+    const size_t b_grp = (size_t)B * cd.n_in * 8;  // words of one 4-slot group of the inputs
+    const uint32_t b_dst = sb + OFF_RAWB + ((b_pair * TC_GS + b_g) * 2 + b_c) * 16;
+    // weights are read once (evict first); inputs once per output-channel
+    // tile, by CTAs that run together (evict last)
+    const uint64_t pol_w = policy_evict_first(), pol_x = policy_evict_last();
+    auto issue = [&](int t) {
+      if (t < T) {
+        const int g0 = TC_GS * (t % nch), grp = grp0 + t / nch, r = t % TC_RING;
+        const uint32_t* ag = a_src + ((size_t)(grp >> 1) * G * 2 + (grp & 1)) * a_plane;
 #pragma unroll
-      for (int j = 0; j < 7; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0;
+        for (int k = 0; k < 2; ++k) {
+          const int g = 2 * a_gp + k;
+          const bool ok = a_ok && g0 + g < G;
+          cp16_pol(a_dst + r * RAWA_STEP + g * TC_M * 16, ok ? ag + (size_t)(g0 + g) * 2 * a_plane : w_tc,
+                   ok ? 16 : 0, pol_w);
+        }
+        if (pt < TC_CW * TC_GS) {
+          const bool ok = b_ok && g0 + b_g < G;
+          cp16_pol(b_dst + r * RAWB_STEP, ok ? b_src + grp * b_grp + (size_t)(g0 + b_g) * 8 : c_hat, ok ? 16 : 0,
+                   pol_x);
+        }
+      }
+      cp_commit();
+    };
+    // conversion roles: A row rrow, K chunk chh; B column pt >> 4, slot (pt >> 2) & 3, ciphertext pt & 3
+    const int rrow = 32 * (warp & 3) + lane, chh = warp >> 2;
+    const int bc_col = pt >> 4, bc_s = (pt >> 2) & 3, bc_g = pt & 3;
+    const uint32_t q = lc.q;
+    const uint32_t w1s = (uint32_t)((256ull << 32) / q), w2s = (uint32_t)((65536ull << 32) / q),
+                   w3s = (uint32_t)((16777216ull << 32) / q);
+    const uint2 bias_a = make_uint2(H_2048, 0), zero2 = make_uint2(0, 0);
 #pragma unroll 1
-      for (int g0 = 0; g0 < Gp; g0 += TC_GK) {
-        // A fragment: rows grp, grp+8; K columns 4t..4t+3 (g = g0+t) and 16+4t.. (g = g0+4+t)
-        const uint32_t* w0 = ws + (g0 + t) * TC_WROW;
-        const uint32_t* w1 = ws + (g0 + 4 + t) * TC_WROW;
-        const uint32_t a[4] = {w0[grp], w0[grp + 8], w1[grp], w1[grp + 8]};
-        const uint32_t* x0 = xs + (g0 + t) * TC_COLS;
-        const uint32_t* x1 = xs + (g0 + 4 + t) * TC_COLS;
+    for (int t = 0; t < TC_RING - 1; ++t) issue(t);
+#pragma unroll 1
+    for (int t = 0; t < T; ++t) {
+      const int st = t % TC_NS, r = t % TC_RING, g0 = TC_GS * (t % nch);
+      // stage st was last read by the MMAs of step t - TC_NS
+      if (!mbar_wait_bounded(&tile_empty[st], ((t / TC_NS) & 1) ^ 1)) p_abort[t & 1] = 1;
+      cp_wait<TC_RING - 2>();
+      named_bar_sync(1, TC_NPROD);  // raw step t visible to every producer; raw step t - 1 converted
+      if (p_abort[t & 1]) break;
+      issue(t + TC_RING - 1);        // into the ring slot of step t - 1
+      uint8_t* stage = tsm + OFF_TILE + st * STAGE_BYTES;
+      {  // A: 4 slots of row rrow, ciphertexts g0 + 2 chh, + 1
+        const uint4* ra = reinterpret_cast<const uint4*>(tsm + OFF_RAWA + r * RAWA_STEP);
+        const int gg = g0 + 2 * chh;
+        const uint4 x0 = ra[(2 * chh) * TC_M + rrow], x1 = ra[(2 * chh + 1) * TC_M + rrow];
+        const uint32_t w0[TC_U] = {x0.x, x0.y, x0.z, x0.w}, w1[TC_U] = {x1.x, x1.y, x1.z, x1.w};
+        uint8_t* ta = stage + ((rrow >> 3) * 2 + chh) * 128 + (rrow & 7) * 16;
+        if (gg + 1 < G) {
 #pragma unroll
-        for (int j = 0; j < 7; ++j) {
-          if (j < ntiles) {  // warp-uniform
-            // B fragment: column n = 8j + grp of the tile, K rows as for A
-            const int n = 8 * j + grp, cl = n / 7, s = n % 7;
-            mma_u8(acc[j], a, digit_window(x0[cl], s), digit_window(x1[cl], s));
+          for (int s = 0; s < TC_U; ++s) {
+            const uint2 d0 = digits4(w0[s]), d1 = digits4(w1[s]);
+            *reinterpret_cast<uint4*>(ta + s * TILEA_SLOT) = make_uint4(d0.x, d0.y, d1.x, d1.y);
+          }
+        } else {  // the last K step: ciphertext G carries the bias column, beyond it zeros
+#pragma unroll
+          for (int s = 0; s < TC_U; ++s) {
+            const uint2 d0 = gg < G ? digits4(w0[s]) : gg == G ? bias_a : zero2;
+            const uint2 d1 = gg + 1 == G ? bias_a : zero2;
+            *reinterpret_cast<uint4*>(ta + s * TILEA_SLOT) = make_uint4(d0.x, d0.y, d1.x, d1.y);
           }
         }
       }
-      // accumulators -> ys[row][n]: c0, c1 at row grp, c2, c3 at row grp + 8; n = 8j + 2t + {0, 1}
+      {  // B: rows (col, e), K (g, a) of slot bc_s
+        const uint32_t x = reinterpret_cast<const uint32_t*>(
+            tsm + OFF_RAWB + r * RAWB_STEP)[(((bc_col >> 1) * TC_GS + bc_g) * 2 + (bc_col & 1)) * 4 + bc_s];
+        const int gg = g0 + bc_g;
+        uint2 dd[4];
+        if (gg < G) {
+          const uint32_t y0 = x + 0x80808080u;
+          const uint32_t y1 = shoup_mul(x, 256u, w1s, q) + 0x80808080u;  // X'_a in [0, 2q), congruent to 256^a X
+          const uint32_t y2 = shoup_mul(x, 65536u, w2s, q) + 0x80808080u;
+          const uint32_t y3 = shoup_mul(x, 16777216u, w3s, q) + 0x80808080u;
 #pragma unroll
-      for (int j = 0; j < 7; ++j) {
-        if (j < ntiles) {
-          ys[grp * (TC_N + 1) + 8 * j + 2 * t] = acc[j][0];
-          ys[grp * (TC_N + 1) + 8 * j + 2 * t + 1] = acc[j][1];
-          ys[(grp + 8) * (TC_N + 1) + 8 * j + 2 * t] = acc[j][2];
-          ys[(grp + 8) * (TC_N + 1) + 8 * j + 2 * t + 1] = acc[j][3];
+          for (int e = 0; e < 4; ++e)
+            dd[e] = make_uint2(digits2(__byte_perm(y0, y1, e | ((4 + e) << 8))),
+                               digits2(__byte_perm(y2, y3, e | ((4 + e) << 8))));
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) dd[e] = make_uint2(gg == G ? H_6144 : 0, 0);
+        }
+        uint8_t* tb = stage + TC_U * TILEA_SLOT + bc_s * TILEB_SLOT + (bc_g >> 1) * 128 + (bc_g & 1) * 8;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int row = 4 * bc_col + e;
+          *reinterpret_cast<uint2*>(tb + (row >> 3) * 256 + (row & 7) * 16) = dd[e];
         }
       }
-      __syncwarp();
-      // Y = sum_s 2^(8s) Y_s mod q for the 16 x ncols outputs (lanes on valid
-      // pairs only): Y_0..Y_4 by shifts, plus ((Y_5 + 2^8 Y_6) mod q) *
-      // (2^40 mod q), one reduction.  With Y_s < 4 * 192 * 255^2 < 2^26 (G at
-      // most 192, the shared-memory limit) the first part stays below 2^59
-      // and the second below 2^60.
-      for (int p = lane; p < TC_ROWS * ncols; p += 32) {
-        const int ii = (int)(((unsigned)p * rc) >> 16), cl = p - ii * ncols;  // p / ncols, p < 128
-        const int* v = ys + ii * (TC_N + 1) + 7 * cl;
-        uint64_t lo = 0;
+      fence_async_smem();
+      mbar_arrive(&tile_full[st]);
+    }
+    cp_wait<0>();
+    if (p_abort[0] | p_abort[1]) s_abort = 1;
+  } else if (warp == TC_MMA_WARP) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+#pragma unroll 1
+      for (int t = 0; t < T; ++t) {
+        const int st = t % TC_NS, ch = t % nch, grp = t / nch, ab = grp & 1;
+        if (ch == 0 && !mbar_wait_bounded(&acc_empty[ab], ((grp >> 1) & 1) ^ 1)) {
+          s_abort = 1;
+          break;
+        }
+        if (!mbar_wait_bounded(&tile_full[st], (t / TC_NS) & 1)) {
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ta = sb + OFF_TILE + st * STAGE_BYTES, tb = ta + TC_U * TILEA_SLOT;
 #pragma unroll
-        for (int s = 0; s < 5; ++s) lo += (uint64_t)(uint32_t)v[s] << (8 * s);
-        const uint64_t hi = (uint64_t)(uint32_t)v[5] + ((uint64_t)(uint32_t)v[6] << 8);
-        Ot[(ii * TC_COLS + cl) * UP + uu] = red64(lo + (uint64_t)red64(hi, lc) * c40, lc);
+        for (int s = 0; s < TC_U; ++s)
+          mma_f16(tbase + (ab * TC_U + s) * TC_NN, smem_desc(ta + s * TILEA_SLOT, 128, 256),
+                  smem_desc(tb + s * TILEB_SLOT, 128, 256), idesc_f16(TC_M, TC_NN), ch > 0);
+        mma_commit(&tile_empty[st]);
+        if (ch == nch - 1) mma_commit(&acc_full[ab]);
       }
-      __syncwarp();  // ys is rewritten by the next slot
     }
-    __syncthreads();
-    // rows (i, column) of the group: U consecutive slots each, as 16-byte stores
-    for (int e = tid; e < TC_ROWS * TC_COLS * U4; e += TC_THREADS) {
-      const int q4 = e % U4, cl = (e / U4) % TC_COLS, ii = e / (U4 * TC_COLS);
-      if (i0 + ii < cd.Cout && cl < ncols)
-        reinterpret_cast<uint4*>(y_hat + colbase[cl] + (size_t)ii * rowstride)[q4] =
-            reinterpret_cast<const uint4*>(Ot + (ii * TC_COLS + cl) * UP)[q4];
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int qd = warp & 3;                          // tensor-memory lane quadrant: the warp index mod 4
+    const int hc = (warp - TC_PROD_WARPS) >> 2;       // columns 8 hc .. 8 hc + 7
+    const int rrow = 32 * qd + lane;
+    const bool row_ok = i0 + rrow < cd.Cout;
+    const float qinv = 1.0f / (float)lc.q;
+    const uint32_t nq = 0u - lc.q, cfix = FP_BIAS * lc.q + lc.q - FP_BIAS * 0x01010101u;
+    const uint32_t ta = tbase + ((uint32_t)(32 * qd) << 16);
+    // Groups come in pairs (8 slots, one 32-byte sector of every output row):
+    // the even group's results wait in registers for the odd one's.
+    constexpr int HS = 32 * TC_EPI_WARPS;  // hold[local column][slot][epilogue thread]
+    uint32_t* hold = reinterpret_cast<uint32_t*>(tsm + OFF_HOLD) + (tid - 32 * TC_PROD_WARPS);
+#pragma unroll 1
+    for (int grp = 0; grp < TC_GPC; ++grp) {
+      const int ab = grp & 1, u0 = 4 * (grp0 + grp);
+      if (!mbar_wait_bounded(&acc_full[ab], (grp >> 1) & 1)) {
+        s_abort = 1;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int p = 0; p < TC_CW / 4; ++p) {  // columns 8 hc + 2p, + 1
+        uint32_t v[TC_U][8];
+#pragma unroll
+        for (int s = 0; s < TC_U; ++s) tmem_ld8(ta + (ab * TC_U + s) * TC_NN + 4 * (8 * hc + 2 * p), v[s]);
+        tmem_wait_ld();
+        if (p == TC_CW / 4 - 1) {  // this warp's accumulators of the buffer are in registers
+          tc_fence_before();
+          mbar_arrive(&acc_empty[ab]);
+        }
+#pragma unroll
+        for (int cc2 = 0; cc2 < 2; ++cc2) {
+          const int cl = 2 * p + cc2, c = 8 * hc + cl;
+          uint32_t o[TC_U];
+#pragma unroll
+          for (int s = 0; s < TC_U; ++s) o[s] = recombine(&v[s][4 * cc2], qinv, nq, cfix);
+          if (ab == 0) {
+#pragma unroll
+            for (int s = 0; s < TC_U; ++s) hold[(cl * TC_U + s) * HS] = o[s];
+          } else {
+            const long long co = colout[c];
+            if (row_ok && co >= 0) {
+              uint4* dst = reinterpret_cast<uint4*>(y_hat + co + (size_t)(i0 + rrow) * rowstride + u0 - TC_U);
+              __stcs(dst, make_uint4(hold[(cl * TC_U) * HS], hold[(cl * TC_U + 1) * HS], hold[(cl * TC_U + 2) * HS],
+                                     hold[(cl * TC_U + 3) * HS]));
+              __stcs(dst + 1, make_uint4(o[0], o[1], o[2], o[3]));
+            }
+          }
+        }
+      }
     }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (s_abort && tid == 0) atomicOr(err, 1ull);
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tbase, TC_TMEM_COLS);
   }
 }
 
-// Row r = (oct * 2 + c) * L + l of y (NTT domain, values in [0, q)) becomes
+// Row r = (oct * 2 + c) * L + l of y (NTT domain, values in [0, 2q)) becomes
 // N times its inverse transform, + Delta_l * r[oct] when c == 0 and r is set.
+// Launched after the contraction as a programmatic dependent: it waits for
+// the contraction before its first read.
 template <int LOGN>
 __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
     k_intt_mask_rows(uint32_t* __restrict__ y, const uint32_t* __restrict__ r, const uint32_t* __restrict__ tw,
@@ -223,6 +484,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
   const size_t oct = row / (2 * (size_t)L);
   const LimbConst lc = cc.limb[l];
   uint32_t* p = y + row * N;
+  pdl_wait();
   for (int v = threadIdx.x; v < N / 4; v += T)
     *reinterpret_cast<uint4*>(sm + pad(4 * v)) = reinterpret_cast<const uint4*>(p)[v];
   __syncthreads();  // the whole row is in shared memory before any of it is overwritten
@@ -230,40 +492,93 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
                                 MaskStore{p, (r && c == 0) ? r + oct * N : nullptr, lc});
 }
 
-// Slots per warp for a layer: the most (4, 2) that still lets two CTAs share
-// an SM (113 KB of shared memory each), else 1.
-static int tc_spw(int G) {
-  const int gp = (G + TC_GK - 1) / TC_GK * TC_GK;
-  for (int spw = 4; spw > 1; spw /= 2)
-    if (tc_smem_words(spw, gp) * 4 <= 113 * 1024) return spw;
-  return 1;
+// Slot-tiled copy of the encoded weights for k_conv_tc: w_tc[l][u / 8][g][h][i][j]
+// = w_hat[l][i][g][u] with u = 8 (u / 8) + 4 h + j.  The same words in another
+// order: the weights of one K step of one CTA (4 ciphertexts, 2 halves, 128
+// output channels, 8 slots) become 8 runs of 2 KB.  One thread per (l, i, g,
+// slot group).
+__global__ void k_tc_weights(const uint32_t* __restrict__ w_hat, uint32_t* __restrict__ w_tc, int Cout, int G, int N,
+                             long long total) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int ng = N / 8;
+  const int grp = (int)(e % ng);
+  const long long lig = e / ng;  // (l * Cout + i) * G + g
+  const int g = (int)(lig % G), i = (int)((lig / G) % Cout), l = (int)(lig / ((long long)G * Cout));
+  const uint4* src = reinterpret_cast<const uint4*>(w_hat + lig * N + 8 * grp);
+  const uint4 a = src[0], b = src[1];
+  uint4* dst = reinterpret_cast<uint4*>(w_tc + ((((size_t)l * ng + grp) * G + g) * 2) * Cout * 4 + (size_t)i * 4);
+  dst[0] = a;
+  dst[(size_t)Cout] = b;
 }
 
-size_t conv_tc_smem_bytes(int G) {
-  const int gp = (G + TC_GK - 1) / TC_GK * TC_GK;
-  return tc_smem_words(tc_spw(G), gp) * 4;
-}
-
-template <int SPW>
-static cudaError_t conv_tc(int B, const ConvDims& cd, const uint32_t* w_hat, const uint32_t* c_hat, uint32_t* y_hat,
-                           int N, const CtxConst& cc, cudaStream_t st) {
-  const int gp = (cd.G + TC_GK - 1) / TC_GK * TC_GK;
-  const size_t smem = tc_smem_words(SPW, gp) * 4;
-  const dim3 grid(N / (8 * SPW), (cd.Cout + TC_ROWS - 1) / TC_ROWS, cc.L);
-  k_conv_tc<SPW><<<grid, TC_THREADS, smem, st>>>(w_hat, c_hat, y_hat, cd, B, N, cc);
+cudaError_t launch_tc_weights(const uint32_t* w_hat, uint32_t* w_tc, int L, int Cout, int G, int N, cudaStream_t st) {
+  const long long total = (long long)L * Cout * G * (N / 8);
+  if (total == 0) return cudaSuccess;
+  const long long blocks = (total + 255) / 256;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  k_tc_weights<<<(unsigned)blocks, 256, 0, st>>>(w_hat, w_tc, Cout, G, N, total);
   return cudaGetLastError();
 }
 
+// Slot-tiled copy of the NTT-domain inputs for k_conv_tc: c_tc[l][u / 4][b][ct][c][j]
+// = c_hat[b][ct][c][l][u] with u = 4 (u / 4) + j, so that one K step of one
+// CTA reads its 4 ciphertexts x 2 components of an image as one 128-byte run.
+// One thread per (l, b, ct, 4-slot group, c); neighbouring threads take the
+// two components, so each writes half of one 32-byte sector.
+__global__ void k_tc_inputs(const uint32_t* __restrict__ c_hat, uint32_t* __restrict__ c_tc, int n_in, int L, int N,
+                            long long total) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int c = (int)(e & 1), ng = N / 4;
+  const long long rest = e >> 1;
+  const int grp = (int)(rest % ng);
+  const long long bct = rest / ng;  // (b * L + l) * n_in + ct
+  const long long lb = bct / n_in;
+  const int ct = (int)(bct % n_in);
+  const int l = (int)(lb % L);
+  const long long b = lb / L;
+  const uint4 v = reinterpret_cast<const uint4*>(c_hat + (((b * n_in + ct) * 2 + c) * L + l) * (long long)N)[grp];
+  const long long B = total / ((long long)2 * ng * n_in * L);
+  reinterpret_cast<uint4*>(c_tc)[(((l * (long long)ng + grp) * B + b) * n_in + ct) * 2 + c] = v;
+}
+
+cudaError_t launch_tc_inputs(const uint32_t* c_hat, uint32_t* c_tc, int B, int n_in, int L, int N, cudaStream_t st) {
+  const long long total = (long long)B * n_in * L * 2 * (N / 4);
+  if (total == 0) return cudaSuccess;
+  const long long blocks = (total + 255) / 256;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  k_tc_inputs<<<(unsigned)blocks, 256, 0, st>>>(c_hat, c_tc, n_in, L, N, total);
+  return cudaGetLastError();
+}
+
+size_t conv_tc_smem_bytes() { return TC_SMEM; }
+
+static cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, size_t smem, cudaStream_t st, cudaLaunchAttribute* at,
+                                     bool pdl) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cfg;
+}
+
+// pdl: the previous operation in `st` is the forward NTT of these inputs.
 cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_hat, const uint32_t* c_hat, uint32_t* y_hat,
-                           int N, const CtxConst& cc, cudaStream_t st) {
+                           int N, const CtxConst& cc, unsigned long long* err, cudaStream_t st, bool pdl) {
   if (B == 0 || cd.Cout == 0) return cudaSuccess;
-  if ((cd.Cout + TC_ROWS - 1) / TC_ROWS > 65535 || conv_tc_smem_bytes(cd.G) > TC_MAX_DYN_SMEM)
-    return cudaErrorInvalidConfiguration;
-  switch (tc_spw(cd.G)) {
-    case 4: return conv_tc<4>(B, cd, w_hat, c_hat, y_hat, N, cc, st);
-    case 2: return conv_tc<2>(B, cd, w_hat, c_hat, y_hat, N, cc, st);
-    default: return conv_tc<1>(B, cd, w_hat, c_hat, y_hat, N, cc, st);
-  }
+  if (cd.G < 1 || cd.G > kTcMaxG) return cudaErrorInvalidValue;
+  const long long mtiles = (cd.Cout + TC_M - 1) / TC_M, nchunks = (2LL * B * cd.bands + TC_CW - 1) / TC_CW;
+  if (mtiles * nchunks > 0x7fffffffLL || N % (4 * TC_GPC) != 0) return cudaErrorInvalidConfiguration;
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)(mtiles * nchunks), N / (4 * TC_GPC), cc.L), dim3(TC_THREADS),
+                                      TC_SMEM, st, at, pdl);
+  return cudaLaunchKernelEx(&cfg, k_conv_tc, w_hat, c_hat, y_hat, cd, B, N, cc, err);
 }
 
 template <int LOGN>
@@ -273,13 +588,8 @@ static cudaError_t intt_rows_setup() {
 }
 
 cudaError_t launch_tc_setup(int logn) {
-  // the contraction kernels may use up to the per-CTA maximum of shared
-  // memory less 1 KB kept for their static part (the column offsets)
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_DYN_SMEM)) ||
-      (e = cudaFuncSetAttribute(k_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_DYN_SMEM)) ||
-      (e = cudaFuncSetAttribute(k_conv_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_DYN_SMEM)))
-    return e;
+  cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  if (e != cudaSuccess) return e;
   switch (logn) {
     case 11: return intt_rows_setup<11>();
     case 12: return intt_rows_setup<12>();
@@ -291,20 +601,23 @@ cudaError_t launch_tc_setup(int logn) {
 
 template <int LOGN>
 static cudaError_t intt_rows(long long rows, uint32_t* y, const uint32_t* r, const uint32_t* tw, const CtxConst& cc,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool pdl) {
   constexpr int N = 1 << LOGN;
-  k_intt_mask_rows<LOGN><<<(unsigned)rows, N / 32, (size_t)padded_words(N) * 4, st>>>(y, r, tw, cc);
-  return cudaGetLastError();
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)rows), dim3(N / 32), (size_t)padded_words(N) * 4, st, at, pdl);
+  return cudaLaunchKernelEx(&cfg, k_intt_mask_rows<LOGN>, y, r, tw, cc);
 }
 
+// pdl: the previous operation in `st` is the contraction that wrote y.
 cudaError_t launch_intt_mask_rows(int logn, long long rows, uint32_t* y, const uint32_t* r, const uint32_t* tw,
-                                  const CtxConst& cc, cudaStream_t st) {
+                                  const CtxConst& cc, cudaStream_t st, bool pdl) {
   if (rows == 0) return cudaSuccess;
+  if (rows > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   switch (logn) {
-    case 11: return intt_rows<11>(rows, y, r, tw, cc, st);
-    case 12: return intt_rows<12>(rows, y, r, tw, cc, st);
-    case 13: return intt_rows<13>(rows, y, r, tw, cc, st);
-    case 14: return intt_rows<14>(rows, y, r, tw, cc, st);
+    case 11: return intt_rows<11>(rows, y, r, tw, cc, st, pdl);
+    case 12: return intt_rows<12>(rows, y, r, tw, cc, st, pdl);
+    case 13: return intt_rows<13>(rows, y, r, tw, cc, st, pdl);
+    case 14: return intt_rows<14>(rows, y, r, tw, cc, st, pdl);
   }
   return cudaErrorInvalidValue;
 }

@@ -26,6 +26,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 FL_OK, FL_ERR_ARG, FL_ERR_SHAPE, FL_ERR_CUDA, FL_ERR_OOM, FL_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 FL_STACK_PER_LAYER, FL_STACK_PERSISTENT, FL_STACK_QUEUE = 0, 1, 2
 FL_NOALLOC_SCRATCH_BYTES = 16 << 20
+FL_TC_MAX_G = 64
 FL_STACK_MAX_LAYERS = 64
 
 
@@ -64,6 +65,10 @@ _SIGS = {
     "fl_mask_to_share": ([_vp, _i, _vp, _vp, _vp], _i),
     "fl_he_conv2d_direct": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "fl_he_conv2d_tc": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "fl_tc_weights": ([_vp, _gp, _vp, _vp, _vp], _i),
+    "fl_he_conv2d_tc_workspace_bytes": ([_vp, _gp, _i], _sz),
+    "fl_he_conv2d_tc_from_ntt": ([_vp, _gp, _i, _vp, _vp, _sz, _vp, _vp], _i),
+    "fl_intt_mask_outputs": ([_vp, _gp, _i, _vp, _vp, _vp], _i),
     "fl_mod_switch": ([_vp, _i, _vp, _i, _vp, _vp], _i),
     "fl_he_conv2d_otf": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_he_conv2d_mask": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
@@ -74,6 +79,7 @@ _SIGS = {
     "fl_he_conv2d_stack_ntt": ([_vp, ctypes.POINTER(StackLayer), _i, _vp, _sz, _vp], _i),
     "fl_he_conv2d_stack_run": ([_vp, ctypes.POINTER(StackLayer), _i, _vp, _sz, _vp], _i),
     "fl_stack_error": ([_vp, _vp, ctypes.POINTER(ctypes.c_uint64)], _i),
+    "fl_tc_error": ([_vp, _vp, ctypes.POINTER(ctypes.c_uint64)], _i),
     "fl_he_conv2d_mask_noalloc": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "fl_ctx_set_stack_kernel": ([_vp, _i], _i),
     "fl_ctx_get_stack_kernel": ([_vp], _i),
@@ -349,17 +355,63 @@ class Context:
                                         _stream(stream)))
         return out
 
-    def he_conv2d_tc(self, g, w_hat, ct_in, out=None, workspace=None, r=None, stream=None) -> torch.Tensor:
-        """Byte-split tensor-core form: the same ciphertexts as he_conv2d (plus
-        the mask when r is given) from the same encoded weights."""
+    def tc_workspace(self, g, B: int) -> torch.Tensor:
+        """Workspace of he_conv2d_tc: the inputs' NTT images and their
+        slot-tiled copy."""
+        nbytes = _lib.fl_he_conv2d_tc_workspace_bytes(self.h, ctypes.byref(g), B)
+        return torch.empty(max(nbytes, 16) // 4, dtype=torch.int32, device=f"cuda:{self.device}")
+
+    def tc_weights(self, g, w_hat, out=None, stream=None) -> torch.Tensor:
+        """The encoded weights [L][Cout][G][N] re-laid for he_conv2d_tc:
+        [L][N/8][G][2][Cout][4] (slot groups of 8)."""
+        _dev_u32(w_hat, (self.L, g.Cout, g.G, self.N), "w_hat")
+        shape = (self.L, self.N // 8, g.G, 2, g.Cout, 4)
+        out = torch.empty(shape, dtype=torch.int32, device=w_hat.device) if out is None else out
+        _dev_u32(out, shape, "out")
+        _check(_lib.fl_tc_weights(self.h, ctypes.byref(g), _ptr(w_hat), _ptr(out), _stream(stream)))
+        return out
+
+    def he_conv2d_tc(self, g, w_tc, ct_in, out=None, workspace=None, r=None, stream=None) -> torch.Tensor:
+        """Tensor-core form (tcgen05, fp16 digits, fp32 accumulation): the
+        same ciphertexts as he_conv2d (plus the mask when r is given) from
+        the encoded weights re-laid by tc_weights.  G <= FL_TC_MAX_G."""
         B = ct_in.shape[0]
         _dev_u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
+        _dev_u32(w_tc, (self.L, self.N // 8, g.G, 2, g.Cout, 4), "w_tc")
+        if r is not None:
+            _dev_u32(r, (B, g.n_out, self.N), "r")
         out = self._new(B, g.n_out, 2, self.L, self.N) if out is None else out
-        workspace = self.workspace(g, B) if workspace is None else workspace
-        _check(_lib.fl_he_conv2d_tc(self.h, ctypes.byref(g), B, _ptr(w_hat), _ptr(ct_in), _ptr(r), _ptr(out),
+        _dev_u32(out, (B, g.n_out, 2, self.L, self.N), "out")
+        workspace = self.tc_workspace(g, B) if workspace is None else workspace
+        _check(_lib.fl_he_conv2d_tc(self.h, ctypes.byref(g), B, _ptr(w_tc), _ptr(ct_in), _ptr(r), _ptr(out),
                                     _ptr(workspace), workspace.numel() * workspace.element_size(),
                                     _stream(stream)))
         return out
+
+    def he_conv2d_tc_from_ntt(self, g, B, w_tc, workspace, out, stream=None):
+        """Stage of he_conv2d_tc: the tensor-core contraction from a workspace
+        filled by he_conv2d_ntt_inputs; out gets NTT-domain values in [0, 2q)."""
+        _check(_lib.fl_he_conv2d_tc_from_ntt(self.h, ctypes.byref(g), B, _ptr(w_tc), _ptr(workspace),
+                                             workspace.numel() * workspace.element_size(), _ptr(out),
+                                             _stream(stream)))
+        return out
+
+    def intt_mask_outputs(self, g, out, r=None, stream=None):
+        """Stage of he_conv2d_tc: in-place inverse NTT of NTT-domain outputs,
+        plus the mask when r is given."""
+        B = out.shape[0]
+        _dev_u32(out, (B, g.n_out, 2, self.L, self.N), "out")
+        _check(_lib.fl_intt_mask_outputs(self.h, ctypes.byref(g), B, _ptr(r), _ptr(out), _stream(stream)))
+        return out
+
+    def tc_error(self, stream=None) -> int:
+        """Synchronise and read (and clear) the tensor-core form's error word:
+        0, or bit 0 when a bounded wait inside he_conv2d_tc ran out."""
+        v = ctypes.c_uint64()
+        rc = _lib.fl_tc_error(self.h, _stream(stream), ctypes.byref(v))
+        if rc not in (FL_OK, FL_ERR_TIMEOUT):
+            _check(rc)
+        return v.value
 
     def mod_switch(self, ct, L_out: int, out=None, stream=None) -> torch.Tensor:
         """Ciphertexts [..., 2, L, N] -> [..., 2, L_out, N] under the first L_out primes."""

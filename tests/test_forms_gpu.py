@@ -129,10 +129,13 @@ def test_otf_weights_bit_exact(fg, oracle, N, L, shape, B):
             assert (ym[b, sl] == oracle.mask(want, r[b, sl], c.primes)).all()
 
 
-# ------------------------------------------------------------------ byte-split tensor-core contraction
+# ------------------------------------------------------------------ tensor-core contraction (tcgen05)
 TC_CASES = CASES + [
-    (2048, 2, (8, 40, 6, 6, 3, 1, 1), 9),        # 18 columns: three column groups, the last ragged; 3 row tiles
+    (2048, 2, (8, 40, 6, 6, 3, 1, 1), 9),        # 18 columns: two column tiles, the second ragged
     (4096, 3, (96, 17, 8, 8, 3, 1, 1), 3),       # several K steps, Cout 17
+    (2048, 2, (8, 300, 6, 6, 3, 1, 1), 2),       # three output-channel tiles, the last ragged
+    (2048, 1, (512, 8, 14, 14, 3, 1, 1), 1),     # G = 64, the exactness limit (bias in its own K step)
+    (2048, 2, (504, 5, 14, 14, 3, 1, 1), 2),     # G = 63 (bias in the last K step)
 ]
 
 
@@ -149,8 +152,8 @@ def test_tc_form_bit_exact(fg, oracle, N, L, shape, B):
     r = synth.masks(14, (B, g.n_out, N), T)
     dw, dct, dr = dev(w, torch.int8), dev(ct), dev(r)
     wh = c.encode_weights(g, dw)
-    ym = u32(c.he_conv2d_tc(g, wh, dct, r=dr))
-    y = u32(c.he_conv2d_tc(g, wh, dct))
+    ym = u32(c.he_conv2d_tc(g, c.tc_weights(g, wh), dct, r=dr))
+    y = u32(c.he_conv2d_tc(g, c.tc_weights(g, wh), dct))
     assert (ym == u32(c.he_conv2d(g, wh, dct, r=dr))).all()
     assert (y == u32(c.he_conv2d(g, wh, dct))).all()
     assert (u32(dct) == ct).all()
@@ -163,21 +166,27 @@ def test_tc_form_bit_exact(fg, oracle, N, L, shape, B):
 
 
 def test_tc_form_extreme_digits(fg):
-    """Weights and inputs whose three low bytes are all 255 (the largest digit
-    products) and G = 20, so every tensor-core partial sum is at its bound:
-    the tensor-core form still equals the plain form."""
+    """G = 64 (the exactness limit) with weights and inputs made of residues
+    whose balanced digits are extreme (q - 1, 2^24 - 1, and byte patterns
+    0x80 / 0x7f that give digits of -128 and 127): the tensor-core form
+    still equals the plain form.  No bounded wait ran out."""
     N, L = 2048, 2
     c = ctx(fg, N, L)
-    g = c.geom(160, 20, 14, 14, 3, 1, 1)  # 8 channels of 16 x 16 padded rows per ciphertext
-    assert g.G == 20
-    big = [((q >> 24) << 24) - 1 for q in c.primes]  # bytes ff ff ff, then the top byte minus one
-    wh = torch.empty((L, g.Cout, g.G, N), dtype=torch.int32, device="cuda")
-    ct = torch.empty((1, g.n_in, 2, L, N), dtype=torch.int32, device="cuda")
-    for l, v in enumerate(big):
-        wh[l] = int(np.uint32(v).view(np.int32))
-        ct[:, :, :, l] = int(np.uint32(v).view(np.int32))
-    r = dev(synth.masks(15, (1, g.n_out, N), T))
-    assert torch.equal(c.he_conv2d_tc(g, wh, ct, r=r), c.he_conv2d(g, wh, ct, r=r))
+    g = c.geom(512, 20, 14, 14, 3, 1, 1)  # 8 channels of 16 x 16 padded rows per ciphertext
+    assert g.G == 64
+    rng = np.random.default_rng(16)
+    for pat in range(3):
+        wh = torch.empty((L, g.Cout, g.G, N), dtype=torch.int32, device="cuda")
+        ct = torch.empty((1, g.n_in, 2, L, N), dtype=torch.int32, device="cuda")
+        for l, q in enumerate(c.primes):
+            vals = [q - 1, (1 << 24) - 1, 0x00808080, 0x007F7F7F, 0x3F808080 % q, ((q >> 24) << 24) - 1]
+            a = rng.choice(vals, size=(g.Cout, g.G, N)) if pat == 2 else np.full((g.Cout, g.G, N), vals[pat])
+            x = rng.choice(vals, size=(1, g.n_in, 2, N)) if pat == 2 else np.full((1, g.n_in, 2, N), vals[pat])
+            wh[l] = torch.from_numpy(a.astype(np.uint32).view(np.int32)).cuda()
+            ct[:, :, :, l] = torch.from_numpy(x.astype(np.uint32).view(np.int32)).cuda()
+        r = dev(synth.masks(15 + pat, (1, g.n_out, N), T))
+        assert torch.equal(c.he_conv2d_tc(g, c.tc_weights(g, wh), ct, r=r), c.he_conv2d(g, wh, ct, r=r)), pat
+    assert c.tc_error() == 0
 
 
 def test_tc_form_empty_batch(fg):
@@ -185,19 +194,51 @@ def test_tc_form_empty_batch(fg):
     g = c.geom(3, 4, 8, 8, 3, 1, 1)
     wh = c.encode_weights(g, torch.zeros((4, 3, 3, 3), dtype=torch.int8, device="cuda"))
     empty = torch.empty((0, g.n_in, 2, 2, 2048), dtype=torch.int32, device="cuda")
-    assert c.he_conv2d_tc(g, wh, empty, workspace=torch.empty(16, dtype=torch.int32, device="cuda")).shape[0] == 0
+    ws = torch.empty(16, dtype=torch.int32, device="cuda")
+    assert c.he_conv2d_tc(g, c.tc_weights(g, wh), empty, workspace=ws).shape[0] == 0
 
 
-def test_tc_form_refuses_g_beyond_shared_memory(fg):
-    """G = 200 input ciphertexts do not fit one CTA's shared memory in the
-    tensor-core form: refused on the host before any launch; the plain form
-    still takes the layer."""
+def test_tc_form_stages_equal_the_one_call_form(fg):
+    """Input NTT, tensor-core contraction and inverse NTT + mask as three calls
+    give fl_he_conv2d_tc's ciphertexts (B = 3, two output-channel tiles)."""
+    N, L, B = 2048, 2, 3
+    c = ctx(fg, N, L)
+    g = c.geom(24, 130, 8, 8, 3, 1, 1)
+    wt = c.tc_weights(g, c.encode_weights(g, dev(synth.weights(4, (g.Cout, g.Cin, g.k, g.k)), torch.int8)))
+    ct = dev(synth.raw_ciphertexts(4, c.primes, (B, g.n_in, 2, L, N)))
+    r = dev(synth.masks(4, (B, g.n_out, N), T))
+    want = c.he_conv2d_tc(g, wt, ct, r=r)
+    ws = c.tc_workspace(g, B)
+    out = torch.full_like(want, -1)
+    c.he_conv2d_ntt_inputs(g, ct, ws)
+    c.he_conv2d_tc_from_ntt(g, B, wt, ws, out)
+    c.intt_mask_outputs(g, out, r=r)
+    assert torch.equal(out, want)
+    assert c.tc_error() == 0
+
+
+def test_tc_weights_are_the_encoded_weights_in_slot_groups(fg):
+    """tc_weights is a permutation: word [l][u/8][g][(u%8)/4][i][u%4] of the
+    re-laid weights is word [l][i][g][u] of the encoded ones."""
+    N, L = 2048, 2
+    c = ctx(fg, N, L)
+    g = c.geom(24, 5, 8, 8, 3, 1, 1)
+    wh = c.encode_weights(g, dev(synth.weights(3, (g.Cout, g.Cin, g.k, g.k)), torch.int8))
+    got = c.tc_weights(g, wh).cpu().numpy()
+    want = wh.cpu().numpy().reshape(L, g.Cout, g.G, N // 8, 2, 4).transpose(0, 3, 2, 4, 1, 5)
+    assert (got == want).all()
+
+
+def test_tc_form_refuses_g_beyond_the_exact_range(fg):
+    """G = 65 input ciphertexts would let the fp32 digit sums leave the exact
+    integer range: refused on the host before any launch (FL_ERR_SHAPE);
+    the plain form still takes the layer."""
     N, L = 2048, 1
     c = ctx(fg, N, L)
-    g = c.geom(1600, 1, 14, 14, 3, 1, 1)  # 8 channels of 16 x 16 padded rows per ciphertext
-    assert g.G == 200
+    g = c.geom(520, 1, 14, 14, 3, 1, 1)  # 8 channels of 16 x 16 padded rows per ciphertext
+    assert g.G == fg.FL_TC_MAX_G + 1
     wh = torch.zeros((L, g.Cout, g.G, N), dtype=torch.int32, device="cuda")
     ct = torch.zeros((1, g.n_in, 2, L, N), dtype=torch.int32, device="cuda")
-    with pytest.raises(fg.FlashError, match="shared memory"):
-        c.he_conv2d_tc(g, wh, ct)
+    with pytest.raises(fg.FlashError, match="exact"):
+        c.he_conv2d_tc(g, c.tc_weights(g, wh), ct)
     assert int(c.he_conv2d(g, wh, ct).abs().sum()) == 0

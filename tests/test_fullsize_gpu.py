@@ -110,11 +110,13 @@ def test_tc_form_full_stack_in_the_bench_configuration(fg, oracle, config):
     specs, filters = _bench_layers(c, wl, 7)
     assert max(sp["g"].G for sp in specs) == (52 if config == "resnet50-b8" else 10)
     for sp in specs:
-        sp["ws"] = c.workspace(sp["g"], wl.B)
+        sp["ws"] = c.tc_workspace(sp["g"], wl.B)
+        sp["w_tc"] = c.tc_weights(sp["g"], sp["w_hat"])
+        del sp["w_hat"]
 
     def step(st):
         for sp in specs:
-            c.he_conv2d_tc(sp["g"], sp["w_hat"], sp["ct_in"], out=sp["out"], workspace=sp["ws"], r=sp["r"],
+            c.he_conv2d_tc(sp["g"], sp["w_tc"], sp["ct_in"], out=sp["out"], workspace=sp["ws"], r=sp["r"],
                            stream=st)
 
     stream, graph = _replay_once(step)
