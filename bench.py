@@ -428,7 +428,7 @@ class ClockSampler:
                 "reasons": reasons, "samples_under_load": len(load)}
 
 
-def run_gpu(args, wl, rank, world, local_rank):
+def run_gpu(args, wl, rank, world, local_rank, emit=True):
     import torch
     import torch.distributed as dist
 
@@ -459,22 +459,37 @@ def run_gpu(args, wl, rank, world, local_rank):
         a = synth.device_uniform_residues(seed, ctx.primes, (B, g.n_in, L, N), li, device=dev)
         e = synth.device_cbd_noise(seed, (B, g.n_in, N), li, device=dev)
         w_dev = to_dev(w, torch.int8)
-        w_hat = ctx.encode_weights(g, w_dev) if args.form in ("ntt", "tc") else None
+        w_hat = ctx.encode_weights(g, w_dev) if args.form in ("ntt", "tc", "auto") else None
         if args.form == "tc":  # the tensor-core form reads the weights in slot groups of 8
             w_hat = ctx.tc_weights(g, w_hat)
         lay = {"g": g, "w": w_dev, "w_hat": w_hat,
                "ct": ctx.encrypt(sk, g, to_dev(x), a, e),
                "r": synth.device_masks(seed, (B, g.n_out, N), T_PLAIN, li, device=dev),
                "out": torch.empty((B, g.n_out, 2, L, N), dtype=torch.int32, device=dev)}
+        lay["ct_in"] = lay["ct"]
+        lay["form"] = "tc" if args.form == "tc" else "plain"
         del a, e
         layers.append(lay)
+    tuning = {}
+    if args.form == "auto":
+        # per layer the faster of the plain fused form and the tensor-core
+        # form (layers that choose the latter keep only their re-laid weights)
+        from paper_2401_16732_gb300.autotune import tune_forms
+        tuning["forms"] = tune_forms(ctx, layers, stream=stream, cache=None)
+        for lay in layers:
+            if lay["form"] == "tc":
+                lay["ws"] = ctx.tc_workspace(lay["g"], B)
+    plain_layers = [lay for lay in layers if lay["form"] == "plain"]
+    tc_layers = [lay for lay in layers if lay["form"] == "tc"]
     arr = ws = None
-    if args.form == "ntt":
+    if args.form == "ntt" or (args.form == "auto" and plain_layers):
         arr = ctx.stack_layers([{"g": lay["g"], "w_hat": lay["w_hat"], "ct_in": lay["ct"], "r": lay["r"],
-                                 "out": lay["out"]} for lay in layers])
+                                 "out": lay["out"]} for lay in plain_layers])
         ws = ctx.stack_workspace(arr)
     torch.cuda.synchronize()
-    if args.form in ("direct", "otf", "tc"):
+    if args.form == "auto" and arr is None:
+        tuned = {"kernel": "tc", "ms": None}
+    elif args.form in ("direct", "otf", "tc"):
         tuned = {"kernel": args.form, "ms": None}
         if args.form in ("otf", "tc"):
             for lay in layers:
@@ -494,6 +509,37 @@ def run_gpu(args, wl, rank, world, local_rank):
         # / `arr_` select another set of output buffers
         outs = outs or [lay["out"] for lay in layers]
         arr_ = arr if arr_ is None else arr_
+        if args.form == "auto":
+            # the plain layers as one stack call, then the tensor-core layers;
+            # with `events` ({"stack": 3 events, "tc": 4 per layer}) the
+            # stages are bracketed and called separately
+            if arr_ is not None:
+                if events is None:
+                    ctx.he_conv2d_stack(arr_, ws, stream=stream, stage="all")
+                else:
+                    events["stack"][0].record(stream)
+                    ctx.he_conv2d_stack(arr_, ws, stream=stream, stage="ntt")
+                    events["stack"][1].record(stream)
+                    ctx.he_conv2d_stack(arr_, ws, stream=stream, stage="run")
+                    events["stack"][2].record(stream)
+            k = 0
+            for lay, o in zip(layers, outs):
+                if lay["form"] != "tc":
+                    continue
+                if events is None:
+                    ctx.he_conv2d_tc(lay["g"], lay["w_tc"], lay["ct"], out=o, workspace=lay["ws"], r=lay["r"],
+                                     stream=stream)
+                    continue
+                ev = events["tc"][k]
+                k += 1
+                ev[0].record(stream)
+                ctx.he_conv2d_ntt_inputs(lay["g"], lay["ct"], lay["ws"], stream=stream)
+                ev[1].record(stream)
+                ctx.he_conv2d_tc_from_ntt(lay["g"], B, lay["w_tc"], lay["ws"], o, stream=stream)
+                ev[2].record(stream)
+                ctx.intt_mask_outputs(lay["g"], o, r=lay["r"], stream=stream)
+                ev[3].record(stream)
+            return
         if events is not None and args.form != "tc":
             events[0].record(stream)
         if args.form == "direct":
@@ -545,6 +591,14 @@ def run_gpu(args, wl, rank, world, local_rank):
         ctx.he_conv2d_stack(arr_, ws, stream=stream, stage="run")
         events[2].record(stream)
 
+    if args.form in ("ntt", "tc", "auto") and not args.no_tune:
+        # pass plan of the input NTTs (and of the tensor-core form's
+        # inverse-NTT rows), tensor-core tile: each timed on the whole step
+        from paper_2401_16732_gb300.autotune import tune_ntt_plan, tune_tc_tile
+        tuning["ntt_plan"] = tune_ntt_plan(ctx, lambda st: step(), stream=stream)
+        if tc_layers:
+            tuning["tc_tile"] = tune_tc_tile(ctx, lambda st: step(), stream=stream)
+
     # capture one step in a CUDA graph (40 launches for ResNet-18)
     with torch.cuda.stream(stream):
         step()
@@ -552,9 +606,11 @@ def run_gpu(args, wl, rank, world, local_rank):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         step()
-    launches_per_step = {"persistent": 2, "queue": 2, "direct": len(layers), "otf": 2 * len(layers),
-                         "tc": 3 * len(layers)}.get(
-        tuned["kernel"], 1 + len(layers))
+    stack_launches = {"persistent": 2, "queue": 2}.get(tuned["kernel"], 1 + len(plain_layers))
+    launches_per_step = {"direct": len(layers), "otf": 2 * len(layers), "tc": 4 * len(layers)}.get(
+        tuned["kernel"], stack_launches)
+    if args.form == "auto":  # stack launches + input NTT, input layout, contraction, inverse NTT per TC layer
+        launches_per_step = (stack_launches if plain_layers else 0) + 4 * len(tc_layers)
 
     def barrier():
         if world > 1:
@@ -591,22 +647,26 @@ def run_gpu(args, wl, rank, world, local_rank):
     for _ in range(nrep):
         with torch.cuda.stream(stream):
             torch.cuda._sleep(2_000_000)
-        if args.form == "tc":
-            evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in layers]
-            step(evs)
+        if args.form in ("tc", "auto"):
+            tcev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in tc_layers]
+            sev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            step(tcev if args.form == "tc" else {"stack": sev, "tc": tcev})
             stream.synchronize()
-            for ev in evs:
+            for ev in tcev:
                 kern["ntt"] += ev[0].elapsed_time(ev[1]) / nrep
                 kern["tc"] += ev[1].elapsed_time(ev[2]) / nrep
                 kern["intt"] += ev[2].elapsed_time(ev[3]) / nrep
-            kern["conv"] = kern["tc"] + kern["intt"]
+            if args.form == "auto" and arr is not None:
+                kern["ntt"] += sev[0].elapsed_time(sev[1]) / nrep
+                kern["stack"] = kern.get("stack", 0.0) + sev[1].elapsed_time(sev[2]) / nrep
+            kern["conv"] = kern["tc"] + kern["intt"] + kern.get("stack", 0.0)
             continue
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         step(evs)
         stream.synchronize()
         kern["ntt"] += evs[0].elapsed_time(evs[1]) / nrep
         kern["conv"] += evs[1].elapsed_time(evs[2]) / nrep
-    if args.form == "tc" and ctx.tc_error(stream):
+    if args.form in ("tc", "auto") and ctx.tc_error(stream):
         raise RuntimeError("a bounded wait of the tensor-core contraction ran out")
     err_word = ctx.stack_error(ws, stream=stream) if ws is not None else 0
     if err_word:
@@ -635,9 +695,9 @@ def run_gpu(args, wl, rank, world, local_rank):
         if free > 1.25 * d2h + (2 << 30):
             outs2 = [torch.empty_like(lay["out"]) for lay in layers]
             arr2 = None
-            if args.form == "ntt":
+            if arr is not None:
                 arr2 = ctx.stack_layers([{"g": lay["g"], "w_hat": lay["w_hat"], "ct_in": lay["ct"], "r": lay["r"],
-                                          "out": o} for lay, o in zip(layers, outs2)])
+                                          "out": o} for lay, o in zip(layers, outs2) if lay["form"] == "plain"])
             with torch.cuda.stream(stream):
                 step(outs=outs2, arr_=arr2)
             stream.synchronize()
@@ -793,6 +853,19 @@ def run_gpu(args, wl, rank, world, local_rank):
         roof, other_k = (tc_line, intt_line) if kern["tc"] >= kern["intt"] else (intt_line, tc_line)
         roof = dict(roof, other_kernels=[other_k], ntt_inputs_ms_per_step=kern["ntt"])
         kname = roof["kernel"]
+    if args.form == "auto":
+        # the step's kernels: the plain layers' stack (contraction + INTT +
+        # mask, fused) and the tensor-core layers' contraction and
+        # inverse-NTT rows; against the ALU bound on every output INTT
+        ks = (kern.get("stack", 0.0) + kern["tc"] + kern["intt"]) * 1e-3
+        roof = dict(alu_line, achieved=bfly / ks / 1e12, frac=bfly / ks / ALU_BFLY_PEAK,
+                    kernel=f"{len(plain_layers)} layers plain (stack kernel {tuned['kernel']}), "
+                           f"{len(tc_layers)} layers tensor-core (k_conv_tc + k_intt_mask_rows)",
+                    kernel_ms_per_step={"plain_stack": kern.get("stack", 0.0), "k_conv_tc": kern["tc"],
+                                        "k_intt_mask_rows": kern["intt"], "input_ntt": kern["ntt"]},
+                    algorithmic_butterflies_per_step=bfly, other_roofline=dict(hbm_line, achieved=conv_bytes / ks / 1e9,
+                                                                             frac=conv_bytes / ks / 1e9 / hbm))
+        kname = roof["kernel"]
     line = {
         "metric": "encrypted conv layers/s", "value": value, "unit": "layers/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -800,7 +873,8 @@ def run_gpu(args, wl, rank, world, local_rank):
         "config": {"workload": wl.name, "layers": len(layers), "batch": B, "N": N, "L": L, "t": T_PLAIN,
                    "l2": f"no flush: {step_bytes / 1e9:.2f} GB of algorithmic traffic per step > {L2_BYTES / 1e6:.0f} MB L2",
                    "graph": "one CUDA graph per step: input NTT of all layers + the contraction/INTT/mask kernel(s)",
-                   "stack_kernel": tuned["kernel"], "autotune_ms": tuned["ms"], "form": args.form},
+                   "stack_kernel": tuned["kernel"], "autotune_ms": tuned["ms"], "form": args.form,
+                   "ntt_plan": ctx.ntt_plan, "tc_tile": ctx.tc_tile, "tuning": tuning},
         "slot_mac_per_s": world * macs * args.steps / (ms * 1e-3),
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,
@@ -812,8 +886,65 @@ def run_gpu(args, wl, rank, world, local_rank):
         line["e2e_switched"] = e2e_switched
     if world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(wl, args.seed)
+    if not emit:
+        return line
+    if world == 1 and args.config == "resnet18" and args.form == "ntt" and not args.no_batched:
+        del layers, graph, arr, ws
+        line["batched"] = run_batched(args, local_rank)
     print(json.dumps(line), flush=True)
     return 0
+
+
+BATCHED = (("resnet18-b64", "ntt"), ("resnet18-b64", "tc"), ("resnet18-b64", "auto"),
+           ("resnet50-b8", "ntt"), ("resnet50-b8", "tc"), ("resnet50-b8", "auto"))
+
+
+def run_batched(args, local_rank):
+    """The batched stacks (ResNet-18 CIFAR B=64, ResNet-50 ImageNet B=8) in the
+    plain form, the tensor-core form and the autotuned per-layer mix, each
+    measured as the default line is (one CUDA graph per step, device-side
+    events, clocks during the timed region), at up to 5 timed steps, without
+    the end-to-end and CPU legs.  Returns {config: {form: summary}}."""
+    import argparse as _ap
+
+    import torch
+    out = {}
+    for cfg, form in BATCHED:
+        a = _ap.Namespace(**vars(args))
+        a.config, a.form, a.steps, a.skip_e2e, a.skip_cpu, a.no_batched = cfg, form, min(args.steps, 5), True, True, True
+        torch.cuda.empty_cache()
+        try:
+            ln = run_gpu(a, WORKLOADS[cfg], 0, 1, local_rank, emit=False)
+        except Exception as exc:  # report, keep the headline line
+            out.setdefault(cfg, {})[form] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            continue
+        r = ln["roofline"]
+        summ = {"value": ln["value"], "unit": ln["unit"], "ms_per_step": ln["ms_per_step"], "steps": ln["steps"],
+                "gpu_launches": ln["gpu_launches"], "stack_kernel": ln["config"]["stack_kernel"],
+                "ntt_plan": ln["config"]["ntt_plan"], "tc_tile": ln["config"]["tc_tile"], "clocks": ln["clocks"],
+                "roofline": {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel",
+                                               "kernel_ms_per_step", "traffic", "peak_source") if k in r}}
+        if "other_roofline" in r:
+            summ["roofline"]["other_roofline"] = {k: r["other_roofline"][k] for k in ("bound", "achieved", "unit",
+                                                                                      "frac")}
+        if "other_kernels" in r:
+            summ["roofline"]["other_kernels"] = [{k: o[k] for k in ("kernel", "bound", "achieved", "unit", "frac",
+                                                                  "kernel_ms_per_step") if k in o}
+                                                 for o in r["other_kernels"]]
+        tun = ln["config"].get("tuning") or {}
+        if "forms" in tun:
+            summ["forms"] = [f["form"] for f in tun["forms"]]
+            summ["form_ms"] = [f["ms"] for f in tun["forms"]]
+        summ["tuning_ms"] = {k: v["ms"] for k, v in tun.items() if k != "forms"}
+        out.setdefault(cfg, {})[form] = summ
+        del ln
+    torch.cuda.empty_cache()
+    for cfg, forms in out.items():
+        if "ntt" in forms and "value" in forms["ntt"]:
+            for f, summ in forms.items():
+                if f != "ntt" and "value" in summ:
+                    summ["speedup_over_plain"] = summ["value"] / forms["ntt"]["value"]
+    return out
 
 
 def run_x2x(args, rank, world, local_rank):
@@ -1034,10 +1165,15 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--form", default="ntt", choices=["ntt", "direct", "otf", "tc"],
+    ap.add_argument("--form", default="ntt", choices=["ntt", "direct", "otf", "tc", "auto"],
                     help="ntt: the NTT route with encoded weights (default); direct: the paper's DRot + CMult form "
                          "on the GPU; otf: the NTT route with weights rebuilt on the fly (no encoded weights); "
-                         "tc: the NTT route with the byte-split tensor-core contraction (not fused with the INTT)")
+                         "tc: the NTT route with the tensor-core contraction (tcgen05, not fused with the INTT); "
+                         "auto: per layer the faster of the plain and tensor-core forms (autotuned)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default NTT pass plan and tensor-core tile (no autotuning of them)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default workload only: skip the batched-stack measurements added to its line")
     ap.add_argument("--stack-kernel", default="auto", choices=["auto", "per_layer", "persistent", "queue"],
                     help="kernel for the contraction/INTT/mask stage (auto: time both, keep the faster)")
     args = ap.parse_args()

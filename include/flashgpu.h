@@ -337,6 +337,22 @@ int fl_he_conv2d_stack_run(fl_ctx *ctx, const fl_stack_layer *layers, int n_laye
 int fl_ctx_set_stack_kernel(fl_ctx *ctx, int kernel);
 int fl_ctx_get_stack_kernel(const fl_ctx *ctx);
 
+/* Tuning choices of a context (the Python package's autotuner times them
+ * per workload); every choice gives bit-identical results.
+ * - NTT pass plan: the forward NTT of the inputs (single layers, stacks and
+ *   the tensor-core form; also fl_ntt_forward) and the inverse-NTT-rows kernel of the
+ *   tensor-core form run log2 N stages as two row-strided passes of radix
+ *   2^r1 and 2^(log2 N - 5 - r1), then one radix-32 pass.  Available r1:
+ *   3 at N = 2048; 3, 4 at 4096; 3, 4, 5 at 8192; 4, 5 at 16384; 0 selects
+ *   the default (3, 4, 4, 5 for the four ring degrees).  FL_ERR_ARG for any
+ *   other value.  The getter returns the r1 in use.
+ * - Tensor-core tile: slot groups of 4 per CTA of fl_he_conv2d_tc (4, 8 or
+ *   16; 0 selects the default 16).  FL_ERR_ARG otherwise. */
+int fl_ctx_set_ntt_plan(fl_ctx *ctx, int r1);
+int fl_ctx_get_ntt_plan(const fl_ctx *ctx);
+int fl_ctx_set_tc_tile(fl_ctx *ctx, int groups);
+int fl_ctx_get_tc_tile(const fl_ctx *ctx);
+
 /* Synchronise `stream` and read the error word of a workspace last used by
  * fl_he_conv2d_stack into *error_host.  Returns FL_OK when the word is 0 and
  * FL_ERR_TIMEOUT when an internal wait ran out: bit 0 means the contraction

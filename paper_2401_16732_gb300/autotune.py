@@ -99,3 +99,121 @@ def tune_stack(ctx: flashgpu.Context, specs, arr, ws, stream=None, reps: int = 3
         except OSError:
             pass
     return {"kernel": best, "ms": ms, "cached": False}
+
+
+# ---------------------------------------------------------------------------
+# NTT pass plan, tensor-core tile and per-layer form
+# ---------------------------------------------------------------------------
+def time_call(fn, stream, reps: int = 3, graph: bool = True) -> float:
+    """Mean milliseconds of `fn(stream)`: 4*reps back-to-back replays of it
+    captured as a CUDA graph (graph=True, after two warm-up replays), else
+    the best of reps+1 eager calls."""
+    torch.cuda.synchronize()
+    st = stream if stream != torch.cuda.default_stream(stream.device) else torch.cuda.Stream(stream.device)
+    if graph:
+        with torch.cuda.stream(st):
+            fn(st)
+        st.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            fn(st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            for _ in range(2):
+                g.replay()
+            e0.record(st)
+            for _ in range(4 * reps):
+                g.replay()
+            e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / (4 * reps)
+    best = None
+    for _ in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn(st)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return best
+
+
+def _choose(ctx, attr: str, options, fn, stream, reps, graph):
+    """Time fn with ctx.<attr> set to every option; keep the fastest set."""
+    ms = {}
+    for opt in options:
+        setattr(ctx, attr, opt)
+        ms[str(opt)] = time_call(fn, stream, reps, graph)
+    best = min(ms, key=ms.get)
+    setattr(ctx, attr, int(best))
+    return {"choice": int(best), "ms": ms}
+
+
+def tune_ntt_plan(ctx: flashgpu.Context, fn, stream=None, reps: int = 3, graph: bool = True):
+    """Pick the NTT pass plan (first row pass radix 2^r1) for a workload: fn
+    runs the workload's step (its input NTTs, and the inverse-NTT-rows kernel
+    of the tensor-core form, use the context's plan)."""
+    stream = stream or torch.cuda.current_stream()
+    return _choose(ctx, "ntt_plan", flashgpu.NTT_PLANS[ctx.N.bit_length() - 1], fn, stream, reps, graph)
+
+
+def tune_tc_tile(ctx: flashgpu.Context, fn, stream=None, reps: int = 3, graph: bool = True):
+    """Pick the tensor-core tile (slot groups of 4 per CTA) for a workload."""
+    stream = stream or torch.cuda.current_stream()
+    return _choose(ctx, "tc_tile", flashgpu.TC_TILES, fn, stream, reps, graph)
+
+
+def tune_forms(ctx: flashgpu.Context, layers, stream=None, reps: int = 3, graph: bool = True,
+               cache: str | None = DEFAULT_CACHE):
+    """Per layer, time the plain fused form (he_conv2d with the mask) against
+    the tensor-core form (he_conv2d_tc) and keep the faster.  `layers` holds
+    dicts with g, w_hat, ct_in, r, out; the tensor-core weights are built for
+    the timing and kept (as "w_tc") only for layers that choose that form, and
+    "w_hat" is dropped from those, so at most one extra weight copy is live at
+    a time.  Layers with G above FL_TC_MAX_G stay plain.  Returns the list of
+    {"form", "ms": {"plain", "tc"}} per layer; each layer dict gets "form"."""
+    stream = stream or torch.cuda.current_stream()
+    table = {}
+    if cache and os.path.exists(cache):
+        try:
+            with open(cache) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+    dev = torch.cuda.get_device_name(ctx.device)
+    out = []
+    for lay in layers:
+        g, B = lay["g"], int(lay["ct_in"].shape[0])
+        key = hashlib.sha256(json.dumps([dev, "form", ctx.N, ctx.L, ctx.ntt_plan, ctx.tc_tile, B,
+                                         (g.Cin, g.Cout, g.H, g.W, g.k, g.stride, g.pad)]).encode()).hexdigest()[:24]
+        if g.G > flashgpu.FL_TC_MAX_G:
+            res = {"form": "plain", "ms": {"plain": None, "tc": None}}
+        elif key in table:
+            res = dict(table[key], cached=True)
+        else:
+            ws = ctx.workspace(g, B)
+            wst = ctx.tc_workspace(g, B)
+            w_tc = ctx.tc_weights(g, lay["w_hat"])
+            ms = {"plain": time_call(lambda st: ctx.he_conv2d(g, lay["w_hat"], lay["ct_in"], out=lay["out"],
+                                                              workspace=ws, r=lay["r"], stream=st),
+                                     stream, reps, graph),
+                  "tc": time_call(lambda st: ctx.he_conv2d_tc(g, w_tc, lay["ct_in"], out=lay["out"], workspace=wst,
+                                                              r=lay["r"], stream=st),
+                                  stream, reps, graph)}
+            res = {"form": min(ms, key=ms.get), "ms": ms}
+            table[key] = res
+            del ws, wst, w_tc
+        lay["form"] = res["form"]
+        if res["form"] == "tc":
+            lay["w_tc"] = ctx.tc_weights(g, lay["w_hat"])
+            del lay["w_hat"]
+        out.append(res)
+    if cache:
+        try:
+            os.makedirs(os.path.dirname(cache), exist_ok=True)
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1)
+        except OSError:
+            pass
+    return out

@@ -25,6 +25,8 @@ constexpr int kAuxStreams = 3;
 struct fl_ctx {
   int N, logN, L, device, sms;
   int stack_kernel;  // FL_STACK_PER_LAYER, FL_STACK_PERSISTENT or FL_STACK_QUEUE
+  int ntt_plan;      // first row-pass radix exponent of the input NTT and inverse-NTT-rows kernels (0: default)
+  int tc_tile;       // slot groups of 4 per tensor-core CTA (0: default)
   // per-layer stack launches fan out over these (fork/join through events)
   cudaStream_t aux[kAuxStreams];
   cudaEvent_t fork_ev, join_ev[kAuxStreams];
@@ -509,7 +511,7 @@ static int stage_ntt(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_
                      cudaStream_t st) {
   const int rows = B * geom->n_in * 2 * ctx->L;
   return launched(fl::launch_ntt_fwd(ctx->logN, rows, ct_in_dev, rows, 0, (uint32_t*)ws, rows, 0, 1, ctx->tw,
-                                     ctx->cc, st),
+                                     ctx->cc, st, ctx->ntt_plan),
                   "input ntt");
 }
 
@@ -642,7 +644,8 @@ static int stage_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t
   if ((rc = launched(fl::launch_tc_inputs(c_hat, c_tc, B, geom->n_in, ctx->L, ctx->N, st), "tensor-core input layout")))
     return rc;
   return launched(fl::launch_conv_tc(B, fl::ConvDims{geom->Cout, geom->G, geom->n_in, geom->n_out, geom->bands},
-                                     w_tc_dev, c_tc, ct_out_dev, ctx->N, ctx->cc, ctx->tc_err, st, true),
+                                     w_tc_dev, c_tc, ct_out_dev, ctx->N, ctx->cc, ctx->tc_err, st, true,
+                                     ctx->tc_tile),
                   "tensor-core contraction");
 }
 
@@ -658,7 +661,7 @@ int fl_he_conv2d_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t
   if ((rc = stage_ntt(ctx, geom, B, ct_in_dev, workspace_dev, st))) return rc;
   if ((rc = stage_tc(ctx, geom, B, w_tc_dev, workspace_dev, ct_out_dev, st))) return rc;
   return launched(fl::launch_intt_mask_rows(ctx->logN, (long long)B * geom->n_out * 2 * ctx->L, ct_out_dev, r_dev,
-                                            ctx->tw, ctx->cc, st, true),
+                                            ctx->tw, ctx->cc, st, true, ctx->ntt_plan),
                   "output inverse ntt");
 }
 
@@ -682,7 +685,7 @@ int fl_intt_mask_outputs(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uin
   if ((long long)B * geom->n_out * 2 * ctx->L > 0x7fffffffLL)
     return fail(FL_ERR_ARG, "B=%d: too many output rows for one launch", B);
   return launched(fl::launch_intt_mask_rows(ctx->logN, (long long)B * geom->n_out * 2 * ctx->L, ct_out_dev, r_dev,
-                                            ctx->tw, ctx->cc, (cudaStream_t)stream, false),
+                                            ctx->tw, ctx->cc, (cudaStream_t)stream, false, ctx->ntt_plan),
                   "output inverse ntt");
 }
 
@@ -810,7 +813,8 @@ static int stack_impl(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, v
   if ((stages & 2) && ctx->stack_kernel != FL_STACK_PERSISTENT &&
       (e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess)
     return cuda_fail(e, "control reset");
-  if ((stages & 1) && (rc = launched(fl::launch_ntt_multi(ctx->logN, segs, ctx->tw, ctx->cc, st), "stack input ntt")))
+  if ((stages & 1) &&
+      (rc = launched(fl::launch_ntt_multi(ctx->logN, segs, ctx->tw, ctx->cc, st, ctx->ntt_plan), "stack input ntt")))
     return rc;
   if (!(stages & 2)) return FL_OK;
   if (ctx->stack_kernel == FL_STACK_PERSISTENT)
@@ -854,6 +858,28 @@ int fl_ctx_set_stack_kernel(fl_ctx* ctx, int kernel) {
 }
 
 int fl_ctx_get_stack_kernel(const fl_ctx* ctx) { return ctx ? ctx->stack_kernel : FL_ERR_ARG; }
+
+int fl_ctx_set_ntt_plan(fl_ctx* ctx, int r1) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (!fl::plan_available(ctx->logN, r1))
+    return fail(FL_ERR_ARG, "pass plan r1=%d is not available at N=%d", r1, ctx->N);
+  ctx->ntt_plan = r1;
+  return FL_OK;
+}
+
+int fl_ctx_get_ntt_plan(const fl_ctx* ctx) { return ctx ? (ctx->ntt_plan ? ctx->ntt_plan : fl::default_plan_r1(ctx->logN)) : 0; }
+
+int fl_ctx_set_tc_tile(fl_ctx* ctx, int groups) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (groups != 0 && groups != 4 && groups != 8 && groups != 16)
+    return fail(FL_ERR_ARG, "tensor-core tile of %d slot groups (4, 8 or 16)", groups);
+  ctx->tc_tile = groups;
+  return FL_OK;
+}
+
+int fl_ctx_get_tc_tile(const fl_ctx* ctx) { return ctx ? (ctx->tc_tile ? ctx->tc_tile : 16) : 0; }
 
 int fl_he_conv2d_stack(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, void* workspace_dev,
                        size_t workspace_bytes, void* stream) {
@@ -905,7 +931,7 @@ int fl_ntt_forward(fl_ctx* ctx, int n, uint32_t* data_dev, void* stream) {
   if ((rc = check_ptrs({data_dev})) || (rc = rows_ok((long long)n * ctx->L, "ntt"))) return rc;
   const int rows = n * ctx->L;
   return launched(fl::launch_ntt_fwd(ctx->logN, rows, data_dev, rows, 0, data_dev, rows, 0, 1, ctx->tw, ctx->cc,
-                                     (cudaStream_t)stream),
+                                     (cudaStream_t)stream, ctx->ntt_plan),
                   "ntt");
 }
 

@@ -227,6 +227,13 @@ template <> struct Plan<11> { static constexpr int R1 = 3, R2 = 3; };
 template <> struct Plan<12> { static constexpr int R1 = 4, R2 = 3; };
 template <> struct Plan<13> { static constexpr int R1 = 4, R2 = 4; };
 template <> struct Plan<14> { static constexpr int R1 = 5, R2 = 4; };
+// Other pass plans of the same transform: the first row-strided pass is
+// radix 2^R1, the second 2^(LOGN - 5 - R1), the last radix 32; each row pass
+// needs 3 <= R <= 5.  The result is the same canonical transform for every
+// plan, so a caller may pick any valid plan (autotuned per workload).
+__host__ __device__ constexpr bool plan_ok(int logn, int r1) {
+  return r1 >= 3 && r1 <= 5 && logn - 5 - r1 >= 3 && logn - 5 - r1 <= 5;
+}
 
 // Resident CTAs per SM the register budget (64 per thread) is sized for:
 // 1024 threads per SM.  Kernels on two polynomials run 2 * N/32 threads (one
@@ -374,11 +381,12 @@ __device__ __forceinline__ void pass32(uint32_t* v, const uint4* __restrict__ tg
 // Full forward NTT of one polynomial by T = N/32 threads: global `src` ->
 // shared `s`, result in shared memory reduced to [0, q).  Caller syncs
 // before reading `s`.  tw_l: the limb's tables (TwLayout words).
-template <int LOGN>
+template <int LOGN, int R1 = Plan<LOGN>::R1>
 __device__ __forceinline__ void ntt_forward_to_smem(uint32_t* s, const uint32_t* __restrict__ src,
                                                     const uint32_t* __restrict__ tw_l,
                                                     const LimbConst& lc, int tid) {
-  constexpr int N = 1 << LOGN, T = N / 32, R1 = Plan<LOGN>::R1, R2 = Plan<LOGN>::R2;
+  constexpr int N = 1 << LOGN, T = N / 32, R2 = LOGN - 5 - R1;
+  static_assert(plan_ok(LOGN, R1), "pass plan");
   const uint2* f = reinterpret_cast<const uint2*>(tw_l) + TW_FWD * N;
   const uint4* tg = reinterpret_cast<const uint4*>(tw_l + TwLayout<LOGN>::PAIRS_WORDS) + TW_FWD * 16 * T;
   fwd_pass<LOGN, T, 0, R1, true>(s, src, f, lc.q, lc.two_q, tid);
@@ -401,10 +409,11 @@ __device__ __forceinline__ void ntt_forward_to_smem(uint32_t* s, const uint32_t*
 // `epi(value_in_[0,2q), u)`.  `bar()` synchronises every thread that takes
 // part (several polynomials may be transformed side by side by disjoint
 // thread groups sharing one barrier).
-template <int LOGN, class Epi, class Bar, bool SCALE = true>
+template <int LOGN, class Epi, class Bar, bool SCALE = true, int R1 = Plan<LOGN>::R1>
 __device__ __forceinline__ void intt_from_smem_bar(uint32_t* s, const uint32_t* __restrict__ tw_l,
                                                    const LimbConst& lc, int tid, Epi epi, Bar bar) {
-  constexpr int N = 1 << LOGN, T = N / 32, R1 = Plan<LOGN>::R1, R2 = Plan<LOGN>::R2;
+  constexpr int N = 1 << LOGN, T = N / 32, R2 = LOGN - 5 - R1;
+  static_assert(plan_ok(LOGN, R1), "pass plan");
   const uint2* f = reinterpret_cast<const uint2*>(tw_l) + TW_INV * N;
   const uint4* tg = reinterpret_cast<const uint4*>(tw_l + TwLayout<LOGN>::PAIRS_WORDS) + TW_INV * 16 * T;
   {
@@ -428,11 +437,11 @@ __device__ __forceinline__ void intt_from_smem(uint32_t* s, const uint32_t* __re
 }
 
 // N times the inverse transform, for inputs that already carry N^-1.
-template <int LOGN, class Epi>
+template <int LOGN, class Epi, int R1 = Plan<LOGN>::R1>
 __device__ __forceinline__ void intt_from_smem_unscaled(uint32_t* s, const uint32_t* __restrict__ tw_l,
                                                         const LimbConst& lc, int tid, Epi epi) {
   auto bar = [] { __syncthreads(); };
-  intt_from_smem_bar<LOGN, Epi, decltype(bar), false>(s, tw_l, lc, tid, epi, bar);
+  intt_from_smem_bar<LOGN, Epi, decltype(bar), false, R1>(s, tw_l, lc, tid, epi, bar);
 }
 
 }  // namespace fl

@@ -24,7 +24,7 @@ namespace fl {
 // src + ((r / src_per) * src_stride + r % src_per) * N (same for dst), and
 // uses limb (r / limb_div) % L.
 // --------------------------------------------------------------------------
-template <int LOGN>
+template <int LOGN, int R1 = Plan<LOGN>::R1>
 __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
     k_ntt_fwd(const uint32_t* __restrict__ src, int src_per, int src_stride, uint32_t* dst,
               int dst_per, int dst_stride, int limb_div, const uint32_t* __restrict__ tw,
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
   const LimbConst lc = cc.limb[l];
   const uint32_t* x = src + ((size_t)(r / src_per) * src_stride + r % src_per) * N;
   uint32_t* y = dst + ((size_t)(r / dst_per) * dst_stride + r % dst_per) * N;
-  ntt_forward_to_smem<LOGN>(sm, x, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, tid);
+  ntt_forward_to_smem<LOGN, R1>(sm, x, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, tid);
   __syncthreads();
   for (int v = tid; v < N / 4; v += T) {
     const uint4 o = *reinterpret_cast<const uint4*>(sm + pad(4 * v));  // 4 slots of one row
@@ -415,6 +415,11 @@ static cudaError_t setup_smem() {
   constexpr int SW = Geo<LOGN>::SMEM_WORDS;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_ntt_fwd<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4))) return e;
+  for (int r1 = 3; r1 <= 5; ++r1) {  // the other instantiated pass plans
+    if (r1 == Plan<LOGN>::R1 || !plan_available(LOGN, r1)) continue;
+    FL_PLAN_DISPATCH(LOGN, r1, (e = cudaFuncSetAttribute(k_ntt_fwd<LG, R1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4)));
+    if (e) return e;
+  }
   if ((e = cudaFuncSetAttribute(k_ntt_inv<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SW * 4))) return e;
   if ((e = cudaFuncSetAttribute(k_conv_intt<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SW * 4))) return e;
   if ((e = cudaFuncSetAttribute(k_conv_intt<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SW * 4))) return e;
@@ -454,12 +459,12 @@ cudaError_t launch_setup(int logn) {
 
 cudaError_t launch_ntt_fwd(int logn, int rows, const uint32_t* src, int src_per, int src_stride,
                            uint32_t* dst, int dst_per, int dst_stride, int limb_div,
-                           const uint32_t* tw, const CtxConst& cc, cudaStream_t st) {
+                           const uint32_t* tw, const CtxConst& cc, cudaStream_t st, int r1) {
   if (rows == 0) return cudaSuccess;
   const int N = 1 << logn;
   const size_t smem = (size_t)padded_words(N) * 4;
-  FL_DISPATCH(logn, (k_ntt_fwd<LG><<<rows, N / 32, smem, st>>>(src, src_per, src_stride, dst, dst_per,
-                                                                dst_stride, limb_div, tw, cc)));
+  FL_PLAN_DISPATCH(logn, r1, (k_ntt_fwd<LG, R1><<<rows, N / 32, smem, st>>>(src, src_per, src_stride, dst, dst_per,
+                                                                            dst_stride, limb_div, tw, cc)));
   return cudaGetLastError();
 }
 

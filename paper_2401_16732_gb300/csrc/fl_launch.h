@@ -85,6 +85,34 @@ struct NttSegs {  // forward NTT of several contiguous row ranges in one launch
   int n;
 };
 
+#ifdef __CUDACC__
+// Dispatch over the instantiated (ring degree, pass plan) pairs: CALL sees
+// constexpr LG (log2 N) and R1 (first row pass radix 2^R1).  r1 = 0 picks
+// the default plan; an invalid pair returns cudaErrorInvalidValue.
+#define FL_PLAN_DISPATCH(logn, r1, CALL)                                              \
+  do {                                                                                \
+    const int r1_ = (r1) ? (r1) : default_plan_r1(logn);                              \
+    switch ((logn) * 8 + r1_) {                                                       \
+      case 11 * 8 + 3: { constexpr int LG = 11, R1 = 3; CALL; break; }              \
+      case 12 * 8 + 3: { constexpr int LG = 12, R1 = 3; CALL; break; }              \
+      case 12 * 8 + 4: { constexpr int LG = 12, R1 = 4; CALL; break; }              \
+      case 13 * 8 + 3: { constexpr int LG = 13, R1 = 3; CALL; break; }              \
+      case 13 * 8 + 4: { constexpr int LG = 13, R1 = 4; CALL; break; }              \
+      case 13 * 8 + 5: { constexpr int LG = 13, R1 = 5; CALL; break; }              \
+      case 14 * 8 + 4: { constexpr int LG = 14, R1 = 4; CALL; break; }              \
+      case 14 * 8 + 5: { constexpr int LG = 14, R1 = 5; CALL; break; }              \
+      default: return cudaErrorInvalidValue;                                          \
+    }                                                                                 \
+  } while (0)
+#endif
+// the default first-pass radix of each ring degree, and whether (logn, r1)
+// is an instantiated plan
+inline int default_plan_r1(int logn) { return logn == 11 ? 3 : logn == 14 ? 5 : 4; }
+inline bool plan_available(int logn, int r1) {
+  return r1 == 0 || (logn == 11 && r1 == 3) || (logn == 12 && (r1 == 3 || r1 == 4)) ||
+         (logn == 13 && r1 >= 3 && r1 <= 5) || (logn == 14 && (r1 == 4 || r1 == 5));
+}
+
 cudaError_t launch_setup(int logn);
 cudaError_t launch_stack_setup(int logn);
 cudaError_t launch_wait_timeout_probe(unsigned long long* err, cudaStream_t st);
@@ -93,11 +121,11 @@ int stack_ctas_per_sm(int logn);
 cudaError_t launch_stack(int logn, const StackArgs& a, unsigned long long* ctl, const uint32_t* tw,
                          const CtxConst& cc, int sms, cudaStream_t st);
 cudaError_t launch_ntt_multi(int logn, const NttSegs& segs, const uint32_t* tw, const CtxConst& cc,
-                             cudaStream_t st);
+                             cudaStream_t st, int r1 = 0);
 size_t twiddle_limb_words(int logn);
 cudaError_t launch_ntt_fwd(int logn, int rows, const uint32_t* src, int src_per, int src_stride,
                            uint32_t* dst, int dst_per, int dst_stride, int limb_div,
-                           const uint32_t* tw, const CtxConst& cc, cudaStream_t st);
+                           const uint32_t* tw, const CtxConst& cc, cudaStream_t st, int r1 = 0);
 cudaError_t launch_ntt_inv(int logn, int rows, uint32_t* data, const uint32_t* tw, const CtxConst& cc,
                            cudaStream_t st);
 cudaError_t launch_conv_queue(int logn, const StackArgs& a, unsigned long long* ctl, const uint32_t* tw,
@@ -139,10 +167,10 @@ cudaError_t launch_tc_setup(int logn);
 size_t conv_tc_smem_bytes();
 cudaError_t launch_tc_weights(const uint32_t* w_hat, uint32_t* w_tc, int L, int Cout, int G, int N, cudaStream_t st);
 cudaError_t launch_tc_inputs(const uint32_t* c_hat, uint32_t* c_tc, int B, int n_in, int L, int N, cudaStream_t st);
-cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_hat, const uint32_t* c_hat, uint32_t* y_hat,
-                           int N, const CtxConst& cc, unsigned long long* err, cudaStream_t st, bool pdl);
+cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_tc, const uint32_t* c_hat, uint32_t* y_hat,
+                           int N, const CtxConst& cc, unsigned long long* err, cudaStream_t st, bool pdl, int gpc = 0);
 cudaError_t launch_intt_mask_rows(int logn, long long rows, uint32_t* y, const uint32_t* r, const uint32_t* tw,
-                                  const CtxConst& cc, cudaStream_t st, bool pdl);
+                                  const CtxConst& cc, cudaStream_t st, bool pdl, int r1 = 0);
 // direct form (fl_direct.cu)
 cudaError_t launch_direct_setup(int logn);
 cudaError_t launch_direct(int logn, int B, const GeomDims& g, const int8_t* w, const uint32_t* ct, uint32_t* out,

@@ -456,7 +456,7 @@ cudaError_t launch_stack(int logn, const StackArgs& a, unsigned long long* ctl, 
 // of a stack).  Segment s covers rows [row_begin[s], row_begin[s+1]) of the
 // grid, reading contiguous rows [..][L][N] from src[s] into dst[s].
 // ---------------------------------------------------------------------------
-template <int LOGN>
+template <int LOGN, int R1 = Plan<LOGN>::R1>
 __global__ void __launch_bounds__((1 << LOGN) / 32, 1024 >> (LOGN - 5))
     k_ntt_fwd_multi(NttSegs segs, const uint32_t* __restrict__ tw, CtxConst cc) {
   constexpr int N = 1 << LOGN, T = N / 32;
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, 1024 >> (LOGN - 5))
   const LimbConst lc = cc.limb[l];
   const uint32_t* x = segs.src[s] + (size_t)lr * N;
   uint32_t* y = segs.dst[s] + (size_t)lr * N;
-  ntt_forward_to_smem<LOGN>(sm, x, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, tid);
+  ntt_forward_to_smem<LOGN, R1>(sm, x, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, tid);
   __syncthreads();
   for (int v = tid; v < N / 4; v += T) {
     const uint4 o = *reinterpret_cast<const uint4*>(sm + pad(4 * v));  // 4 slots of one row
@@ -480,8 +480,15 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, 1024 >> (LOGN - 5))
 
 template <int LOGN>
 static cudaError_t multi_setup() {
-  return cudaFuncSetAttribute(k_ntt_fwd_multi<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              Geo<LOGN>::SMEM_WORDS * 4);
+  cudaError_t e = cudaSuccess;
+  for (int r1 = 3; r1 <= 5; ++r1) {  // every instantiated pass plan
+    if (!plan_available(LOGN, r1)) continue;
+    FL_PLAN_DISPATCH(LOGN, r1, (e = cudaFuncSetAttribute(k_ntt_fwd_multi<LG, R1>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         Geo<LG>::SMEM_WORDS * 4)));
+    if (e) return e;
+  }
+  return e;
 }
 
 cudaError_t launch_ntt_multi_setup(int logn) {
@@ -495,18 +502,12 @@ cudaError_t launch_ntt_multi_setup(int logn) {
 }
 
 cudaError_t launch_ntt_multi(int logn, const NttSegs& segs, const uint32_t* tw, const CtxConst& cc,
-                             cudaStream_t st) {
+                             cudaStream_t st, int r1) {
   const int rows = segs.row_begin[segs.n];
   if (rows == 0) return cudaSuccess;
   const int N = 1 << logn;
   const size_t smem = (size_t)padded_words(N) * 4;
-  switch (logn) {
-    case 11: k_ntt_fwd_multi<11><<<rows, N / 32, smem, st>>>(segs, tw, cc); break;
-    case 12: k_ntt_fwd_multi<12><<<rows, N / 32, smem, st>>>(segs, tw, cc); break;
-    case 13: k_ntt_fwd_multi<13><<<rows, N / 32, smem, st>>>(segs, tw, cc); break;
-    case 14: k_ntt_fwd_multi<14><<<rows, N / 32, smem, st>>>(segs, tw, cc); break;
-    default: return cudaErrorInvalidValue;
-  }
+  FL_PLAN_DISPATCH(logn, r1, (k_ntt_fwd_multi<LG, R1><<<rows, N / 32, smem, st>>>(segs, tw, cc)));
   return cudaGetLastError();
 }
 

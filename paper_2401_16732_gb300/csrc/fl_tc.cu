@@ -55,12 +55,14 @@ constexpr int TC_PROD_WARPS = 8;      // cp.async + digit conversion into the ti
 constexpr int TC_EPI_WARPS = 8;       // recombination, two per tensor-memory lane quadrant
 constexpr int TC_NPROD = 32 * TC_PROD_WARPS;
 constexpr int TC_MMA_WARP = TC_PROD_WARPS + TC_EPI_WARPS;  // one more warp issues the MMAs
-constexpr int TC_THREADS = 32 * (TC_MMA_WARP + 1);          // 416
+constexpr int TC_THREADS = 32 * (TC_MMA_WARP + 1);          // 544
 constexpr int TC_RING = 6;            // raw-residue ring depth, in K steps
 constexpr int TC_NS = 4;              // fp16 tile stages
-constexpr int TC_GPC = 16;            // slot groups per CTA: 64 slots, 256 bytes of every input row
+// slot groups per CTA (the tile's length along the slots): 4, 8 or 16, a
+// template parameter of k_conv_tc chosen per workload (even: the epilogue
+// stores groups in pairs)
+constexpr int TC_GPC_DEFAULT = 16;
 constexpr int TC_TMEM_COLS = 2 * TC_U * TC_NN;  // 512: two accumulator buffers
-static_assert(TC_GPC % 2 == 0, "the epilogue stores groups in pairs");
 // shared-memory layout (bytes)
 constexpr int RAWA_STEP = TC_GS * TC_M * 16;       // [g][row][4 slots]
 constexpr int RAWB_STEP = TC_CW * TC_GS * 16;      // [image/band][g][component][4 slots]
@@ -214,9 +216,9 @@ __device__ __forceinline__ uint32_t recombine(const uint32_t* b, float qinv, uin
 }
 }  // namespace
 
-// Grid (mtiles * nchunks, N / (4 * TC_GPC), L): blockIdx.x picks the 128
+// Grid (mtiles * nchunks, N / (4 * GPC), L): blockIdx.x picks the 128
 // output channels and 16 columns (fastest, so CTAs sharing input slots run
-// together), blockIdx.y the run of TC_GPC groups of 4 slots, blockIdx.z the
+// together), blockIdx.y the run of GPC groups of 4 slots, blockIdx.z the
 // limb.  Step t of the CTA is (group t / nch, K step t % nch) with nch =
 // G / 4 + 1 K steps per group, the last of which carries the bias column.
 // Warp roles (every hand-off an mbarrier with a bounded wait):
@@ -225,6 +227,7 @@ __device__ __forceinline__ uint32_t recombine(const uint32_t* b, float qinv, uin
 //                        commit to tile_empty (and to acc_full after a group)
 //   epilogue (4 warps)   acc_full -> tensor-memory loads -> arrive acc_empty ->
 //                        recombination -> stores of the NTT-domain outputs
+template <int GPC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_conv_tc(const uint32_t* __restrict__ w_tc, const uint32_t* __restrict__ c_hat, uint32_t* __restrict__ y_hat,
               ConvDims cd, int B, int N, CtxConst cc, unsigned long long* err) {
@@ -236,10 +239,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cols = 2 * B * cd.bands, mtiles = (cd.Cout + TC_M - 1) / TC_M;
   const int i0 = (blockIdx.x % mtiles) * TC_M, col0 = (blockIdx.x / mtiles) * TC_CW;
-  const int l = blockIdx.z, grp0 = blockIdx.y * TC_GPC, L = cc.L, G = cd.G;
+  static_assert(GPC % 2 == 0, "the epilogue stores groups in pairs");
+  const int l = blockIdx.z, grp0 = blockIdx.y * GPC, L = cc.L, G = cd.G;
   const LimbConst lc = cc.limb[l];
   const size_t NL = (size_t)L * N, rowstride = (size_t)cd.bands * 2 * NL;
-  const int nch = G / TC_GS + 1, T = TC_GPC * nch;
+  const int nch = G / TC_GS + 1, T = GPC * nch;
   const uint32_t sb = su32(tsm);
 
   if (warp == 0) tmem_alloc(&tmem_base, TC_TMEM_COLS);
@@ -420,7 +424,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr int HS = 32 * TC_EPI_WARPS;  // hold[local column][slot][epilogue thread]
     uint32_t* hold = reinterpret_cast<uint32_t*>(tsm + OFF_HOLD) + (tid - 32 * TC_PROD_WARPS);
 #pragma unroll 1
-    for (int grp = 0; grp < TC_GPC; ++grp) {
+    for (int grp = 0; grp < GPC; ++grp) {
       const int ab = grp & 1, u0 = 4 * (grp0 + grp);
       if (!mbar_wait_bounded(&acc_full[ab], (grp >> 1) & 1)) {
         s_abort = 1;
@@ -472,7 +476,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // N times its inverse transform, + Delta_l * r[oct] when c == 0 and r is set.
 // Launched after the contraction as a programmatic dependent: it waits for
 // the contraction before its first read.
-template <int LOGN>
+template <int LOGN, int R1 = Plan<LOGN>::R1>
 __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
     k_intt_mask_rows(uint32_t* __restrict__ y, const uint32_t* __restrict__ r, const uint32_t* __restrict__ tw,
                      CtxConst cc) {
@@ -488,7 +492,7 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
   for (int v = threadIdx.x; v < N / 4; v += T)
     *reinterpret_cast<uint4*>(sm + pad(4 * v)) = reinterpret_cast<const uint4*>(p)[v];
   __syncthreads();  // the whole row is in shared memory before any of it is overwritten
-  intt_from_smem_unscaled<LOGN>(sm, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, threadIdx.x,
+  intt_from_smem_unscaled<LOGN, MaskStore, R1>(sm, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, threadIdx.x,
                                 MaskStore{p, (r && c == 0) ? r + oct * N : nullptr, lc});
 }
 
@@ -569,27 +573,44 @@ static cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, size_t smem, cudaStr
 }
 
 // pdl: the previous operation in `st` is the forward NTT of these inputs.
-cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_hat, const uint32_t* c_hat, uint32_t* y_hat,
-                           int N, const CtxConst& cc, unsigned long long* err, cudaStream_t st, bool pdl) {
+// gpc: slot groups per CTA (4, 8 or 16; 0 = the default).
+cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_tc, const uint32_t* c_hat, uint32_t* y_hat,
+                           int N, const CtxConst& cc, unsigned long long* err, cudaStream_t st, bool pdl, int gpc) {
   if (B == 0 || cd.Cout == 0) return cudaSuccess;
   if (cd.G < 1 || cd.G > kTcMaxG) return cudaErrorInvalidValue;
+  if (gpc == 0) gpc = TC_GPC_DEFAULT;
+  if (gpc != 4 && gpc != 8 && gpc != 16) return cudaErrorInvalidValue;
   const long long mtiles = (cd.Cout + TC_M - 1) / TC_M, nchunks = (2LL * B * cd.bands + TC_CW - 1) / TC_CW;
-  if (mtiles * nchunks > 0x7fffffffLL || N % (4 * TC_GPC) != 0) return cudaErrorInvalidConfiguration;
+  if (mtiles * nchunks > 0x7fffffffLL || N % (4 * gpc) != 0) return cudaErrorInvalidConfiguration;
   cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)(mtiles * nchunks), N / (4 * TC_GPC), cc.L), dim3(TC_THREADS),
+  cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)(mtiles * nchunks), N / (4 * gpc), cc.L), dim3(TC_THREADS),
                                       TC_SMEM, st, at, pdl);
-  return cudaLaunchKernelEx(&cfg, k_conv_tc, w_hat, c_hat, y_hat, cd, B, N, cc, err);
+  switch (gpc) {
+    case 4: return cudaLaunchKernelEx(&cfg, k_conv_tc<4>, w_tc, c_hat, y_hat, cd, B, N, cc, err);
+    case 8: return cudaLaunchKernelEx(&cfg, k_conv_tc<8>, w_tc, c_hat, y_hat, cd, B, N, cc, err);
+    default: return cudaLaunchKernelEx(&cfg, k_conv_tc<16>, w_tc, c_hat, y_hat, cd, B, N, cc, err);
+  }
 }
 
 template <int LOGN>
 static cudaError_t intt_rows_setup() {
-  return cudaFuncSetAttribute(k_intt_mask_rows<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              padded_words(1 << LOGN) * 4);
+  cudaError_t e = cudaSuccess;
+  for (int r1 = 3; r1 <= 5; ++r1) {  // every instantiated pass plan
+    if (!plan_available(LOGN, r1)) continue;
+    FL_PLAN_DISPATCH(LOGN, r1, (e = cudaFuncSetAttribute(k_intt_mask_rows<LG, R1>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         padded_words(1 << LG) * 4)));
+    if (e) return e;
+  }
+  return e;
 }
 
 cudaError_t launch_tc_setup(int logn) {
-  cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_conv_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)) ||
+      (e = cudaFuncSetAttribute(k_conv_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)) ||
+      (e = cudaFuncSetAttribute(k_conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)))
+    return e;
   switch (logn) {
     case 11: return intt_rows_setup<11>();
     case 12: return intt_rows_setup<12>();
@@ -599,27 +620,19 @@ cudaError_t launch_tc_setup(int logn) {
   return cudaErrorInvalidValue;
 }
 
-template <int LOGN>
-static cudaError_t intt_rows(long long rows, uint32_t* y, const uint32_t* r, const uint32_t* tw, const CtxConst& cc,
-                             cudaStream_t st, bool pdl) {
-  constexpr int N = 1 << LOGN;
-  cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)rows), dim3(N / 32), (size_t)padded_words(N) * 4, st, at, pdl);
-  return cudaLaunchKernelEx(&cfg, k_intt_mask_rows<LOGN>, y, r, tw, cc);
-}
-
 // pdl: the previous operation in `st` is the contraction that wrote y.
 cudaError_t launch_intt_mask_rows(int logn, long long rows, uint32_t* y, const uint32_t* r, const uint32_t* tw,
-                                  const CtxConst& cc, cudaStream_t st, bool pdl) {
+                                  const CtxConst& cc, cudaStream_t st, bool pdl, int r1) {
   if (rows == 0) return cudaSuccess;
   if (rows > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  switch (logn) {
-    case 11: return intt_rows<11>(rows, y, r, tw, cc, st, pdl);
-    case 12: return intt_rows<12>(rows, y, r, tw, cc, st, pdl);
-    case 13: return intt_rows<13>(rows, y, r, tw, cc, st, pdl);
-    case 14: return intt_rows<14>(rows, y, r, tw, cc, st, pdl);
-  }
-  return cudaErrorInvalidValue;
+  cudaLaunchAttribute at[1];
+  cudaError_t e = cudaSuccess;
+  FL_PLAN_DISPATCH(logn, r1, {
+    cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)rows), dim3((1 << LG) / 32),
+                                        (size_t)padded_words(1 << LG) * 4, st, at, pdl);
+    e = cudaLaunchKernelEx(&cfg, k_intt_mask_rows<LG, R1>, y, r, tw, cc);
+  });
+  return e;
 }
 
 }  // namespace fl

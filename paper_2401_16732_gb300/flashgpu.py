@@ -27,6 +27,8 @@ FL_OK, FL_ERR_ARG, FL_ERR_SHAPE, FL_ERR_CUDA, FL_ERR_OOM, FL_ERR_TIMEOUT = 0, -1
 FL_STACK_PER_LAYER, FL_STACK_PERSISTENT, FL_STACK_QUEUE = 0, 1, 2
 FL_NOALLOC_SCRATCH_BYTES = 16 << 20
 FL_TC_MAX_G = 64
+NTT_PLANS = {11: (3,), 12: (3, 4), 13: (3, 4, 5), 14: (4, 5)}  # available first-pass radix exponents
+TC_TILES = (4, 8, 16)
 FL_STACK_MAX_LAYERS = 64
 
 
@@ -65,6 +67,10 @@ _SIGS = {
     "fl_mask_to_share": ([_vp, _i, _vp, _vp, _vp], _i),
     "fl_he_conv2d_direct": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "fl_he_conv2d_tc": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "fl_ctx_set_ntt_plan": ([_vp, _i], _i),
+    "fl_ctx_get_ntt_plan": ([_vp], _i),
+    "fl_ctx_set_tc_tile": ([_vp, _i], _i),
+    "fl_ctx_get_tc_tile": ([_vp], _i),
     "fl_tc_weights": ([_vp, _gp, _vp, _vp, _vp], _i),
     "fl_he_conv2d_tc_workspace_bytes": ([_vp, _gp, _i], _sz),
     "fl_he_conv2d_tc_from_ntt": ([_vp, _gp, _i, _vp, _vp, _sz, _vp, _vp], _i),
@@ -303,6 +309,25 @@ class Context:
     @stack_kernel.setter
     def stack_kernel(self, k: int):
         _check(_lib.fl_ctx_set_stack_kernel(self.h, k))
+
+    @property
+    def ntt_plan(self) -> int:
+        """First row-pass radix exponent r1 of the input NTT and the
+        inverse-NTT-rows kernel (fl_ctx_set_ntt_plan); 0 sets the default."""
+        return _lib.fl_ctx_get_ntt_plan(self.h)
+
+    @ntt_plan.setter
+    def ntt_plan(self, r1: int):
+        _check(_lib.fl_ctx_set_ntt_plan(self.h, r1))
+
+    @property
+    def tc_tile(self) -> int:
+        """Slot groups of 4 per CTA of the tensor-core contraction (4, 8, 16)."""
+        return _lib.fl_ctx_get_tc_tile(self.h)
+
+    @tc_tile.setter
+    def tc_tile(self, groups: int):
+        _check(_lib.fl_ctx_set_tc_tile(self.h, groups))
 
     def stack_error(self, workspace, stream=None) -> int:
         v = ctypes.c_uint64()
