@@ -409,9 +409,14 @@ __device__ __forceinline__ void ntt_forward_to_smem(uint32_t* s, const uint32_t*
 // `epi(value_in_[0,2q), u)`.  `bar()` synchronises every thread that takes
 // part (several polynomials may be transformed side by side by disjoint
 // thread groups sharing one barrier).
+// gsrc: when not null, the first pass reads the thread's 32 coefficients
+// straight from this global row (natural order) instead of from `s`; every
+// such read happens before the first barrier, so the epilogue may write the
+// result over gsrc in place.
 template <int LOGN, class Epi, class Bar, bool SCALE = true, int R1 = Plan<LOGN>::R1>
 __device__ __forceinline__ void intt_from_smem_bar(uint32_t* s, const uint32_t* __restrict__ tw_l,
-                                                   const LimbConst& lc, int tid, Epi epi, Bar bar) {
+                                                   const LimbConst& lc, int tid, Epi epi, Bar bar,
+                                                   const uint32_t* gsrc = nullptr) {
   constexpr int N = 1 << LOGN, T = N / 32, R2 = LOGN - 5 - R1;
   static_assert(plan_ok(LOGN, R1), "pass plan");
   const uint2* f = reinterpret_cast<const uint2*>(tw_l) + TW_INV * N;
@@ -419,7 +424,15 @@ __device__ __forceinline__ void intt_from_smem_bar(uint32_t* s, const uint32_t* 
   {
     uint32_t v[32];
     uint32_t* p = s + tid * ROW;
-    lds_row(p, v);
+    if (gsrc) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint4 x = reinterpret_cast<const uint4*>(gsrc + 32 * tid)[j];
+        v[4 * j] = x.x, v[4 * j + 1] = x.y, v[4 * j + 2] = x.z, v[4 * j + 3] = x.w;
+      }
+    } else {
+      lds_row(p, v);
+    }
     pass32<true>(v, tg, T, tid, lc.q, lc.two_q);
     sts_row(p, v);
   }
@@ -439,9 +452,10 @@ __device__ __forceinline__ void intt_from_smem(uint32_t* s, const uint32_t* __re
 // N times the inverse transform, for inputs that already carry N^-1.
 template <int LOGN, class Epi, int R1 = Plan<LOGN>::R1>
 __device__ __forceinline__ void intt_from_smem_unscaled(uint32_t* s, const uint32_t* __restrict__ tw_l,
-                                                        const LimbConst& lc, int tid, Epi epi) {
+                                                        const LimbConst& lc, int tid, Epi epi,
+                                                        const uint32_t* gsrc = nullptr) {
   auto bar = [] { __syncthreads(); };
-  intt_from_smem_bar<LOGN, Epi, decltype(bar), false, R1>(s, tw_l, lc, tid, epi, bar);
+  intt_from_smem_bar<LOGN, Epi, decltype(bar), false, R1>(s, tw_l, lc, tid, epi, bar, gsrc);
 }
 
 }  // namespace fl

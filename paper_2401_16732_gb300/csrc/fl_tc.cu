@@ -480,7 +480,7 @@ template <int LOGN, int R1 = Plan<LOGN>::R1>
 __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
     k_intt_mask_rows(uint32_t* __restrict__ y, const uint32_t* __restrict__ r, const uint32_t* __restrict__ tw,
                      CtxConst cc) {
-  constexpr int N = 1 << LOGN, T = N / 32;
+  constexpr int N = 1 << LOGN;
   extern __shared__ uint32_t sm[];
   const int L = cc.L;
   const size_t row = blockIdx.x;
@@ -489,11 +489,10 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
   const LimbConst lc = cc.limb[l];
   uint32_t* p = y + row * N;
   pdl_wait();
-  for (int v = threadIdx.x; v < N / 4; v += T)
-    *reinterpret_cast<uint4*>(sm + pad(4 * v)) = reinterpret_cast<const uint4*>(p)[v];
-  __syncthreads();  // the whole row is in shared memory before any of it is overwritten
+  // the first (radix-32) pass reads its coefficients from the row itself;
+  // every read precedes the first barrier, so the result may overwrite it
   intt_from_smem_unscaled<LOGN, MaskStore, R1>(sm, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, threadIdx.x,
-                                MaskStore{p, (r && c == 0) ? r + oct * N : nullptr, lc});
+                                               MaskStore{p, (r && c == 0) ? r + oct * N : nullptr, lc}, p);
 }
 
 // Slot-tiled copy of the encoded weights for k_conv_tc: w_tc[l][u / 8][g][h][i][j]
