@@ -36,7 +36,29 @@ L2_BYTES = 129e6
 # with Shoup multiplication needs 4 ALU-pipe operations (sum, conditional
 # subtract as add + min, difference) and 3 multiplies; the ALU pipe retires 16
 # lanes per clock per SM sub-partition.  152 SMs x 4 x 16 x 2.07 GHz / 4.
-ALU_BFLY_PEAK = 152 * 4 * 16 * 2.07e9 / 4
+ALU_BFLY_DERIVED = 152 * 4 * 16 * 2.07e9 / 4
+_ALU = {}
+
+
+def alu_peak():
+    """(butterflies/s, source): the lazy Gentleman-Sande butterfly rate
+    measured on this GPU by the roofline-ceiling library (libflpeaks, once
+    per process), else the derived figure above."""
+    if "v" not in _ALU:
+        import ctypes
+        try:
+            lib = ctypes.CDLL(os.path.join(ROOT, "paper_2401_16732_gb300", "libflpeaks.so"))
+            lib.fl_measure_butterfly_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+            v = ctypes.c_double()
+            if lib.fl_measure_butterfly_rate(20000, ctypes.byref(v)) != 0 or v.value <= 0:
+                raise RuntimeError("measurement failed")
+            _ALU["v"] = (v.value, "measured: lazy Gentleman-Sande butterflies from registers on every SM "
+                                   "(libflpeaks fl_measure_butterfly_rate), "
+                                   f"derived pipe bound {ALU_BFLY_DERIVED / 1e12:.2f} T/s")
+        except Exception as exc:  # the figure is reported with its source either way
+            _ALU["v"] = (ALU_BFLY_DERIVED, f"derived: 152 SMs x 4 x 16 ALU lanes x 2.07 GHz / 4 ALU ops per "
+                                           f"butterfly (measurement unavailable: {exc})")
+    return _ALU["v"]
 # Direct form: one signed 32x32->64-bit multiply-add per lane per clock on the
 # 16-lane integer multiply pipe (an upper bound).
 DIRECT_MAC_PEAK = 152 * 4 * 16 * 2.07e9
@@ -675,7 +697,8 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
     # ---- end to end: pinned host inputs -> device -> path -> host outputs ----
     e2e = e2e_switched = None
     if not args.skip_e2e:
-        # Every step copies every layer's input ciphertexts in from pinned
+        # The copies go through the library's C-ABI (fl_copy_to_device,
+        # fl_copy_to_host).  Every step copies every layer's input ciphertexts in from pinned
         # host memory and every layer's output ciphertexts back out (one
         # reused host buffer per direction, sized for the largest layer; the
         # bytes moved are those of the whole step).  When a second set of
@@ -730,7 +753,7 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
                 di = k % nb
                 with torch.cuda.stream(stream):
                     for lay in layers:
-                        lay["ct"].view(-1).copy_(h_in[:lay["ct"].numel()], non_blocking=True)
+                        ctx.copy_to_device(h_in[:lay["ct"].numel()], lay["ct"].view(-1), stream=stream)
                     if not L_out:
                         stream.wait_event(ev_done[di])  # this output set has drained
                     g_.replay()
@@ -742,7 +765,7 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
                 with torch.cuda.stream(copy_stream):
                     copy_stream.wait_event(ev_comp[di])
                     for o in (drain[di] if L_out else outs):
-                        h_out[:o.numel()].copy_(o.view(-1), non_blocking=True)
+                        ctx.copy_to_host(o.view(-1), h_out[:o.numel()], stream=copy_stream)
                     ev_done[di].record(copy_stream)
 
             for k in range(2):
@@ -757,7 +780,7 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
             rate, _ = whole_job_rate(B * len(layers) * n_e2e, time.perf_counter() - t0, dev)
             out_bytes = d2h if not L_out else d2h * L_out // L
             return {"value": rate, "unit": "layers/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": out_bytes,
-                    "steps": n_e2e, "pipelined": nb == 2}
+                    "steps": n_e2e, "pipelined": nb == 2, "copies": "fl_copy_to_device / fl_copy_to_host (C-ABI)"}
 
         e2e = run_e2e()
         if L > 2:
@@ -778,6 +801,7 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
     kern_s = kern["conv"] * 1e-3
     achieved = conv_bytes / kern_s / 1e9
     achieved_bfly = bfly / kern_s
+    ALU_BFLY_PEAK, alu_src = alu_peak()
     hbm_floor, alu_floor = conv_bytes / (hbm * 1e9), bfly / ALU_BFLY_PEAK
     value = world * B * len(layers) * args.steps / (ms * 1e-3)
     kname = {"persistent": "k_stack (persistent, warp-specialised, all layers)",
@@ -788,8 +812,7 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
                 "peak_source": peak_kind, "traffic": traffic,
                 "kernel_source_sha256_16": kernel_source_hash(tuned["kernel"])}
     alu_line = {"bound": "alu", "achieved": achieved_bfly / 1e12, "peak": ALU_BFLY_PEAK / 1e12,
-                "unit": "T butterflies/s", "frac": achieved_bfly / ALU_BFLY_PEAK,
-                "peak_source": "derived: 152 SMs x 4 x 16 ALU lanes x 2.07 GHz / 4 ALU ops per butterfly"}
+                "unit": "T butterflies/s", "frac": achieved_bfly / ALU_BFLY_PEAK, "peak_source": alu_src}
     main, other = (hbm_line, alu_line) if hbm_floor >= alu_floor else (alu_line, hbm_line)
     roof = dict(main)
     roof.update({"kernel": kname, "kernel_ms_per_step": kern["conv"], "algorithmic_bytes_per_step": conv_bytes,
@@ -815,8 +838,7 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
         rate = (bfly + wbfly) / kern_s
         obytes = sum(layer_bytes(g, B, L, N) - L * g.Cout * g.G * N * 4 + ntt_bytes(g, B, L, N) for g in geoms)
         roof = {"bound": "alu", "achieved": rate / 1e12, "peak": ALU_BFLY_PEAK / 1e12, "unit": "T butterflies/s",
-                "frac": rate / ALU_BFLY_PEAK, "traffic": None,
-                "peak_source": "derived: 152 SMs x 4 x 16 ALU lanes x 2.07 GHz / 4 ALU ops per butterfly",
+                "frac": rate / ALU_BFLY_PEAK, "traffic": None, "peak_source": alu_src,
                 "kernel": "k_ntt_fwd + k_conv_otf per layer: weight polynomials rebuilt and transformed in shared memory",
                 "kernel_ms_per_step": kern["conv"], "algorithmic_butterflies_per_step": bfly + wbfly,
                 "weight_ntt_butterflies_per_step": wbfly, "hbm_bytes_per_step": obytes,
@@ -1034,13 +1056,13 @@ def run_x2x(args, rank, world, local_rank):
             si = k % 2
             with torch.cuda.stream(stream):
                 for h, d in zip(h_in, (ct_z, ct_x, ct_y)):
-                    d.view(-1).copy_(h, non_blocking=True)
+                    ctx.copy_to_device(h, d.view(-1), stream=stream)
                 stream.wait_event(ev_done[si])
                 step(o1=o1s[si])
                 ev_comp[si].record(stream)
             with torch.cuda.stream(copy_stream):
                 copy_stream.wait_event(ev_comp[si])
-                h_out.copy_(o1s[si].view(-1), non_blocking=True)
+                ctx.copy_to_host(o1s[si].view(-1), h_out, stream=copy_stream)
                 ev_done[si].record(copy_stream)
 
         e2e_step(0)
@@ -1064,9 +1086,9 @@ def run_x2x(args, rank, world, local_rank):
     bytes2 = n * (6 * L + 1) * N * 4     # <X>, <Y>, r^2 - r + v in; result out
     alu1 = bfly1 / (k1 * 1e-3)
     hbm1, hbm2 = bytes1 / (k1 * 1e-3) / 1e9, bytes2 / (k2 * 1e-3) / 1e9
+    ALU_BFLY_PEAK, alu_src = alu_peak()
     roof = {"bound": "alu", "achieved": alu1 / 1e12, "peak": ALU_BFLY_PEAK / 1e12, "unit": "T butterflies/s",
-            "frac": alu1 / ALU_BFLY_PEAK,
-            "peak_source": "derived: 152 SMs x 4 x 16 ALU lanes x 2.07 GHz / 4 ALU ops per butterfly",
+            "frac": alu1 / ALU_BFLY_PEAK, "peak_source": alu_src,
             "traffic": traffic_of("x2x", "round1"),
             "kernel": "k_x2x_round1: forward NTT x2, NTT-domain PMult, inverse NTT x2, + encode(v)",
             "kernel_ms_per_step": k1, "algorithmic_butterflies_per_step": bfly1,

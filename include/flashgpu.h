@@ -118,6 +118,26 @@ size_t fl_decrypt_workspace_bytes(const fl_ctx *ctx, int n);
 int fl_decrypt(fl_ctx *ctx, const uint32_t *sk_dev, int n, const uint32_t *ct_dev,
                uint32_t *m_dev, void *workspace_dev, size_t workspace_bytes, void *stream);
 
+/* Test hook on the noise of decryption (Appendix A: c0 + c1*s = Delta*m + v
+ * mod q, decryption correct while the noise v stays small): for n
+ * ciphertexts ct_dev [n][2][L][N] under the key sk_dev and their expected
+ * messages m_dev uint32 [n][N] in [0, t), *max_noise_host receives the
+ * largest |v| over every coefficient, v taken centred in (-q/2, q/2] (a
+ * double: exact below 2^53).  workspace: fl_noise_workspace_bytes(ctx, n)
+ * device bytes.  Synchronises `stream`. */
+size_t fl_noise_workspace_bytes(const fl_ctx *ctx, int n);
+int fl_noise_inf(fl_ctx *ctx, const uint32_t *sk_dev, int n, const uint32_t *ct_dev, const uint32_t *m_dev,
+                 void *workspace_dev, size_t workspace_bytes, void *stream, double *max_noise_host);
+
+/* Ciphertext words between the caller's host buffer and device memory of
+ * the context's device (`words` 32-bit words, e.g. n*2*L*N for n
+ * ciphertexts): the client's side of the exchange (Sec. 5.2: the client
+ * sends encrypted inputs, the server returns masked ciphertexts).  Enqueued
+ * on `stream`; asynchronous when the host buffer is pinned.  FL_ERR_ARG
+ * when dev is not device memory of the context's device, or host is. */
+int fl_copy_to_device(fl_ctx *ctx, const uint32_t *host, uint32_t *dev, size_t words, void *stream);
+int fl_copy_to_host(fl_ctx *ctx, const uint32_t *dev, uint32_t *host, size_t words, void *stream);
+
 /* Read the convolution outputs out of decrypted output polynomials:
  * m_dev uint32 [B][n_out][N] -> y_dev int32 [B][Cout][Ho][Wo]. */
 int fl_extract_outputs(const fl_conv_geom *geom, int B, const uint32_t *m_dev,

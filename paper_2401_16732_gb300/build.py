@@ -14,6 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libflashgpu.so")
+PEAKS_LIB = os.path.join(PKG, "libflpeaks.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "--extended-lambda"]
@@ -56,5 +57,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+def build_peaks(force: bool = False) -> str:
+    """The roofline-ceiling measurements (csrc/peaks, libflpeaks.so) used by
+    the throughput measurements; not part of the convolution library."""
+    srcs = sorted(glob.glob(os.path.join(CSRC, "peaks", "*.cu")))
+    deps = srcs + [os.path.join(ROOT, "include", "flpeaks.h"), os.path.join(CSRC, "fl_device.cuh")]
+    if not force and os.path.exists(PEAKS_LIB):
+        t = os.path.getmtime(PEAKS_LIB)
+        if all(os.path.getmtime(d) <= t for d in deps):
+            return PEAKS_LIB
+    tmp = PEAKS_LIB + ".tmp"
+    subprocess.check_call([NVCC, *FLAGS, "-shared", "-o", tmp, *srcs])
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
+    print(build_peaks(force="--force" in sys.argv))

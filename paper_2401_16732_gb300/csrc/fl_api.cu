@@ -458,6 +458,78 @@ int fl_decrypt(fl_ctx* ctx, const uint32_t* sk_dev, int n, const uint32_t* ct_de
   return launched(fl::launch_dec_round(ws, m_dev, n, ctx->N, ctx->dc, st), "decrypt round");
 }
 
+size_t fl_noise_workspace_bytes(const fl_ctx* ctx, int n) { return fl_decrypt_workspace_bytes(ctx, n) + 256; }
+
+int fl_noise_inf(fl_ctx* ctx, const uint32_t* sk_dev, int n, const uint32_t* ct_dev, const uint32_t* m_dev,
+                 void* workspace_dev, size_t workspace_bytes, void* stream, double* max_noise_host) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (n < 0 || !max_noise_host) return fail(FL_ERR_ARG, "n=%d or null result pointer", n);
+  if (n == 0) {
+    *max_noise_host = 0.0;
+    return FL_OK;
+  }
+  if ((rc = check_ptrs({sk_dev, ct_dev, m_dev, workspace_dev})) || (rc = rows_ok((long long)n * 2 * ctx->L, "noise")))
+    return rc;
+  if (workspace_bytes < fl_noise_workspace_bytes(ctx, n))
+    return fail(FL_ERR_ARG, "workspace %zu bytes, need %zu", workspace_bytes, fl_noise_workspace_bytes(ctx, n));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = ctx->L;
+  uint32_t* ws = (uint32_t*)workspace_dev;
+  unsigned long long* word = (unsigned long long*)((char*)workspace_dev + fl_decrypt_workspace_bytes(ctx, n));
+  cudaError_t e = cudaMemsetAsync(word, 0, sizeof *word, st);
+  if (e != cudaSuccess) return cuda_fail(e, "noise word");
+  // the phase [c0 + c1 s]_{q_l} per limb, as in fl_decrypt
+  if ((rc = launched(fl::launch_ntt_fwd(ctx->logN, n * L, ct_dev + (size_t)L * ctx->N, L, 2 * L, ws, n * L, 0, 1,
+                                        ctx->tw, ctx->cc, st),
+                     "noise ntt")))
+    return rc;
+  GeomDims none;
+  memset(&none, 0, sizeof none);
+  if ((rc = launched(fl::launch_pmul_intt(ctx->logN, 0, n, ws, const_cast<uint32_t*>(ct_dev), sk_dev, nullptr,
+                                          nullptr, none, ctx->tw, ctx->cc, st),
+                     "noise phase")))
+    return rc;
+  if ((rc = launched(fl::launch_noise(ws, m_dev, n, ctx->N, ctx->dc, ctx->cc, word, st), "noise")))
+    return rc;
+  unsigned long long bits = 0;
+  if ((e = cudaMemcpyAsync(&bits, word, sizeof bits, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cuda_fail(e, "noise read");
+  memcpy(max_noise_host, &bits, sizeof bits);
+  return FL_OK;
+}
+
+// Host <-> device copies of ciphertext words through the library (the
+// caller's buffers; pinned host memory makes them asynchronous).
+static int copy_checks(fl_ctx* ctx, const void* host, const void* dev, size_t words) {
+  int rc;
+  if ((rc = check_ctx(ctx))) return rc;
+  if (words == 0) return FL_OK;
+  if (!host || !dev) return fail(FL_ERR_ARG, "null buffer");
+  cudaPointerAttributes ha{}, da{};
+  if (cudaPointerGetAttributes(&da, dev) != cudaSuccess || da.type != cudaMemoryTypeDevice || da.device != ctx->device)
+    return fail(FL_ERR_ARG, "the device buffer is not device memory of the context's device");
+  if (cudaPointerGetAttributes(&ha, host) == cudaSuccess && ha.type == cudaMemoryTypeDevice)
+    return fail(FL_ERR_ARG, "the host buffer is device memory");
+  cudaGetLastError();  // clear a lookup error left by pageable host memory
+  return FL_OK;
+}
+
+int fl_copy_to_device(fl_ctx* ctx, const uint32_t* host, uint32_t* dev, size_t words, void* stream) {
+  int rc;
+  if ((rc = copy_checks(ctx, host, dev, words)) || words == 0) return rc;
+  const cudaError_t e = cudaMemcpyAsync(dev, host, words * 4, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  return e == cudaSuccess ? FL_OK : cuda_fail(e, "copy to device");
+}
+
+int fl_copy_to_host(fl_ctx* ctx, const uint32_t* dev, uint32_t* host, size_t words, void* stream) {
+  int rc;
+  if ((rc = copy_checks(ctx, host, dev, words)) || words == 0) return rc;
+  const cudaError_t e = cudaMemcpyAsync(host, dev, words * 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  return e == cudaSuccess ? FL_OK : cuda_fail(e, "copy to host");
+}
+
 int fl_extract_outputs(const fl_conv_geom* geom, int B, const uint32_t* m_dev, int32_t* y_dev, void* stream) {
   if (!geom) return fail(FL_ERR_ARG, "null geometry");
   fl_conv_geom ref;

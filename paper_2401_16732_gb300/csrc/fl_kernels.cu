@@ -304,6 +304,34 @@ __global__ void k_dec_round(const uint32_t* __restrict__ ws, uint32_t* __restric
   m[idx] = (uint32_t)((asum + rnd) % dc.t);
 }
 
+// Noise of decryption (Appendix A): v = [c0 + c1 s - Delta m]_q, centred, for
+// every coefficient; ws holds the phase residues [c0 + c1 s]_{q_l} [n][L][N].
+// The residues of v are lifted to Z_q by CRT in 128 bits; the largest |v|
+// (as a double: exact below 2^53) goes to *out through an atomic maximum on
+// its bit pattern (non-negative doubles order like their bits).
+__global__ void k_noise(const uint32_t* __restrict__ ws, const uint32_t* __restrict__ m, int n, int N,
+                        DecConst dc, CtxConst cc, unsigned long long* out) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * N) return;
+  const size_t c = idx / N, u = idx % N;
+  typedef unsigned __int128 u128;
+  const u128 Q = ((u128)dc.qhi << 64) | dc.qlo;
+  const uint64_t msg = m[idx];
+  u128 V = 0;
+  for (int l = 0; l < dc.L; ++l) {
+    const uint64_t q = dc.q[l];
+    const uint64_t x = ws[(c * dc.L + l) * N + u];
+    const uint64_t dm = (cc.limb[l].delta * (msg % q)) % q;
+    const uint64_t v = (x + q - dm) % q;
+    const uint64_t y = (v * dc.inv[l]) % q;
+    V += (u128)y * (((u128)dc.Qhi[l] << 64) | dc.Qlo[l]);
+  }
+  while (V >= Q) V -= Q;
+  const u128 a = (V << 1) > Q ? Q - V : V;  // |centred v|
+  const double d = (double)(uint64_t)(a >> 64) * 18446744073709551616.0 + (double)(uint64_t)a;
+  atomicMax(out, (unsigned long long)__double_as_longlong(d));
+}
+
 __global__ void k_extract(const uint32_t* __restrict__ m, int32_t* __restrict__ y, GeomDims g, int B,
                           int N) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -565,6 +593,14 @@ cudaError_t launch_dec_round(const uint32_t* ws, uint32_t* m, int n, int N, cons
   const size_t total = (size_t)n * N;
   if (total == 0) return cudaSuccess;
   k_dec_round<<<blocks_for(total, 256), 256, 0, st>>>(ws, m, n, N, dc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_noise(const uint32_t* ws, const uint32_t* m, int n, int N, const DecConst& dc, const CtxConst& cc,
+                         unsigned long long* out, cudaStream_t st) {
+  const size_t total = (size_t)n * N;
+  if (total == 0) return cudaSuccess;
+  k_noise<<<blocks_for(total, 256), 256, 0, st>>>(ws, m, n, N, dc, cc, out);
   return cudaGetLastError();
 }
 

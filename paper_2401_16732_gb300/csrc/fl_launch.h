@@ -138,6 +138,8 @@ cudaError_t launch_pmul_intt(int logn, int mode, int n, uint32_t* ws, uint32_t* 
                              const uint32_t* tw, const CtxConst& cc, cudaStream_t st);
 cudaError_t launch_dec_round(const uint32_t* ws, uint32_t* m, int n, int N, const DecConst& dc,
                              cudaStream_t st);
+cudaError_t launch_noise(const uint32_t* ws, const uint32_t* m, int n, int N, const DecConst& dc, const CtxConst& cc,
+                         unsigned long long* out, cudaStream_t st);
 cudaError_t launch_extract(const uint32_t* m, int32_t* y, const GeomDims& g, int B, int N,
                            cudaStream_t st);
 cudaError_t launch_mask(uint32_t* ct, const uint32_t* r, int n, int N, const CtxConst& cc,

@@ -71,6 +71,10 @@ _SIGS = {
     "fl_ctx_get_ntt_plan": ([_vp], _i),
     "fl_ctx_set_tc_tile": ([_vp, _i], _i),
     "fl_ctx_get_tc_tile": ([_vp], _i),
+    "fl_noise_workspace_bytes": ([_vp, _i], _sz),
+    "fl_noise_inf": ([_vp, _vp, _i, _vp, _vp, _vp, _sz, _vp, ctypes.POINTER(ctypes.c_double)], _i),
+    "fl_copy_to_device": ([_vp, _vp, _vp, _sz, _vp], _i),
+    "fl_copy_to_host": ([_vp, _vp, _vp, _sz, _vp], _i),
     "fl_tc_weights": ([_vp, _gp, _vp, _vp, _vp], _i),
     "fl_he_conv2d_tc_workspace_bytes": ([_vp, _gp, _i], _sz),
     "fl_he_conv2d_tc_from_ntt": ([_vp, _gp, _i, _vp, _vp, _sz, _vp, _vp], _i),
@@ -428,6 +432,35 @@ class Context:
         _dev_u32(out, (B, g.n_out, 2, self.L, self.N), "out")
         _check(_lib.fl_intt_mask_outputs(self.h, ctypes.byref(g), B, _ptr(r), _ptr(out), _stream(stream)))
         return out
+
+    def noise_inf(self, sk, ct, m, stream=None) -> float:
+        """Largest |v| of the decryption noise (Appendix A) of ct [..., 2, L, N]
+        against the expected messages m [..., N] (values in [0, t))."""
+        n = ct.numel() // (2 * self.L * self.N)
+        _dev_u32(ct, (n, 2, self.L, self.N) if ct.dim() == 4 else tuple(ct.shape), "ct")
+        if m.numel() != n * self.N:
+            raise FlashError(f"m: {m.numel()} values for {n} ciphertexts of {self.N} coefficients")
+        ws = torch.empty(max(_lib.fl_noise_workspace_bytes(self.h, n), 16) // 4, dtype=torch.int32, device=ct.device)
+        v = ctypes.c_double()
+        _check(_lib.fl_noise_inf(self.h, _ptr(sk), n, _ptr(ct), _ptr(m), _ptr(ws), ws.numel() * 4, _stream(stream),
+                                 ctypes.byref(v)))
+        return v.value
+
+    def copy_to_device(self, host, dev, stream=None):
+        """Copy the host tensor's 32-bit words into the device tensor through
+        the library (fl_copy_to_device); asynchronous for pinned host memory."""
+        if host.is_cuda or not dev.is_cuda or host.numel() != dev.numel() or host.element_size() != 4:
+            raise FlashError("copy_to_device: a 32-bit host tensor and a device tensor of the same size")
+        _check(_lib.fl_copy_to_device(self.h, _ptr(host), _ptr(dev), host.numel(), _stream(stream)))
+        return dev
+
+    def copy_to_host(self, dev, host, stream=None):
+        """Copy the device tensor's 32-bit words into the host tensor through
+        the library (fl_copy_to_host); asynchronous for pinned host memory."""
+        if host.is_cuda or not dev.is_cuda or host.numel() != dev.numel() or dev.element_size() != 4:
+            raise FlashError("copy_to_host: a device tensor and a 32-bit host tensor of the same size")
+        _check(_lib.fl_copy_to_host(self.h, _ptr(dev), _ptr(host), dev.numel(), _stream(stream)))
+        return host
 
     def tc_error(self, stream=None) -> int:
         """Synchronise and read (and clear) the tensor-core form's error word:

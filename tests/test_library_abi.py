@@ -31,6 +31,18 @@ def test_library_exports_every_header_symbol(fg):
     assert set(syms) <= exported
 
 
+def test_peak_measurement_library_exports_its_header_symbols():
+    """The roofline-ceiling library bench.py loads (libflpeaks) exports every
+    function include/flpeaks.h declares; it is separate from libflashgpu."""
+    from paper_2401_16732_gb300 import build
+    path = build.build_peaks()
+    with open(os.path.join(ROOT, "include", "flpeaks.h")) as f:
+        syms = re.findall(r"^int (fl_\w+)\(", f.read(), re.M)
+    assert syms == ["fl_measure_butterfly_rate"]
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    assert set(syms) <= set(re.findall(r" T (fl_\w+)", out))
+
+
 GEOMS = [
     (4096, 16, 16, 16, 16, 3, 1, 1), (8192, 3, 64, 32, 32, 3, 1, 1), (8192, 64, 128, 32, 32, 3, 2, 1),
     (8192, 64, 128, 32, 32, 1, 2, 0), (8192, 512, 512, 4, 4, 3, 1, 1), (16384, 3, 64, 224, 224, 7, 2, 3),
