@@ -26,7 +26,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2401_16732_gb300 import synth  # noqa: E402
-from paper_2401_16732_gb300.workloads import WORKLOADS  # noqa: E402
+from paper_2401_16732_gb300.workloads import WORKLOADS, Workload  # noqa: E402
 
 T_PLAIN = 65537
 FALLBACK_HBM_GBS = 6800.0
@@ -75,9 +75,9 @@ KERNEL_SOURCES = {  # the kernel's own file and the shared device header
     "intt_rows": ("fl_tc.cu", "fl_device.cuh"),
 }
 TRAFFIC = {  # (config, kernel): (bytes per step, source hash at capture)
-    ("resnet18", "queue"): (3.354e9, "62ede15b38b67d2f"),
-    ("x2x", "round1"): (1.032e9, "a51b3f0fe9cceca3"),
-    ("x2x", "round2"): (1.071e9, "a51b3f0fe9cceca3"),
+    ("resnet18", "queue"): (3.354e9, "f83a47d431a8b512"),
+    ("x2x", "round1"): (1.0325e9, "5848e4ce26f75efd"),
+    ("x2x", "round2"): (1.0681e9, "5848e4ce26f75efd"),
 }
 
 
@@ -1177,6 +1177,37 @@ def run_serve(args, rank, world, local_rank):
     return 0
 
 
+def run_peaks():
+    """The measured ceilings (libflpeaks): lazy Gentleman-Sande butterflies/s
+    and tcgen05.mma kind::f16 flops/s at M128 K16 and N = 64, 128, 256."""
+    import ctypes
+
+    import torch
+    torch.cuda.init()
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2401_16732_gb300", "libflpeaks.so"))
+    dbl = ctypes.POINTER(ctypes.c_double)
+    lib.fl_measure_butterfly_rate.argtypes = [ctypes.c_int, dbl]
+    lib.fl_measure_tc_f16_rate.argtypes = [ctypes.c_int, ctypes.c_int, dbl, dbl]
+    out = {"device": torch.cuda.get_device_name(0)}
+    v = ctypes.c_double()
+    rc = lib.fl_measure_butterfly_rate(20000, ctypes.byref(v))
+    out["butterflies_per_s"] = v.value if rc == 0 else {"error": rc}
+    tc = {}
+    for n in (64, 128, 256):
+        f, c = ctypes.c_double(), ctypes.c_double()
+        rc = lib.fl_measure_tc_f16_rate(n, 20000, ctypes.byref(f), ctypes.byref(c))
+        tc[f"M128 N{n} K16"] = ({"tflops": f.value / 1e12, "cycles_per_mma": c.value,
+                                 "flop_per_clk_per_sm": 2 * 128 * n * 16 / c.value} if rc == 0 else {"error": rc})
+    out["tcgen05_f16"] = tc
+    try:  # the SM clock right after the measurements, and its maximum
+        nv = NvmlClock(0, gpu_uuid(0))
+        out["sm_mhz_after"], out["sm_max_mhz"] = nv.read()[0], nv.max_mhz
+    except Exception:
+        pass
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1198,12 +1229,28 @@ def main():
                     help="default workload only: skip the batched-stack measurements added to its line")
     ap.add_argument("--stack-kernel", default="auto", choices=["auto", "per_layer", "persistent", "queue"],
                     help="kernel for the contraction/INTT/mask stage (auto: time both, keep the faster)")
+    ap.add_argument("--layers", default=None,
+                    help="comma-separated layer indices: run only these layers of the chosen stack (a smaller "
+                         "workload, e.g. for a profiler capture)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="print the measured roofline ceilings of this GPU (butterfly rate, tcgen05 kind::f16 "
+                         "MMA rates) as one JSON line and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.peaks:
+        return run_peaks()
     if args.config == "serve":
         return run_serve(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
                          int(os.environ.get("LOCAL_RANK", "0")))
     wl = WORKLOADS[args.config] if args.config != "x2x" else None
+    if args.layers:
+        if wl is None:
+            ap.error("--layers selects layers of a convolution stack")
+        idx = [int(v) for v in args.layers.split(",")]
+        if not idx or any(not 0 <= i < len(wl.layers) for i in idx):
+            ap.error(f"--layers: indices in 0..{len(wl.layers) - 1}")
+        wl = Workload(f"{wl.name}: layers {args.layers} only", wl.N, wl.L, wl.B, tuple(wl.layers[i] for i in idx))
+        args.no_batched = True
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -20,9 +20,10 @@
 // minus 0x4B400000 is then P_e itself.
 // Recombination mod q on the CUDA cores: Y = sum_e 256^e P_e (|Y| < 2^46.1)
 // is known exactly mod 2^32 from the bit patterns; its quotient k =
-// round(Y / q) comes from an fp32 estimate of Y (error below 2^22.1, so k is
-// within 0.51 of Y / q), and Y - k q + q lies in [0, 2q), the input range of
-// the inverse NTT, computed exactly in 32-bit arithmetic.
+// round(Y / q) comes from an fp32 estimate of Y (error below 2^24.4, and
+// every prime of a context lies above 2^29, so k is within 0.55 of Y / q),
+// and Y - k q + q lies in [0, 2q), the input range of the inverse NTT,
+// computed exactly in 32-bit arithmetic.
 //
 //   k_tc_weights   (offline) the encoded weights re-laid in slot groups of 8
 //   k_tc_inputs    the NTT images of the inputs re-laid in slot groups of 4
@@ -120,11 +121,13 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 // generic-proxy shared-memory writes visible to the tensor core's (async-proxy) reads
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 8 consecutive tensor-memory columns of this thread's lane
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-               : "r"(taddr));
+// 16 consecutive tensor-memory columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -166,12 +169,15 @@ __device__ __forceinline__ void cp16_pol(uint32_t dst, const void* src, uint32_t
                "r"(src_bytes), "l"(pol)
                : "memory");
 }
+// 4-byte cp.async through L1 (the only form of that size), same policy operand
+__device__ __forceinline__ void cp4_pol(uint32_t dst, const void* src, uint32_t src_bytes, uint64_t pol) {
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2, %3;" ::"r"(dst), "l"(src),
+               "r"(src_bytes), "l"(pol)
+               : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int K>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
-__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
 
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
@@ -200,10 +206,15 @@ __device__ __forceinline__ uint2 digits4(uint32_t v) {
 }
 
 // Y - k q + q in [0, 2q) for Y = sum_e 256^e P_e, from the accumulator bit
-// patterns b[e] = bits(3 * 2^22 + P_e).  The fp32 estimate of Y sums the
-// biased accumulators (|error| < 2^23.1 at |sum| < 2^48) and subtracts the
-// biases' sum 3 * 2^22 * 0x01010101 (rounded: |error| <= 2^23; the
-// subtraction itself is exact), so k = round(Y / q) is within 0.52 of Y / q.
+// patterns b[e] = bits(3 * 2^22 + P_e), b[e] in [2^23, 2^24].  The fp32
+// estimate of Y sums the biased accumulators by three fmas, which round by
+// at most 2^8, 2^16 and 2^24 (the last sum may reach 2^48 + 2^40), and
+// subtracts the biases' sum 3 * 2^22 * 0x01010101, itself rounded by 2^22
+// (the subtraction is exact: both operands are multiples of 2^24 and the
+// difference is below 2^47).  So the estimate is within 2^24.4 of Y, i.e.
+// within 0.042 q for q > 2^29, and with the final rounding to an integer
+// (0.5) and the rounding of 1/q (below 0.005 at |Y / q| < 2^16.1), k is
+// within 0.55 of Y / q.
 // nq = -q mod 2^32; c = FP_BIAS * q + q - FP_BIAS * 0x01010101 mod 2^32 (the
 // biases of k and of the four P_e).
 __device__ __forceinline__ uint32_t recombine(const uint32_t* b, float qinv, uint32_t nq, uint32_t c) {
@@ -225,7 +236,7 @@ __device__ __forceinline__ uint32_t recombine(const uint32_t* b, float qinv, uin
 //   producers (8 warps)  raw ring -> fp16 tile stage t % TC_NS, arrive tile_full
 //   MMA warp (1 thread)  tile_full -> 4 MMAs into accumulator buffer g % 2 ->
 //                        commit to tile_empty (and to acc_full after a group)
-//   epilogue (4 warps)   acc_full -> tensor-memory loads -> arrive acc_empty ->
+//   epilogue (8 warps)   acc_full -> tensor-memory loads -> arrive acc_empty ->
 //                        recombination -> stores of the NTT-domain outputs
 template <int GPC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -234,7 +245,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ __align__(1024) uint8_t tsm[];
   __shared__ uint64_t tile_full[TC_NS], tile_empty[TC_NS], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_abort, p_abort[2];
+  __shared__ int s_abort;
   __shared__ long long colout[TC_CW];  // output word offset of each column, output channel 0; -1 outside
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cols = 2 * B * cd.bands, mtiles = (cd.Cout + TC_M - 1) / TC_M;
@@ -256,7 +267,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&acc_full[k], 1);
       mbar_init(&acc_empty[k], 32 * TC_EPI_WARPS);
     }
-    s_abort = p_abort[0] = p_abort[1] = 0;
+    s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < TC_CW) {
@@ -273,34 +284,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp < TC_PROD_WARPS) {
     // ------------------------------------------------------------ producers
     const int pt = tid;  // 0..255
-    // Raw loads of each K step into ring slot t % TC_RING, 16-byte cp.async:
-    // A (slot-tiled weights w_tc[l][u / 8][g][(u % 8) / 4][i][4]): row pt & 127
-    // of the planes g = 2 (pt >> 7), + 1, so a warp reads 512 contiguous bytes;
-    // B (pt < 64; slot-tiled inputs c_tc[l][u / 4][b][ct][c][4]): image/band
-    // pt >> 3, ciphertext (pt >> 1) & 3, component pt & 1, so 8 threads read
-    // one 128-byte run.  Outside the layer the copies fill zeros.
+    // Raw loads of each K step into ring slot t % TC_RING.  Every producer
+    // thread converts exactly the words it copied itself, so a thread waits
+    // only for its own cp.async groups and the producers need no barrier
+    // among themselves.
+    // A (slot-tiled weights w_tc[l][u / 8][g][(u % 8) / 4][i][4]), 16-byte
+    // copies: row pt & 127 of the planes g = 2 (pt >> 7), + 1, so a warp
+    // reads 512 contiguous bytes.
+    // B (slot-tiled inputs c_tc[l][u / 4][b][ct][c][4]), 4-byte copies:
+    // column pt >> 4 (image/band (pt >> 5), component (pt >> 4) & 1), slot
+    // (pt >> 2) & 3, ciphertext pt & 3, so a warp reads 128 contiguous bytes.
+    // Outside the layer the copies fill zeros.
     const int a_row = pt & (TC_M - 1), a_gp = pt >> 7;
     const bool a_ok = i0 + a_row < cd.Cout;
     const size_t a_plane = (size_t)cd.Cout * 4;  // words of one (8-slot group, g, half) plane
     const uint32_t* a_src = w_tc + (size_t)l * (N / 8) * G * 2 * a_plane + (size_t)(i0 + a_row) * 4;
     const uint32_t a_dst = sb + OFF_RAWA + a_row * 16;
-    const int b_pair = pt >> 3, b_g = (pt >> 1) & 3, b_c = pt & 1;
-    bool b_ok = false;
+    const int bc_col = pt >> 4, bc_s = (pt >> 2) & 3, bc_g = pt & 3;
+    const uint32_t b_off = ((((bc_col >> 1) * TC_GS + bc_g) * 2 + (bc_col & 1)) * 4 + bc_s) * 4;  // bytes in a step
+    bool b_ok;
     const uint32_t* b_src = c_hat;
-    if (pt < TC_CW * TC_GS) {
-      const int colg = col0 + 2 * b_pair + b_c, bb = colg >> 1, b = bb / cd.bands, band = bb - b * cd.bands;
+    {
+      const int colg = col0 + bc_col, bb = colg >> 1, b = bb / cd.bands, band = bb - b * cd.bands;
       b_ok = colg < cols;
-      if (b_ok) b_src = c_hat + (((size_t)l * (N / 4) * B + b) * cd.n_in + (size_t)band * G) * 8 + b_c * 4;
+      if (b_ok)
+        b_src = c_hat + (((size_t)l * (N / 4) * B + b) * cd.n_in + (size_t)band * G + bc_g) * 8 + (colg & 1) * 4 + bc_s;
     }
     const size_t b_grp = (size_t)B * cd.n_in * 8;  // words of one 4-slot group of the inputs
-    const uint32_t b_dst = sb + OFF_RAWB + ((b_pair * TC_GS + b_g) * 2 + b_c) * 16;
     // weights are read once (evict first); inputs once per output-channel
     // tile, by CTAs that run together (evict last)
     const uint64_t pol_w = policy_evict_first(), pol_x = policy_evict_last();
-    auto issue = [&](int t) {
-      if (t < T) {
-        const int g0 = TC_GS * (t % nch), grp = grp0 + t / nch, r = t % TC_RING;
-        const uint32_t* ag = a_src + ((size_t)(grp >> 1) * G * 2 + (grp & 1)) * a_plane;
+    // the next step to issue: K step ich (ciphertexts TC_GS ich ..) of group igrp
+    int it = 0, ich = 0, igrp = grp0;
+    auto issue = [&]() {
+      if (it < T) {
+        const int g0 = TC_GS * ich, r = it % TC_RING;
+        const uint32_t* ag = a_src + ((size_t)(igrp >> 1) * G * 2 + (igrp & 1)) * a_plane;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
           const int g = 2 * a_gp + k;
@@ -308,32 +327,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           cp16_pol(a_dst + r * RAWA_STEP + g * TC_M * 16, ok ? ag + (size_t)(g0 + g) * 2 * a_plane : w_tc,
                    ok ? 16 : 0, pol_w);
         }
-        if (pt < TC_CW * TC_GS) {
-          const bool ok = b_ok && g0 + b_g < G;
-          cp16_pol(b_dst + r * RAWB_STEP, ok ? b_src + grp * b_grp + (size_t)(g0 + b_g) * 8 : c_hat, ok ? 16 : 0,
-                   pol_x);
+        const bool ok = b_ok && g0 + bc_g < G;
+        cp4_pol(sb + OFF_RAWB + r * RAWB_STEP + b_off, ok ? b_src + igrp * b_grp + (size_t)g0 * 8 : c_hat,
+                ok ? 4 : 0, pol_x);
+        ++it;
+        if (++ich == nch) {
+          ich = 0;
+          ++igrp;
         }
       }
       cp_commit();
     };
-    // conversion roles: A row rrow, K chunk chh; B column pt >> 4, slot (pt >> 2) & 3, ciphertext pt & 3
+    // conversion role of A: row rrow (= a_row), K chunk chh (= a_gp)
     const int rrow = 32 * (warp & 3) + lane, chh = warp >> 2;
-    const int bc_col = pt >> 4, bc_s = (pt >> 2) & 3, bc_g = pt & 3;
     const uint32_t q = lc.q;
     const uint32_t w1s = (uint32_t)((256ull << 32) / q), w2s = (uint32_t)((65536ull << 32) / q),
                    w3s = (uint32_t)((16777216ull << 32) / q);
     const uint2 bias_a = make_uint2(H_2048, 0), zero2 = make_uint2(0, 0);
+    bool aborted = false;
 #pragma unroll 1
-    for (int t = 0; t < TC_RING - 1; ++t) issue(t);
+    for (int t = 0; t < TC_RING - 1; ++t) issue();
+    int ch = 0;  // K step of step t within its group
 #pragma unroll 1
     for (int t = 0; t < T; ++t) {
-      const int st = t % TC_NS, r = t % TC_RING, g0 = TC_GS * (t % nch);
+      const int st = t % TC_NS, r = t % TC_RING, g0 = TC_GS * ch;
+      if (++ch == nch) ch = 0;
       // stage st was last read by the MMAs of step t - TC_NS
-      if (!mbar_wait_bounded(&tile_empty[st], ((t / TC_NS) & 1) ^ 1)) p_abort[t & 1] = 1;
-      cp_wait<TC_RING - 2>();
-      named_bar_sync(1, TC_NPROD);  // raw step t visible to every producer; raw step t - 1 converted
-      if (p_abort[t & 1]) break;
-      issue(t + TC_RING - 1);        // into the ring slot of step t - 1
+      if (!mbar_wait_bounded(&tile_empty[st], ((t / TC_NS) & 1) ^ 1)) {
+        aborted = true;
+        break;
+      }
+      cp_wait<TC_RING - 2>();  // this thread's copies of step t have landed
+      issue();                 // step t + TC_RING - 1, into the ring slot this thread emptied at step t - 1
       uint8_t* stage = tsm + OFF_TILE + st * STAGE_BYTES;
       {  // A: 4 slots of row rrow, ciphertexts g0 + 2 chh, + 1
         const uint4* ra = reinterpret_cast<const uint4*>(tsm + OFF_RAWA + r * RAWA_STEP);
@@ -357,8 +382,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
       {  // B: rows (col, e), K (g, a) of slot bc_s
-        const uint32_t x = reinterpret_cast<const uint32_t*>(
-            tsm + OFF_RAWB + r * RAWB_STEP)[(((bc_col >> 1) * TC_GS + bc_g) * 2 + (bc_col & 1)) * 4 + bc_s];
+        const uint32_t x = *reinterpret_cast<const uint32_t*>(tsm + OFF_RAWB + r * RAWB_STEP + b_off);
         const int gg = g0 + bc_g;
         uint2 dd[4];
         if (gg < G) {
@@ -385,7 +409,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_arrive(&tile_full[st]);
     }
     cp_wait<0>();
-    if (p_abort[0] | p_abort[1]) s_abort = 1;
+    if (aborted) s_abort = 1;
   } else if (warp == TC_MMA_WARP) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
@@ -420,7 +444,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t nq = 0u - lc.q, cfix = FP_BIAS * lc.q + lc.q - FP_BIAS * 0x01010101u;
     const uint32_t ta = tbase + ((uint32_t)(32 * qd) << 16);
     // Groups come in pairs (8 slots, one 32-byte sector of every output row):
-    // the even group's results wait in registers for the odd one's.
+    // the even group's results wait in shared memory for the odd one's.
     constexpr int HS = 32 * TC_EPI_WARPS;  // hold[local column][slot][epilogue thread]
     uint32_t* hold = reinterpret_cast<uint32_t*>(tsm + OFF_HOLD) + (tid - 32 * TC_PROD_WARPS);
 #pragma unroll 1
@@ -432,18 +456,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       tc_fence_after();
 #pragma unroll
-      for (int p = 0; p < TC_CW / 4; ++p) {  // columns 8 hc + 2p, + 1
-        uint32_t v[TC_U][8];
+      for (int p = 0; p < TC_CW / 8; ++p) {  // columns 8 hc + 4p .. + 3
+        uint32_t v[TC_U][16];
 #pragma unroll
-        for (int s = 0; s < TC_U; ++s) tmem_ld8(ta + (ab * TC_U + s) * TC_NN + 4 * (8 * hc + 2 * p), v[s]);
+        for (int s = 0; s < TC_U; ++s) tmem_ld16(ta + (ab * TC_U + s) * TC_NN + 4 * (8 * hc + 4 * p), v[s]);
         tmem_wait_ld();
-        if (p == TC_CW / 4 - 1) {  // this warp's accumulators of the buffer are in registers
+        if (p == TC_CW / 8 - 1) {  // this warp's accumulators of the buffer are in registers
           tc_fence_before();
           mbar_arrive(&acc_empty[ab]);
         }
 #pragma unroll
-        for (int cc2 = 0; cc2 < 2; ++cc2) {
-          const int cl = 2 * p + cc2, c = 8 * hc + cl;
+        for (int cc2 = 0; cc2 < 4; ++cc2) {
+          const int cl = 4 * p + cc2, c = 8 * hc + cl;
           uint32_t o[TC_U];
 #pragma unroll
           for (int s = 0; s < TC_U; ++s) o[s] = recombine(&v[s][4 * cc2], qinv, nq, cfix);

@@ -38,7 +38,7 @@ def test_peak_measurement_library_exports_its_header_symbols():
     path = build.build_peaks()
     with open(os.path.join(ROOT, "include", "flpeaks.h")) as f:
         syms = re.findall(r"^int (fl_\w+)\(", f.read(), re.M)
-    assert syms == ["fl_measure_butterfly_rate"]
+    assert syms == ["fl_measure_butterfly_rate", "fl_measure_tc_f16_rate"]
     out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
     assert set(syms) <= set(re.findall(r" T (fl_\w+)", out))
 
