@@ -54,7 +54,6 @@ constexpr int TC_U = 4;               // slots per group: one accumulator buffer
 constexpr int TC_GS = 4;              // input ciphertexts per K step: 4 x 4 weight digits = K 16
 constexpr int TC_PROD_WARPS = 8;      // cp.async + digit conversion into the tile ring
 constexpr int TC_EPI_WARPS = 8;       // recombination, two per tensor-memory lane quadrant
-constexpr int TC_NPROD = 32 * TC_PROD_WARPS;
 constexpr int TC_MMA_WARP = TC_PROD_WARPS + TC_EPI_WARPS;  // one more warp issues the MMAs
 constexpr int TC_THREADS = 32 * (TC_MMA_WARP + 1);          // 544
 constexpr int TC_RING = 6;            // raw-residue ring depth, in K steps
@@ -260,12 +259,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) tmem_alloc(&tmem_base, TC_TMEM_COLS);
   if (tid == 0) {
     for (int k = 0; k < TC_NS; ++k) {
-      mbar_init(&tile_full[k], TC_NPROD);
+      mbar_init(&tile_full[k], TC_PROD_WARPS);  // one arrival per producer warp
       mbar_init(&tile_empty[k], 1);
     }
     for (int k = 0; k < 2; ++k) {
       mbar_init(&acc_full[k], 1);
-      mbar_init(&acc_empty[k], 32 * TC_EPI_WARPS);
+      mbar_init(&acc_empty[k], TC_EPI_WARPS);
     }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -352,8 +351,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = 0; t < T; ++t) {
       const int st = t % TC_NS, r = t % TC_RING, g0 = TC_GS * ch;
       if (++ch == nch) ch = 0;
-      // stage st was last read by the MMAs of step t - TC_NS
-      if (!mbar_wait_bounded(&tile_empty[st], ((t / TC_NS) & 1) ^ 1)) {
+      // stage st was last read by the MMAs of step t - TC_NS; the decision
+      // to stop is the warp's, so that no lane is left at __syncwarp
+      if (__any_sync(0xffffffffu, !mbar_wait_bounded(&tile_empty[st], ((t / TC_NS) & 1) ^ 1))) {
         aborted = true;
         break;
       }
@@ -405,8 +405,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           *reinterpret_cast<uint2*>(tb + (row >> 3) * 256 + (row & 7) * 16) = dd[e];
         }
       }
+      // every lane's tile writes visible to the tensor core, then one
+      // arrival per warp
       fence_async_smem();
-      mbar_arrive(&tile_full[st]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tile_full[st]);
     }
     cp_wait<0>();
     if (aborted) s_abort = 1;
@@ -450,7 +453,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll 1
     for (int grp = 0; grp < GPC; ++grp) {
       const int ab = grp & 1, u0 = 4 * (grp0 + grp);
-      if (!mbar_wait_bounded(&acc_full[ab], (grp >> 1) & 1)) {
+      // the decision to stop is the warp's: the tensor-memory loads below are
+      // warp-collective
+      if (__any_sync(0xffffffffu, !mbar_wait_bounded(&acc_full[ab], (grp >> 1) & 1))) {
         s_abort = 1;
         break;
       }
@@ -463,7 +468,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tmem_wait_ld();
         if (p == TC_CW / 8 - 1) {  // this warp's accumulators of the buffer are in registers
           tc_fence_before();
-          mbar_arrive(&acc_empty[ab]);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[ab]);  // one arrival per epilogue warp
         }
 #pragma unroll
         for (int cc2 = 0; cc2 < 4; ++cc2) {
