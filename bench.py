@@ -450,6 +450,16 @@ class ClockSampler:
                 "reasons": reasons, "samples_under_load": len(load)}
 
 
+def share_tc_workspace(ctx, layers, B):
+    """One tensor-core workspace, of the largest layer's size, for all the
+    given layers: they run one after another on one stream, and a workspace
+    larger than a layer needs is valid for it."""
+    if layers:
+        ws = ctx.tc_workspace(max((lay["g"] for lay in layers), key=lambda g: g.n_in), B)
+        for lay in layers:
+            lay["ws"] = ws
+
+
 def run_gpu(args, wl, rank, world, local_rank, emit=True):
     import torch
     import torch.distributed as dist
@@ -498,9 +508,7 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
         # form (layers that choose the latter keep only their re-laid weights)
         from paper_2401_16732_gb300.autotune import tune_forms
         tuning["forms"] = tune_forms(ctx, layers, stream=stream, cache=None)
-        for lay in layers:
-            if lay["form"] == "tc":
-                lay["ws"] = ctx.tc_workspace(lay["g"], B)
+        share_tc_workspace(ctx, [lay for lay in layers if lay["form"] == "tc"], B)
     plain_layers = [lay for lay in layers if lay["form"] == "plain"]
     tc_layers = [lay for lay in layers if lay["form"] == "tc"]
     arr = ws = None
@@ -513,9 +521,11 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
         tuned = {"kernel": "tc", "ms": None}
     elif args.form in ("direct", "otf", "tc"):
         tuned = {"kernel": args.form, "ms": None}
-        if args.form in ("otf", "tc"):
+        if args.form == "tc":
+            share_tc_workspace(ctx, layers, B)
+        elif args.form == "otf":
             for lay in layers:
-                lay["ws"] = (ctx.tc_workspace if args.form == "tc" else ctx.workspace)(lay["g"], B)
+                lay["ws"] = ctx.workspace(lay["g"], B)
     elif args.stack_kernel == "auto":
         from paper_2401_16732_gb300.autotune import tune_stack
         tuned = tune_stack(ctx, [{"g": lay["g"], "ct_in": lay["ct"], "r": lay["r"]} for lay in layers], arr, ws,

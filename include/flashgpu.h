@@ -247,9 +247,10 @@ int fl_he_conv2d_direct(fl_ctx *ctx, const fl_conv_geom *geom, int B, const int8
  * - Tiling: a CTA holds 128 output channels x 16 (image/band, component)
  *   columns x 8 slots of one limb in tensor memory; the K dimension runs
  *   over (input ciphertext, weight digit) in steps of 16.
- * - Weights: w_tc_dev holds the encoded weights of fl_encode_weights
- *   re-laid by fl_tc_weights into slot groups of 8, so that each CTA reads
- *   its weights as contiguous runs (fl_weights_bytes bytes, the same words).
+ * - Weights: w_tc_dev holds the weight tiles of fl_tc_weights (fp16 digits
+ *   in the MMA's shared-memory layout), which the kernel bulk-copies into
+ *   shared memory as they are; only the inputs are split into digits on
+ *   the fly.
  * - Unlike the plain form it is not fused with the inverse NTT: a tile spans
  *   128 output channels of 8 slots, while the inverse NTT needs every slot of
  *   one output.  So the NTT-domain outputs go through ct_out_dev, and a
@@ -262,13 +263,26 @@ int fl_he_conv2d_direct(fl_ctx *ctx, const fl_conv_geom *geom, int B, const int8
  * fl_he_conv2d), then their copy in slot groups of 4 ([L][N/4][B][n_in][2][4])
  * that the contraction reads: 2 * B*n_in*2*L*N*4 bytes. */
 size_t fl_he_conv2d_tc_workspace_bytes(const fl_ctx *ctx, const fl_conv_geom *geom, int B);
-/* The encoded weights w_hat_dev [L][Cout][G][N] (fl_encode_weights) re-laid
- * for fl_he_conv2d_tc: w_tc_dev [L][N/8][G][2][Cout][4], word
- * [l][u/8][g][(u%8)/4][i][u%4] = w_hat[l][i][g][u].  fl_weights_bytes bytes;
- * the buffers must not overlap.  Offline, like the encoding itself. */
-int fl_tc_weights(fl_ctx *ctx, const fl_conv_geom *geom, const uint32_t *w_hat_dev, uint32_t *w_tc_dev,
+/* Bytes of the tensor-core weight tiles of one layer (fl_tc_weights):
+ * L * ceil(Cout/128) * (N/4) * ceil(G/4) * 16384; 0 when G > FL_TC_MAX_G
+ * or an argument is NULL. */
+size_t fl_tc_weights_bytes(const fl_ctx *ctx, const fl_conv_geom *geom);
+/* The encoded weights w_hat_dev [L][Cout][G][N] (fl_encode_weights) as the
+ * weight tiles of fl_he_conv2d_tc, w_tc_dev (fl_tc_weights_bytes bytes of
+ * fp16 bit patterns, 16-byte aligned, not overlapping w_hat_dev).  For every
+ * limb l, tile of 128 output channels mt, 4-slot group u4 = u / 4 and K step
+ * kc (input ciphertexts 4 kc .. 4 kc + 3), one 16 KB tile, ordered
+ * [l][mt][u4][kc]: slot u % 4 takes 4 KB, in which row r (output channel
+ * i = 128 mt + r) and K index k = 4 (g % 4) + a hold the balanced base-256
+ * digit a of w_hat[l][i][g][u], d_a(v) = byte_a(v + 0x80808080) - 128, at
+ * byte ((r / 8) * 2 + k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 (8 x 16-byte
+ * core matrices, K-major).  Rows beyond Cout and ciphertexts beyond G are
+ * zeros.  About 2 to 3 times the bytes of w_hat: two bytes per digit, K
+ * padded to a multiple of 4 ciphertexts, rows to a multiple of 128.
+ * Offline, like the encoding itself.  G > FL_TC_MAX_G: FL_ERR_SHAPE. */
+int fl_tc_weights(fl_ctx *ctx, const fl_conv_geom *geom, const uint32_t *w_hat_dev, uint16_t *w_tc_dev,
                   void *stream);
-int fl_he_conv2d_tc(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_tc_dev,
+int fl_he_conv2d_tc(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint16_t *w_tc_dev,
                     const uint32_t *ct_in_dev, const uint32_t *r_dev, uint32_t *ct_out_dev,
                     void *workspace_dev, size_t workspace_bytes, void *stream);
 
@@ -281,7 +295,7 @@ int fl_he_conv2d_tc(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t
  * in-place inverse NTT of B * n_out such NTT-domain output ciphertexts
  * (whose weights carried N^-1) plus Delta * r on c0 when r_dev is not NULL;
  * the result is fl_he_conv2d_mask's. */
-int fl_he_conv2d_tc_from_ntt(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *w_tc_dev,
+int fl_he_conv2d_tc_from_ntt(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint16_t *w_tc_dev,
                              void *workspace_dev, size_t workspace_bytes, uint32_t *ct_out_dev, void *stream);
 int fl_intt_mask_outputs(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *r_dev, uint32_t *ct_out_dev,
                          void *stream);

@@ -708,7 +708,7 @@ static int tc_checks(fl_ctx* ctx, const fl_conv_geom* geom, int B, size_t worksp
 // slot-tiled copy of the NTT images (second half of the workspace), then the
 // tensor-core contraction; `pdl`: the contraction follows the copy as a
 // programmatic dependent launch
-static int stage_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_tc_dev, const void* ws,
+static int stage_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint16_t* w_tc_dev, const void* ws,
                     uint32_t* ct_out_dev, cudaStream_t st) {
   const uint32_t* c_hat = (const uint32_t*)ws;
   uint32_t* c_tc = (uint32_t*)ws + fl_he_conv2d_workspace_bytes(ctx, geom, B) / 4;
@@ -721,7 +721,7 @@ static int stage_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t
                   "tensor-core contraction");
 }
 
-int fl_he_conv2d_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_tc_dev, const uint32_t* ct_in_dev,
+int fl_he_conv2d_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint16_t* w_tc_dev, const uint32_t* ct_in_dev,
                     const uint32_t* r_dev, uint32_t* ct_out_dev, void* workspace_dev, size_t workspace_bytes,
                     void* stream) {
   int rc;
@@ -737,7 +737,7 @@ int fl_he_conv2d_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t
                   "output inverse ntt");
 }
 
-int fl_he_conv2d_tc_from_ntt(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* w_tc_dev,
+int fl_he_conv2d_tc_from_ntt(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint16_t* w_tc_dev,
                              void* workspace_dev, size_t workspace_bytes, uint32_t* ct_out_dev, void* stream) {
   int rc;
   if ((rc = tc_checks(ctx, geom, B, workspace_bytes))) return rc;
@@ -761,15 +761,23 @@ int fl_intt_mask_outputs(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uin
                   "output inverse ntt");
 }
 
-int fl_tc_weights(fl_ctx* ctx, const fl_conv_geom* geom, const uint32_t* w_hat_dev, uint32_t* w_tc_dev, void* stream) {
+size_t fl_tc_weights_bytes(const fl_ctx* ctx, const fl_conv_geom* geom) {
+  if (!ctx || !geom || geom->G < 1 || geom->G > FL_TC_MAX_G) return 0;
+  return fl::tc_weights_bytes(ctx->L, geom->Cout, geom->G, ctx->N);
+}
+
+int fl_tc_weights(fl_ctx* ctx, const fl_conv_geom* geom, const uint32_t* w_hat_dev, uint16_t* w_tc_dev, void* stream) {
   int rc;
   if ((rc = check_ctx(ctx)) || (rc = check_geom(ctx, geom))) return rc;
+  if (geom->G > FL_TC_MAX_G)
+    return fail(FL_ERR_SHAPE, "G=%d input ciphertexts per band: above %d, the tensor-core form is not exact",
+                geom->G, FL_TC_MAX_G);
   if ((rc = check_ptrs({w_hat_dev, w_tc_dev}))) return rc;
-  const size_t bytes = fl_weights_bytes(ctx, geom);
+  const size_t in_bytes = fl_weights_bytes(ctx, geom), out_bytes = fl_tc_weights_bytes(ctx, geom);
   const uintptr_t a = (uintptr_t)w_hat_dev, b = (uintptr_t)w_tc_dev;
-  if (a < b + bytes && b < a + bytes) return fail(FL_ERR_ARG, "w_hat and w_tc overlap");
+  if (a < b + out_bytes && b < a + in_bytes) return fail(FL_ERR_ARG, "w_hat and w_tc overlap");
   return launched(fl::launch_tc_weights(w_hat_dev, w_tc_dev, ctx->L, geom->Cout, geom->G, ctx->N, (cudaStream_t)stream),
-                  "tensor-core weight layout");
+                  "tensor-core weight tiles");
 }
 
 int fl_tc_error(fl_ctx* ctx, void* stream, uint64_t* error_host) {

@@ -167,9 +167,11 @@ cudaError_t launch_conv_otf(int logn, int B, const GeomDims& gd, const int8_t* w
 constexpr int kTcMaxG = 64;
 cudaError_t launch_tc_setup(int logn);
 size_t conv_tc_smem_bytes();
-cudaError_t launch_tc_weights(const uint32_t* w_hat, uint32_t* w_tc, int L, int Cout, int G, int N, cudaStream_t st);
+// bytes of the tensor-core weight tiles of one layer (k_tc_weights)
+size_t tc_weights_bytes(int L, int Cout, int G, int N);
+cudaError_t launch_tc_weights(const uint32_t* w_hat, uint16_t* w_tc, int L, int Cout, int G, int N, cudaStream_t st);
 cudaError_t launch_tc_inputs(const uint32_t* c_hat, uint32_t* c_tc, int B, int n_in, int L, int N, cudaStream_t st);
-cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_tc, const uint32_t* c_hat, uint32_t* y_hat,
+cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint16_t* w_tc, const uint32_t* c_hat, uint32_t* y_hat,
                            int N, const CtxConst& cc, unsigned long long* err, cudaStream_t st, bool pdl, int gpc = 0);
 cudaError_t launch_intt_mask_rows(int logn, long long rows, uint32_t* y, const uint32_t* r, const uint32_t* tw,
                                   const CtxConst& cc, cudaStream_t st, bool pdl, int r1 = 0);

@@ -15,9 +15,9 @@
 // So per slot one matrix product with K = (g, a) (4G) and N = (col, e) (4 per
 // column) gives four partial sums P_e per output.  |P_e| <= 4G * 128^2 =
 // G * 2^16 <= 2^22 for G <= 64, so every fp32 partial sum is an exact integer.
-// One more K column carries a bias 2048 * 6144 = 3 * 2^22 (both factors exact
-// in fp16), which puts every accumulator in [2^23, 2^24]: the fp32 bit pattern
-// minus 0x4B400000 is then P_e itself.
+// Every accumulator starts at 3 * 2^22 (written into tensor memory before
+// each group), which keeps every partial sum in [2^23, 2^24]: the fp32 bit
+// pattern minus 0x4B400000 is then P_e itself.
 // Recombination mod q on the CUDA cores: Y = sum_e 256^e P_e (|Y| < 2^46.1)
 // is known exactly mod 2^32 from the bit patterns; its quotient k =
 // round(Y / q) comes from an fp32 estimate of Y (error below 2^24.4, and
@@ -25,16 +25,20 @@
 // and Y - k q + q lies in [0, 2q), the input range of the inverse NTT,
 // computed exactly in 32-bit arithmetic.
 //
-//   k_tc_weights   (offline) the encoded weights re-laid in slot groups of 8
+//   k_tc_weights   (offline) the encoded weights as fp16 digit tiles in the
+//                  MMA's shared-memory layout, 16 KB per K step
 //   k_tc_inputs    the NTT images of the inputs re-laid in slot groups of 4
 //   k_conv_tc      one CTA per SM and (128 output channels, 16 columns, limb,
-//                  run of 16 groups of 4 slots), warp-specialised: 8 producer
-//                  warps (cp.async ring of raw residues -> fp16 digit tiles in
-//                  the canonical K-major layout, 4 stages), one MMA warp (4
-//                  MMAs M128 N64 K16 per K step, one per slot, into one of two
-//                  tensor-memory accumulator buffers), 8 epilogue warps
-//                  (tensor-memory loads, recombination, 32-byte stores of the
-//                  NTT-domain outputs in [0, 2q)); every hand-off an mbarrier
+//                  run of 16 groups of 4 slots), warp-specialised: one warp
+//                  bulk-copies each K step's weight tile into its operand
+//                  stage (cp.async.bulk, completion on an mbarrier); 8
+//                  producer warps split the inputs into fp16 digit tiles
+//                  (4-byte cp.async ring -> canonical K-major layout); one
+//                  MMA warp issues 4 MMAs M128 N64 K16 per K step, one per
+//                  slot, into one of two tensor-memory accumulator buffers;
+//                  8 epilogue warps load the accumulators, recombine, store
+//                  the NTT-domain outputs in [0, 2q) in 32-byte runs and
+//                  reset the buffer to the bias; every hand-off an mbarrier
 //                  with a bounded wait
 //   k_intt_mask_rows   in-place inverse NTT of every output row, + Delta*r on
 //                  component 0 (the encoded weights carry N^-1, so the
@@ -52,34 +56,34 @@ constexpr int TC_CW = 16;             // columns per CTA; MMA N = 4 * 16 = 64 (c
 constexpr int TC_NN = 4 * TC_CW;
 constexpr int TC_U = 4;               // slots per group: one accumulator buffer of 4 x 64 columns
 constexpr int TC_GS = 4;              // input ciphertexts per K step: 4 x 4 weight digits = K 16
-constexpr int TC_PROD_WARPS = 8;      // cp.async + digit conversion into the tile ring
+constexpr int TC_PROD_WARPS = 8;      // input copies + digit conversion into the B tiles
 constexpr int TC_EPI_WARPS = 8;       // recombination, two per tensor-memory lane quadrant
-constexpr int TC_MMA_WARP = TC_PROD_WARPS + TC_EPI_WARPS;  // one more warp issues the MMAs
-constexpr int TC_THREADS = 32 * (TC_MMA_WARP + 1);          // 544
-constexpr int TC_RING = 6;            // raw-residue ring depth, in K steps
-constexpr int TC_NS = 4;              // fp16 tile stages
+constexpr int TC_MMA_WARP = TC_PROD_WARPS + TC_EPI_WARPS;  // one warp issues the MMAs,
+constexpr int TC_LOAD_WARP = TC_MMA_WARP + 1;              // one the bulk copies of the weight tiles
+constexpr int TC_THREADS = 32 * (TC_LOAD_WARP + 1);        // 576
+constexpr int TC_RING = 6;            // raw-input ring depth, in K steps
+constexpr int TC_NS = 6;              // operand stages (weight tile + input tile)
 // slot groups per CTA (the tile's length along the slots): 4, 8 or 16, a
 // template parameter of k_conv_tc chosen per workload (even: the epilogue
 // stores groups in pairs)
 constexpr int TC_GPC_DEFAULT = 16;
 constexpr int TC_TMEM_COLS = 2 * TC_U * TC_NN;  // 512: two accumulator buffers
 // shared-memory layout (bytes)
-constexpr int RAWA_STEP = TC_GS * TC_M * 16;       // [g][row][4 slots]
 constexpr int RAWB_STEP = TC_CW * TC_GS * 16;      // [image/band][g][component][4 slots]
 constexpr int TILEA_SLOT = TC_M * 32;              // 128 rows x 16 halves
+constexpr int TILEA_STEP = TC_U * TILEA_SLOT;      // one weight tile: 16 KB, one bulk copy
 constexpr int TILEB_SLOT = TC_NN * 32 + 16;        // 64 rows x 16 halves, +16 B against bank conflicts
-constexpr int STAGE_BYTES = TC_U * (TILEA_SLOT + TILEB_SLOT);
-constexpr int OFF_RAWA = 0;
-constexpr int OFF_RAWB = OFF_RAWA + TC_RING * RAWA_STEP;
-constexpr int OFF_TILE = (OFF_RAWB + TC_RING * RAWB_STEP + 1023) / 1024 * 1024;
-constexpr int OFF_HOLD = OFF_TILE + TC_NS * STAGE_BYTES;  // epilogue: even group's results [col][slot][thread]
+constexpr int STAGE_BYTES = TILEA_STEP + TC_U * TILEB_SLOT;
+constexpr int OFF_TILE = 0;
+constexpr int OFF_RAWB = OFF_TILE + TC_NS * STAGE_BYTES;
+constexpr int OFF_HOLD = OFF_RAWB + TC_RING * RAWB_STEP;  // epilogue: even group's results [col][slot][thread]
 constexpr int TC_SMEM = OFF_HOLD + (TC_CW / 2) * TC_U * 32 * TC_EPI_WARPS * 4;
+static_assert(STAGE_BYTES % 16 == 0 && OFF_HOLD % 16 == 0, "bulk copies and vector accesses stay 16-byte aligned");
 // more than half of the SM's shared memory: one CTA per SM, which then owns
 // all of tensor memory
 static_assert(TC_SMEM > 116 * 1024 && TC_SMEM <= 220 * 1024, "one CTA per SM with room for the static part");
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // 2 s bound on every wait
 constexpr uint32_t FP_BIAS = 0x4B400000u;                 // bits of 3 * 2^22 in fp32
-constexpr uint16_t H_2048 = 0x6800, H_6144 = 0x6E00;      // fp16 2048, 6144
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -128,6 +132,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
 }
+// the same 16 columns set to one value
+__device__ __forceinline__ void tmem_st16_const(uint32_t taddr, uint32_t x) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(x)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -161,12 +173,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return false;
 }
 
-// 16-byte cp.async (src_bytes 0 fills the destination with zeros) with an
-// L2 eviction policy (createpolicy)
-__device__ __forceinline__ void cp16_pol(uint32_t dst, const void* src, uint32_t src_bytes, uint64_t pol) {
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(dst), "l"(src),
-               "r"(src_bytes), "l"(pol)
+// arrive on bar and announce `bytes` more bytes of transactions for its
+// current phase (the bulk copy that follows completes them)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes)
                : "memory");
+}
+// bulk copy (no tensor map) of `bytes` contiguous bytes global -> shared,
+// completed on bar; both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(su32(bar)), "l"(pol)
+      : "memory");
 }
 // 4-byte cp.async through L1 (the only form of that size), same policy operand
 __device__ __forceinline__ void cp4_pol(uint32_t dst, const void* src, uint32_t src_bytes, uint64_t pol) {
@@ -230,36 +250,42 @@ __device__ __forceinline__ uint32_t recombine(const uint32_t* b, float qinv, uin
 // output channels and 16 columns (fastest, so CTAs sharing input slots run
 // together), blockIdx.y the run of GPC groups of 4 slots, blockIdx.z the
 // limb.  Step t of the CTA is (group t / nch, K step t % nch) with nch =
-// G / 4 + 1 K steps per group, the last of which carries the bias column.
+// ceil(G / 4) K steps per group.
 // Warp roles (every hand-off an mbarrier with a bounded wait):
-//   producers (8 warps)  raw ring -> fp16 tile stage t % TC_NS, arrive tile_full
-//   MMA warp (1 thread)  tile_full -> 4 MMAs into accumulator buffer g % 2 ->
-//                        commit to tile_empty (and to acc_full after a group)
-//   epilogue (8 warps)   acc_full -> tensor-memory loads -> arrive acc_empty ->
-//                        recombination -> stores of the NTT-domain outputs
+//   load warp (1 thread) tile_empty -> bulk copy of the weight tile into stage
+//                        t % TC_NS, completing a_full
+//   producers (8 warps)  tile_empty -> raw input ring -> fp16 input tile of
+//                        stage t % TC_NS, arrive tile_full
+//   MMA warp (1 thread)  a_full + tile_full -> 4 MMAs into accumulator buffer
+//                        grp % 2 -> commit to tile_empty (and to acc_full
+//                        after a group)
+//   epilogue (8 warps)   acc_full -> tensor-memory loads -> recombination ->
+//                        stores of the NTT-domain outputs -> bias written
+//                        back into the buffer -> arrive acc_empty
 template <int GPC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_conv_tc(const uint32_t* __restrict__ w_tc, const uint32_t* __restrict__ c_hat, uint32_t* __restrict__ y_hat,
+    k_conv_tc(const uint16_t* __restrict__ w_tc, const uint32_t* __restrict__ c_hat, uint32_t* __restrict__ y_hat,
               ConvDims cd, int B, int N, CtxConst cc, unsigned long long* err) {
   extern __shared__ __align__(1024) uint8_t tsm[];
-  __shared__ uint64_t tile_full[TC_NS], tile_empty[TC_NS], acc_full[2], acc_empty[2];
+  __shared__ uint64_t a_full[TC_NS], tile_full[TC_NS], tile_empty[TC_NS], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
   __shared__ long long colout[TC_CW];  // output word offset of each column, output channel 0; -1 outside
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cols = 2 * B * cd.bands, mtiles = (cd.Cout + TC_M - 1) / TC_M;
-  const int i0 = (blockIdx.x % mtiles) * TC_M, col0 = (blockIdx.x / mtiles) * TC_CW;
+  const int mt = blockIdx.x % mtiles, i0 = mt * TC_M, col0 = (blockIdx.x / mtiles) * TC_CW;
   static_assert(GPC % 2 == 0, "the epilogue stores groups in pairs");
   const int l = blockIdx.z, grp0 = blockIdx.y * GPC, L = cc.L, G = cd.G;
   const LimbConst lc = cc.limb[l];
   const size_t NL = (size_t)L * N, rowstride = (size_t)cd.bands * 2 * NL;
-  const int nch = G / TC_GS + 1, T = GPC * nch;
+  const int nch = (G + TC_GS - 1) / TC_GS, T = GPC * nch;
   const uint32_t sb = su32(tsm);
 
   if (warp == 0) tmem_alloc(&tmem_base, TC_TMEM_COLS);
   if (tid == 0) {
     for (int k = 0; k < TC_NS; ++k) {
-      mbar_init(&tile_full[k], TC_PROD_WARPS);  // one arrival per producer warp
+      mbar_init(&a_full[k], 1);                 // the weight tile's bulk copy
+      mbar_init(&tile_full[k], TC_PROD_WARPS);  // the input tile: one arrival per producer warp
       mbar_init(&tile_empty[k], 1);
     }
     for (int k = 0; k < 2; ++k) {
@@ -283,22 +309,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp < TC_PROD_WARPS) {
     // ------------------------------------------------------------ producers
     const int pt = tid;  // 0..255
-    // Raw loads of each K step into ring slot t % TC_RING.  Every producer
-    // thread converts exactly the words it copied itself, so a thread waits
-    // only for its own cp.async groups and the producers need no barrier
-    // among themselves.
-    // A (slot-tiled weights w_tc[l][u / 8][g][(u % 8) / 4][i][4]), 16-byte
-    // copies: row pt & 127 of the planes g = 2 (pt >> 7), + 1, so a warp
-    // reads 512 contiguous bytes.
-    // B (slot-tiled inputs c_tc[l][u / 4][b][ct][c][4]), 4-byte copies:
-    // column pt >> 4 (image/band (pt >> 5), component (pt >> 4) & 1), slot
-    // (pt >> 2) & 3, ciphertext pt & 3, so a warp reads 128 contiguous bytes.
-    // Outside the layer the copies fill zeros.
-    const int a_row = pt & (TC_M - 1), a_gp = pt >> 7;
-    const bool a_ok = i0 + a_row < cd.Cout;
-    const size_t a_plane = (size_t)cd.Cout * 4;  // words of one (8-slot group, g, half) plane
-    const uint32_t* a_src = w_tc + (size_t)l * (N / 8) * G * 2 * a_plane + (size_t)(i0 + a_row) * 4;
-    const uint32_t a_dst = sb + OFF_RAWA + a_row * 16;
+    // The input tiles.  Raw words of each K step go into ring slot
+    // t % TC_RING by 4-byte cp.async (c_tc[l][u / 4][b][ct][c][4]): column
+    // pt >> 4 (image/band (pt >> 5), component (pt >> 4) & 1), slot
+    // (pt >> 2) & 3, ciphertext pt & 3, so a warp reads 128 contiguous bytes;
+    // outside the layer the copies fill zeros.  Every producer thread
+    // converts exactly the word it copied itself, so it waits only for its
+    // own copy groups and the producers need no barrier among themselves.
     const int bc_col = pt >> 4, bc_s = (pt >> 2) & 3, bc_g = pt & 3;
     const uint32_t b_off = ((((bc_col >> 1) * TC_GS + bc_g) * 2 + (bc_col & 1)) * 4 + bc_s) * 4;  // bytes in a step
     bool b_ok;
@@ -310,25 +327,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         b_src = c_hat + (((size_t)l * (N / 4) * B + b) * cd.n_in + (size_t)band * G + bc_g) * 8 + (colg & 1) * 4 + bc_s;
     }
     const size_t b_grp = (size_t)B * cd.n_in * 8;  // words of one 4-slot group of the inputs
-    // weights are read once (evict first); inputs once per output-channel
-    // tile, by CTAs that run together (evict last)
-    const uint64_t pol_w = policy_evict_first(), pol_x = policy_evict_last();
-    // the next step to issue: K step ich (ciphertexts TC_GS ich ..) of group igrp
-    int it = 0, ich = 0, igrp = grp0;
+    // the inputs are read once per output-channel tile, by CTAs that run
+    // together (evict last)
+    const uint64_t pol_x = policy_evict_last();
+    int it = 0, ich = 0, igrp = grp0;  // the next step to copy: K step ich of group igrp
     auto issue = [&]() {
       if (it < T) {
-        const int g0 = TC_GS * ich, r = it % TC_RING;
-        const uint32_t* ag = a_src + ((size_t)(igrp >> 1) * G * 2 + (igrp & 1)) * a_plane;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int g = 2 * a_gp + k;
-          const bool ok = a_ok && g0 + g < G;
-          cp16_pol(a_dst + r * RAWA_STEP + g * TC_M * 16, ok ? ag + (size_t)(g0 + g) * 2 * a_plane : w_tc,
-                   ok ? 16 : 0, pol_w);
-        }
+        const int g0 = TC_GS * ich;
         const bool ok = b_ok && g0 + bc_g < G;
-        cp4_pol(sb + OFF_RAWB + r * RAWB_STEP + b_off, ok ? b_src + igrp * b_grp + (size_t)g0 * 8 : c_hat,
-                ok ? 4 : 0, pol_x);
+        cp4_pol(sb + OFF_RAWB + (it % TC_RING) * RAWB_STEP + b_off,
+                ok ? b_src + igrp * b_grp + (size_t)g0 * 8 : c_hat, ok ? 4 : 0, pol_x);
         ++it;
         if (++ich == nch) {
           ich = 0;
@@ -337,73 +345,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       cp_commit();
     };
-    // conversion role of A: row rrow (= a_row), K chunk chh (= a_gp)
-    const int rrow = 32 * (warp & 3) + lane, chh = warp >> 2;
     const uint32_t q = lc.q;
     const uint32_t w1s = (uint32_t)((256ull << 32) / q), w2s = (uint32_t)((65536ull << 32) / q),
                    w3s = (uint32_t)((16777216ull << 32) / q);
-    const uint2 bias_a = make_uint2(H_2048, 0), zero2 = make_uint2(0, 0);
     bool aborted = false;
 #pragma unroll 1
     for (int t = 0; t < TC_RING - 1; ++t) issue();
-    int ch = 0;  // K step of step t within its group
 #pragma unroll 1
     for (int t = 0; t < T; ++t) {
-      const int st = t % TC_NS, r = t % TC_RING, g0 = TC_GS * ch;
-      if (++ch == nch) ch = 0;
+      const int st = t % TC_NS, r = t % TC_RING;
       // stage st was last read by the MMAs of step t - TC_NS; the decision
       // to stop is the warp's, so that no lane is left at __syncwarp
       if (__any_sync(0xffffffffu, !mbar_wait_bounded(&tile_empty[st], ((t / TC_NS) & 1) ^ 1))) {
         aborted = true;
         break;
       }
-      cp_wait<TC_RING - 2>();  // this thread's copies of step t have landed
+      cp_wait<TC_RING - 2>();  // this thread's copy of step t has landed
       issue();                 // step t + TC_RING - 1, into the ring slot this thread emptied at step t - 1
-      uint8_t* stage = tsm + OFF_TILE + st * STAGE_BYTES;
-      {  // A: 4 slots of row rrow, ciphertexts g0 + 2 chh, + 1
-        const uint4* ra = reinterpret_cast<const uint4*>(tsm + OFF_RAWA + r * RAWA_STEP);
-        const int gg = g0 + 2 * chh;
-        const uint4 x0 = ra[(2 * chh) * TC_M + rrow], x1 = ra[(2 * chh + 1) * TC_M + rrow];
-        const uint32_t w0[TC_U] = {x0.x, x0.y, x0.z, x0.w}, w1[TC_U] = {x1.x, x1.y, x1.z, x1.w};
-        uint8_t* ta = stage + ((rrow >> 3) * 2 + chh) * 128 + (rrow & 7) * 16;
-        if (gg + 1 < G) {
+      // B: rows (col, e), K (g, a) of slot bc_s
+      const uint32_t x = *reinterpret_cast<const uint32_t*>(tsm + OFF_RAWB + r * RAWB_STEP + b_off);
+      // (the copies filled zeros beyond G, and the digits of 0 are zeros)
+      const uint32_t y0 = x + 0x80808080u;
+      const uint32_t y1 = shoup_mul(x, 256u, w1s, q) + 0x80808080u;  // X'_a in [0, 2q), congruent to 256^a X
+      const uint32_t y2 = shoup_mul(x, 65536u, w2s, q) + 0x80808080u;
+      const uint32_t y3 = shoup_mul(x, 16777216u, w3s, q) + 0x80808080u;
+      uint2 dd[4];
 #pragma unroll
-          for (int s = 0; s < TC_U; ++s) {
-            const uint2 d0 = digits4(w0[s]), d1 = digits4(w1[s]);
-            *reinterpret_cast<uint4*>(ta + s * TILEA_SLOT) = make_uint4(d0.x, d0.y, d1.x, d1.y);
-          }
-        } else {  // the last K step: ciphertext G carries the bias column, beyond it zeros
+      for (int e = 0; e < 4; ++e)
+        dd[e] = make_uint2(digits2(__byte_perm(y0, y1, e | ((4 + e) << 8))),
+                           digits2(__byte_perm(y2, y3, e | ((4 + e) << 8))));
+      uint8_t* tb = tsm + OFF_TILE + st * STAGE_BYTES + TILEA_STEP + bc_s * TILEB_SLOT + (bc_g >> 1) * 128 +
+                    (bc_g & 1) * 8;
 #pragma unroll
-          for (int s = 0; s < TC_U; ++s) {
-            const uint2 d0 = gg < G ? digits4(w0[s]) : gg == G ? bias_a : zero2;
-            const uint2 d1 = gg + 1 == G ? bias_a : zero2;
-            *reinterpret_cast<uint4*>(ta + s * TILEA_SLOT) = make_uint4(d0.x, d0.y, d1.x, d1.y);
-          }
-        }
-      }
-      {  // B: rows (col, e), K (g, a) of slot bc_s
-        const uint32_t x = *reinterpret_cast<const uint32_t*>(tsm + OFF_RAWB + r * RAWB_STEP + b_off);
-        const int gg = g0 + bc_g;
-        uint2 dd[4];
-        if (gg < G) {
-          const uint32_t y0 = x + 0x80808080u;
-          const uint32_t y1 = shoup_mul(x, 256u, w1s, q) + 0x80808080u;  // X'_a in [0, 2q), congruent to 256^a X
-          const uint32_t y2 = shoup_mul(x, 65536u, w2s, q) + 0x80808080u;
-          const uint32_t y3 = shoup_mul(x, 16777216u, w3s, q) + 0x80808080u;
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            dd[e] = make_uint2(digits2(__byte_perm(y0, y1, e | ((4 + e) << 8))),
-                               digits2(__byte_perm(y2, y3, e | ((4 + e) << 8))));
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) dd[e] = make_uint2(gg == G ? H_6144 : 0, 0);
-        }
-        uint8_t* tb = stage + TC_U * TILEA_SLOT + bc_s * TILEB_SLOT + (bc_g >> 1) * 128 + (bc_g & 1) * 8;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int row = 4 * bc_col + e;
-          *reinterpret_cast<uint2*>(tb + (row >> 3) * 256 + (row & 7) * 16) = dd[e];
-        }
+      for (int e = 0; e < 4; ++e) {
+        const int row = 4 * bc_col + e;
+        *reinterpret_cast<uint2*>(tb + (row >> 3) * 256 + (row & 7) * 16) = dd[e];
       }
       // every lane's tile writes visible to the tensor core, then one
       // arrival per warp
@@ -413,26 +389,56 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     cp_wait<0>();
     if (aborted) s_abort = 1;
+  } else if (warp == TC_LOAD_WARP) {
+    // ------------------------------------------------------------ weight tiles
+    // k_tc_weights stored every (limb, output-channel tile, 4-slot group,
+    // K step) as the 16 KB weight tile of one stage, in the MMA's shared-
+    // memory layout, and a CTA's steps as consecutive tiles: one bulk copy
+    // per step, read once (evict first).
+    if (lane == 0) {
+      const uint64_t pol_w = policy_evict_first();
+      const uint8_t* src =
+          reinterpret_cast<const uint8_t*>(w_tc) + (((size_t)l * mtiles + mt) * (N / 4) + grp0) * nch * TILEA_STEP;
+      int t = 0;
+#pragma unroll 1
+      for (; t < T; ++t) {
+        const int st = t % TC_NS;
+        if (!mbar_wait_bounded(&tile_empty[st], ((t / TC_NS) & 1) ^ 1)) {
+          s_abort = 1;
+          break;
+        }
+        mbar_arrive_expect_tx(&a_full[st], TILEA_STEP);
+        bulk_g2s(sb + OFF_TILE + st * STAGE_BYTES, src + (size_t)t * TILEA_STEP, TILEA_STEP, &a_full[st], pol_w);
+      }
+      // no copy may still be writing when the CTA exits: wait for the last
+      // one into every stage (earlier ones completed before their stage was
+      // reused)
+#pragma unroll 1
+      for (int k = t > TC_NS ? t - TC_NS : 0; k < t; ++k)
+        if (!mbar_wait_bounded(&a_full[k % TC_NS], (k / TC_NS) & 1)) s_abort = 1;
+    }
   } else if (warp == TC_MMA_WARP) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
 #pragma unroll 1
       for (int t = 0; t < T; ++t) {
         const int st = t % TC_NS, ch = t % nch, grp = t / nch, ab = grp & 1;
-        if (ch == 0 && !mbar_wait_bounded(&acc_empty[ab], ((grp >> 1) & 1) ^ 1)) {
+        // use grp >> 1 of buffer ab needs the epilogue's arrival number
+        // grp >> 1 (the first one: the bias written before any group)
+        if (ch == 0 && !mbar_wait_bounded(&acc_empty[ab], (grp >> 1) & 1)) {
           s_abort = 1;
           break;
         }
-        if (!mbar_wait_bounded(&tile_full[st], (t / TC_NS) & 1)) {
+        if (!mbar_wait_bounded(&a_full[st], (t / TC_NS) & 1) || !mbar_wait_bounded(&tile_full[st], (t / TC_NS) & 1)) {
           s_abort = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t ta = sb + OFF_TILE + st * STAGE_BYTES, tb = ta + TC_U * TILEA_SLOT;
+        const uint32_t ta = sb + OFF_TILE + st * STAGE_BYTES, tb = ta + TILEA_STEP;
 #pragma unroll
         for (int s = 0; s < TC_U; ++s)
           mma_f16(tbase + (ab * TC_U + s) * TC_NN, smem_desc(ta + s * TILEA_SLOT, 128, 256),
-                  smem_desc(tb + s * TILEB_SLOT, 128, 256), idesc_f16(TC_M, TC_NN), ch > 0);
+                  smem_desc(tb + s * TILEB_SLOT, 128, 256), idesc_f16(TC_M, TC_NN), 1u);  // onto the bias
         mma_commit(&tile_empty[st]);
         if (ch == nch - 1) mma_commit(&acc_full[ab]);
       }
@@ -450,6 +456,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // the even group's results wait in shared memory for the odd one's.
     constexpr int HS = 32 * TC_EPI_WARPS;  // hold[local column][slot][epilogue thread]
     uint32_t* hold = reinterpret_cast<uint32_t*>(tsm + OFF_HOLD) + (tid - 32 * TC_PROD_WARPS);
+    // Every accumulator of a buffer starts at 3 * 2^22: this warp writes the
+    // bias into its lanes and columns (column chunk p of every slot) once it
+    // has read them, and hands the buffer back to the MMA warp.
+    auto bias = [&](int ab, int p) {
+#pragma unroll
+      for (int s = 0; s < TC_U; ++s) tmem_st16_const(ta + (ab * TC_U + s) * TC_NN + 4 * (8 * hc + 4 * p), FP_BIAS);
+    };
+    auto release = [&](int ab) {
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[ab]);  // one arrival per epilogue warp
+    };
+#pragma unroll
+    for (int ab = 0; ab < 2; ++ab) {
+#pragma unroll
+      for (int p = 0; p < TC_CW / 8; ++p) bias(ab, p);
+      release(ab);
+    }
 #pragma unroll 1
     for (int grp = 0; grp < GPC; ++grp) {
       const int ab = grp & 1, u0 = 4 * (grp0 + grp);
@@ -466,11 +491,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int s = 0; s < TC_U; ++s) tmem_ld16(ta + (ab * TC_U + s) * TC_NN + 4 * (8 * hc + 4 * p), v[s]);
         tmem_wait_ld();
-        if (p == TC_CW / 8 - 1) {  // this warp's accumulators of the buffer are in registers
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&acc_empty[ab]);  // one arrival per epilogue warp
-        }
 #pragma unroll
         for (int cc2 = 0; cc2 < 4; ++cc2) {
           const int cl = 4 * p + cc2, c = 8 * hc + cl;
@@ -490,7 +510,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
           }
         }
+        bias(ab, p);  // this chunk's accumulators have been read
       }
+      release(ab);
     }
   }
   tc_fence_before();
@@ -525,32 +547,56 @@ __global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
                                                MaskStore{p, (r && c == 0) ? r + oct * N : nullptr, lc}, p);
 }
 
-// Slot-tiled copy of the encoded weights for k_conv_tc: w_tc[l][u / 8][g][h][i][j]
-// = w_hat[l][i][g][u] with u = 8 (u / 8) + 4 h + j.  The same words in another
-// order: the weights of one K step of one CTA (4 ciphertexts, 2 halves, 128
-// output channels, 8 slots) become 8 runs of 2 KB.  One thread per (l, i, g,
-// slot group).
-__global__ void k_tc_weights(const uint32_t* __restrict__ w_hat, uint32_t* __restrict__ w_tc, int Cout, int G, int N,
-                             long long total) {
+// The encoded weights as k_conv_tc's weight tiles: for every limb l,
+// output-channel tile mt (128 rows), 4-slot group u4 and K step kc (input
+// ciphertexts 4 kc .. 4 kc + 3), one 16 KB tile of fp16 digits in the MMA's
+// shared-memory layout, tiles ordered [l][mt][u4][kc].  Within a tile, slot
+// s = u % 4 takes 4 KB; row r, K index k = 4 (g % 4) + a (digit a of
+// ciphertext g) sits in core matrix (r / 8, k / 8) at byte ((r / 8) * 2 +
+// k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.  Rows beyond Cout and
+// ciphertexts beyond G are zeros.  One thread per (tile, 16-byte chunk of a
+// slot), for the 4 slots: it reads 4 consecutive slots of 2 ciphertexts.
+__global__ void k_tc_weights(const uint32_t* __restrict__ w_hat, uint16_t* __restrict__ w_tc, int Cout, int G, int N,
+                             int mtiles, int nch, long long total) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= total) return;
-  const int ng = N / 8;
-  const int grp = (int)(e % ng);
-  const long long lig = e / ng;  // (l * Cout + i) * G + g
-  const int g = (int)(lig % G), i = (int)((lig / G) % Cout), l = (int)(lig / ((long long)G * Cout));
-  const uint4* src = reinterpret_cast<const uint4*>(w_hat + lig * N + 8 * grp);
-  const uint4 a = src[0], b = src[1];
-  uint4* dst = reinterpret_cast<uint4*>(w_tc + ((((size_t)l * ng + grp) * G + g) * 2) * Cout * 4 + (size_t)i * 4);
-  dst[0] = a;
-  dst[(size_t)Cout] = b;
+  const int c = (int)(e & 255);  // chunk (r / 8, kh, r % 8) of a slot
+  long long rest = e >> 8;
+  const int kc = (int)(rest % nch);
+  rest /= nch;
+  const int u4 = (int)(rest % (N / 4));
+  rest /= N / 4;
+  const int mt = (int)(rest % mtiles), l = (int)(rest / mtiles);
+  const int kh = (c >> 3) & 1, i = mt * TC_M + (c >> 4) * 8 + (c & 7);
+  uint2 d[2][TC_U];
+#pragma unroll
+  for (int gl = 0; gl < 2; ++gl) {
+    const int g = TC_GS * kc + 2 * kh + gl;
+    uint4 v = make_uint4(0, 0, 0, 0);  // the digits of 0 are zeros
+    if (i < Cout && g < G) v = *reinterpret_cast<const uint4*>(w_hat + (((size_t)l * Cout + i) * G + g) * N + 4 * u4);
+    d[gl][0] = digits4(v.x);
+    d[gl][1] = digits4(v.y);
+    d[gl][2] = digits4(v.z);
+    d[gl][3] = digits4(v.w);
+  }
+  uint4* dst = reinterpret_cast<uint4*>(w_tc + ((((size_t)l * mtiles + mt) * (N / 4) + u4) * nch + kc) * (TILEA_STEP / 2));
+#pragma unroll
+  for (int s = 0; s < TC_U; ++s)
+    dst[s * (TILEA_SLOT / 16) + c] = make_uint4(d[0][s].x, d[0][s].y, d[1][s].x, d[1][s].y);
 }
 
-cudaError_t launch_tc_weights(const uint32_t* w_hat, uint32_t* w_tc, int L, int Cout, int G, int N, cudaStream_t st) {
-  const long long total = (long long)L * Cout * G * (N / 8);
+size_t tc_weights_bytes(int L, int Cout, int G, int N) {
+  return (size_t)L * ((Cout + TC_M - 1) / TC_M) * (N / 4) * ((G + TC_GS - 1) / TC_GS) * TILEA_STEP;
+}
+
+cudaError_t launch_tc_weights(const uint32_t* w_hat, uint16_t* w_tc, int L, int Cout, int G, int N, cudaStream_t st) {
+  if (G < 1 || G > kTcMaxG) return cudaErrorInvalidValue;
+  const int mtiles = (Cout + TC_M - 1) / TC_M, nch = (G + TC_GS - 1) / TC_GS;
+  const long long total = (long long)L * mtiles * (N / 4) * nch * 256;
   if (total == 0) return cudaSuccess;
   const long long blocks = (total + 255) / 256;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  k_tc_weights<<<(unsigned)blocks, 256, 0, st>>>(w_hat, w_tc, Cout, G, N, total);
+  k_tc_weights<<<(unsigned)blocks, 256, 0, st>>>(w_hat, w_tc, Cout, G, N, mtiles, nch, total);
   return cudaGetLastError();
 }
 
@@ -603,7 +649,7 @@ static cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, size_t smem, cudaStr
 
 // pdl: the previous operation in `st` is the forward NTT of these inputs.
 // gpc: slot groups per CTA (4, 8 or 16; 0 = the default).
-cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint32_t* w_tc, const uint32_t* c_hat, uint32_t* y_hat,
+cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint16_t* w_tc, const uint32_t* c_hat, uint32_t* y_hat,
                            int N, const CtxConst& cc, unsigned long long* err, cudaStream_t st, bool pdl, int gpc) {
   if (B == 0 || cd.Cout == 0) return cudaSuccess;
   if (cd.G < 1 || cd.G > kTcMaxG) return cudaErrorInvalidValue;

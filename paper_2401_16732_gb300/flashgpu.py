@@ -9,6 +9,7 @@ is missing the import of this module fails.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import re
 
@@ -75,6 +76,7 @@ _SIGS = {
     "fl_noise_inf": ([_vp, _vp, _i, _vp, _vp, _vp, _sz, _vp, ctypes.POINTER(ctypes.c_double)], _i),
     "fl_copy_to_device": ([_vp, _vp, _vp, _sz, _vp], _i),
     "fl_copy_to_host": ([_vp, _vp, _vp, _sz, _vp], _i),
+    "fl_tc_weights_bytes": ([_vp, _gp], _sz),
     "fl_tc_weights": ([_vp, _gp, _vp, _vp, _vp], _i),
     "fl_he_conv2d_tc_workspace_bytes": ([_vp, _gp, _i], _sz),
     "fl_he_conv2d_tc_from_ntt": ([_vp, _gp, _i, _vp, _vp, _sz, _vp, _vp], _i),
@@ -147,6 +149,14 @@ def _stream(stream):
 def _dev_u32(t: torch.Tensor, shape, name):
     if t.dtype not in (torch.int32, torch.uint32) or not t.is_cuda or not t.is_contiguous():
         raise FlashError(f"{name}: expected a contiguous 32-bit CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise FlashError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
+    return t
+
+
+def _dev_i16(t: torch.Tensor, shape, name):
+    if t.dtype not in (torch.int16, torch.uint16) or not t.is_cuda or not t.is_contiguous():
+        raise FlashError(f"{name}: expected a contiguous 16-bit CUDA tensor")
     if tuple(t.shape) != tuple(shape):
         raise FlashError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
     return t
@@ -390,23 +400,34 @@ class Context:
         nbytes = _lib.fl_he_conv2d_tc_workspace_bytes(self.h, ctypes.byref(g), B)
         return torch.empty(max(nbytes, 16) // 4, dtype=torch.int32, device=f"cuda:{self.device}")
 
+    def tc_weight_shape(self, g):
+        """Shape of tc_weights' result: [L][ceil(Cout/128)][N/4][ceil(G/4)][8192]
+        fp16 digits (one 16 KB weight tile per (limb, 128 output channels,
+        4-slot group, K step))."""
+        return (self.L, (g.Cout + 127) // 128, self.N // 4, (g.G + 3) // 4, 8192)
+
     def tc_weights(self, g, w_hat, out=None, stream=None) -> torch.Tensor:
-        """The encoded weights [L][Cout][G][N] re-laid for he_conv2d_tc:
-        [L][N/8][G][2][Cout][4] (slot groups of 8)."""
+        """The encoded weights [L][Cout][G][N] as he_conv2d_tc's weight tiles:
+        balanced base-256 digits in fp16, in the MMA's shared-memory layout
+        (int16 tensor of tc_weight_shape(g); see fl_tc_weights)."""
         _dev_u32(w_hat, (self.L, g.Cout, g.G, self.N), "w_hat")
-        shape = (self.L, self.N // 8, g.G, 2, g.Cout, 4)
-        out = torch.empty(shape, dtype=torch.int32, device=w_hat.device) if out is None else out
-        _dev_u32(out, shape, "out")
+        if g.G > FL_TC_MAX_G:
+            raise FlashError(f"G={g.G} above {FL_TC_MAX_G}: the tensor-core form is not exact")
+        shape = self.tc_weight_shape(g)
+        if 2 * math.prod(shape) != _lib.fl_tc_weights_bytes(self.h, ctypes.byref(g)):
+            raise FlashError("tensor-core weight tiles: the library's size differs from the binding's shape")
+        out = torch.empty(shape, dtype=torch.int16, device=w_hat.device) if out is None else out
+        _dev_i16(out, shape, "out")
         _check(_lib.fl_tc_weights(self.h, ctypes.byref(g), _ptr(w_hat), _ptr(out), _stream(stream)))
         return out
 
     def he_conv2d_tc(self, g, w_tc, ct_in, out=None, workspace=None, r=None, stream=None) -> torch.Tensor:
         """Tensor-core form (tcgen05, fp16 digits, fp32 accumulation): the
         same ciphertexts as he_conv2d (plus the mask when r is given) from
-        the encoded weights re-laid by tc_weights.  G <= FL_TC_MAX_G."""
+        the weight tiles of tc_weights.  G <= FL_TC_MAX_G."""
         B = ct_in.shape[0]
         _dev_u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
-        _dev_u32(w_tc, (self.L, self.N // 8, g.G, 2, g.Cout, 4), "w_tc")
+        _dev_i16(w_tc, self.tc_weight_shape(g), "w_tc")
         if r is not None:
             _dev_u32(r, (B, g.n_out, self.N), "r")
         out = self._new(B, g.n_out, 2, self.L, self.N) if out is None else out
@@ -420,6 +441,7 @@ class Context:
     def he_conv2d_tc_from_ntt(self, g, B, w_tc, workspace, out, stream=None):
         """Stage of he_conv2d_tc: the tensor-core contraction from a workspace
         filled by he_conv2d_ntt_inputs; out gets NTT-domain values in [0, 2q)."""
+        _dev_i16(w_tc, self.tc_weight_shape(g), "w_tc")
         _check(_lib.fl_he_conv2d_tc_from_ntt(self.h, ctypes.byref(g), B, _ptr(w_tc), _ptr(workspace),
                                              workspace.numel() * workspace.element_size(), _ptr(out),
                                              _stream(stream)))

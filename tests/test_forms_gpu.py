@@ -2,6 +2,8 @@
 Algorithm 1 (route O2) and with the NTT route: the direct form (DRot + CMult,
 no NTT) and on-the-fly weights (weight polynomials rebuilt and transformed
 in shared memory, no encoded weights).  All comparisons are bit-exact."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -217,16 +219,38 @@ def test_tc_form_stages_equal_the_one_call_form(fg):
     assert c.tc_error() == 0
 
 
-def test_tc_weights_are_the_encoded_weights_in_slot_groups(fg):
-    """tc_weights is a permutation: word [l][u/8][g][(u%8)/4][i][u%4] of the
-    re-laid weights is word [l][i][g][u] of the encoded ones."""
+def decode_tc_weights(wt, L, Cout, G, N):
+    """Digits of the weight tiles back to [L][rows][4 ceil(G/4)][N] integers
+    sum_a d_a 256^a, following the layout fl_tc_weights documents (16 KB per
+    (limb, 128-row tile, 4-slot group, K step), slot s at 2048 halves, row r
+    and K index k = 4 (g % 4) + a at half ((r / 8) * 2 + k / 8) * 64 +
+    (r % 8) * 8 + k % 8), plus the digits themselves."""
+    mt, nch = (Cout + 127) // 128, (G + 3) // 4
+    h = wt.cpu().numpy().view(np.float16).astype(np.float64)
+    assert (h == np.round(h)).all() and h.min() >= -128 and h.max() <= 127
+    # [l][mt][u4][kc][s][r/8][k/8][r%8][k%8] -> [l][mt][r/8][r%8][kc][k/8][k%8][u4][s]
+    h = h.reshape(L, mt, N // 4, nch, 4, 16, 2, 8, 8).transpose(0, 1, 5, 7, 3, 6, 8, 2, 4)
+    d = h.reshape(L, mt * 128, nch * 4, 4, N)  # [l][row][g][a][u]
+    v = sum(d[:, :, :, a].astype(np.int64) << (8 * a) for a in range(4))
+    return v, d
+
+
+def test_tc_weights_are_the_digits_of_the_encoded_weights(fg):
+    """tc_weights' tiles hold the balanced base-256 digits of every encoded
+    weight (in [-128, 127], summing back to the residue) and zeros in the
+    padding rows and ciphertexts; two row tiles (the second ragged) and G = 9
+    (three K steps, the last ragged)."""
     N, L = 2048, 2
     c = ctx(fg, N, L)
-    g = c.geom(24, 5, 8, 8, 3, 1, 1)
+    g = c.geom(180, 130, 8, 8, 3, 1, 1)
+    assert g.G == 9
     wh = c.encode_weights(g, dev(synth.weights(3, (g.Cout, g.Cin, g.k, g.k)), torch.int8))
-    got = c.tc_weights(g, wh).cpu().numpy()
-    want = wh.cpu().numpy().reshape(L, g.Cout, g.G, N // 8, 2, 4).transpose(0, 3, 2, 4, 1, 5)
-    assert (got == want).all()
+    wt = c.tc_weights(g, wh)
+    assert wt.numel() * 2 == fg._lib.fl_tc_weights_bytes(c.h, ctypes.byref(g))
+    v, d = decode_tc_weights(wt, L, g.Cout, g.G, N)
+    w = wh.cpu().numpy().view(np.uint32).astype(np.int64)
+    assert (v[:, :g.Cout, :g.G] == w).all()
+    assert (d[:, :g.Cout, g.G:] == 0).all() and (d[:, g.Cout:] == 0).all()
 
 
 def test_tc_form_refuses_g_beyond_the_exact_range(fg):
@@ -240,5 +264,11 @@ def test_tc_form_refuses_g_beyond_the_exact_range(fg):
     wh = torch.zeros((L, g.Cout, g.G, N), dtype=torch.int32, device="cuda")
     ct = torch.zeros((1, g.n_in, 2, L, N), dtype=torch.int32, device="cuda")
     with pytest.raises(fg.FlashError, match="exact"):
-        c.he_conv2d_tc(g, c.tc_weights(g, wh), ct)
+        c.tc_weights(g, wh)
+    # the C entry points refuse it too, before touching any buffer
+    buf = torch.zeros(1 << 20, dtype=torch.int32, device="cuda")
+    p = ctypes.c_void_p(buf.data_ptr())
+    assert fg._lib.fl_tc_weights_bytes(c.h, ctypes.byref(g)) == 0
+    assert fg._lib.fl_tc_weights(c.h, ctypes.byref(g), p, p, None) == fg.FL_ERR_SHAPE
+    assert fg._lib.fl_he_conv2d_tc(c.h, ctypes.byref(g), 1, p, p, None, p, p, buf.numel() * 4, None) != 0
     assert int(c.he_conv2d(g, wh, ct).abs().sum()) == 0

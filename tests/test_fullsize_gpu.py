@@ -109,8 +109,9 @@ def test_tc_form_full_stack_in_the_bench_configuration(fg, oracle, config):
     c = fg.Context(wl.N, wl.L)
     specs, filters = _bench_layers(c, wl, 7)
     assert max(sp["g"].G for sp in specs) == (52 if config == "resnet50-b8" else 10)
+    ws = c.tc_workspace(max((sp["g"] for sp in specs), key=lambda g: g.n_in), wl.B)  # shared, as bench.py does
     for sp in specs:
-        sp["ws"] = c.tc_workspace(sp["g"], wl.B)
+        sp["ws"] = ws
         sp["w_tc"] = c.tc_weights(sp["g"], sp["w_hat"])
         del sp["w_hat"]
 
