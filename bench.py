@@ -24,6 +24,11 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The batched ResNet-50 stack in the tensor-core form holds most of the device
+# (weight tiles, outputs, masks of all 53 layers); growable segments keep
+# freed blocks of one size usable for allocations of another.  Read when
+# CUDA starts.
+os.environ.setdefault("PYTORCH_ALLOC_CONF", "expandable_segments:True")
 
 from paper_2401_16732_gb300 import synth  # noqa: E402
 from paper_2401_16732_gb300.workloads import WORKLOADS, Workload  # noqa: E402
@@ -821,8 +826,10 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
     hbm_line = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_source": peak_kind, "traffic": traffic,
                 "kernel_source_sha256_16": kernel_source_hash(tuned["kernel"])}
+    # traffic is the kernel's DRAM bytes, reported whichever roofline binds
     alu_line = {"bound": "alu", "achieved": achieved_bfly / 1e12, "peak": ALU_BFLY_PEAK / 1e12,
-                "unit": "T butterflies/s", "frac": achieved_bfly / ALU_BFLY_PEAK, "peak_source": alu_src}
+                "unit": "T butterflies/s", "frac": achieved_bfly / ALU_BFLY_PEAK, "peak_source": alu_src,
+                "traffic": traffic, "kernel_source_sha256_16": kernel_source_hash(tuned["kernel"])}
     main, other = (hbm_line, alu_line) if hbm_floor >= alu_floor else (alu_line, hbm_line)
     roof = dict(main)
     roof.update({"kernel": kname, "kernel_ms_per_step": kern["conv"], "algorithmic_bytes_per_step": conv_bytes,
@@ -938,12 +945,14 @@ def run_batched(args, local_rank):
     events, clocks during the timed region), at up to 5 timed steps, without
     the end-to-end and CPU legs.  Returns {config: {form: summary}}."""
     import argparse as _ap
+    import gc
 
     import torch
     out = {}
     for cfg, form in BATCHED:
         a = _ap.Namespace(**vars(args))
         a.config, a.form, a.steps, a.skip_e2e, a.skip_cpu, a.no_batched = cfg, form, min(args.steps, 5), True, True, True
+        gc.collect()  # the previous workload's buffers (also after a failed one)
         torch.cuda.empty_cache()
         try:
             ln = run_gpu(a, WORKLOADS[cfg], 0, 1, local_rank, emit=False)

@@ -27,8 +27,9 @@ def fg():
     return flashgpu
 
 
-def _bench_layers(c, wl, seed):
-    """Every layer of a workload as bench.py sets it up: encoded weights,
+def _bench_layers(c, wl, seed, tc=False):
+    """Every layer of a workload as bench.py sets it up: encoded weights (as
+    tensor-core weight tiles, made right after the encoding, when tc),
     fresh uniform-residue inputs and masks of the layer's shape, and output
     buffers; returns the layer specs and the int8 filters."""
     N, L, B = wl.N, wl.L, wl.B
@@ -36,7 +37,10 @@ def _bench_layers(c, wl, seed):
     for li, shape in enumerate(wl.layers):
         g = c.geom(*shape)
         w = synth.weights(seed, (g.Cout, g.Cin, g.k, g.k), li)
-        specs.append({"g": g, "w_hat": c.encode_weights(g, torch.from_numpy(w).to(torch.int8).cuda()),
+        w_hat = c.encode_weights(g, torch.from_numpy(w).to(torch.int8).cuda())
+        wk = {"w_tc": c.tc_weights(g, w_hat)} if tc else {"w_hat": w_hat}
+        del w_hat
+        specs.append({"g": g, **wk,
                       "ct_in": synth.device_uniform_residues(seed, c.primes, (B, g.n_in, 2, L, N), li),
                       "r": synth.device_masks(seed, (B, g.n_out, N), T, li),
                       "out": torch.empty((B, g.n_out, 2, L, N), dtype=torch.int32, device="cuda")})
@@ -106,14 +110,13 @@ def test_tc_form_full_stack_in_the_bench_configuration(fg, oracle, config):
     mask; one CUDA graph per step), against the oracle on two output channels
     of every layer.  ResNet-50's layers reach G = 52 input ciphertexts."""
     wl = WORKLOADS[config]
+    torch.cuda.empty_cache()  # ResNet-50's weight tiles, outputs and masks take most of the device
     c = fg.Context(wl.N, wl.L)
-    specs, filters = _bench_layers(c, wl, 7)
+    specs, filters = _bench_layers(c, wl, 7, tc=True)
     assert max(sp["g"].G for sp in specs) == (52 if config == "resnet50-b8" else 10)
     ws = c.tc_workspace(max((sp["g"] for sp in specs), key=lambda g: g.n_in), wl.B)  # shared, as bench.py does
     for sp in specs:
         sp["ws"] = ws
-        sp["w_tc"] = c.tc_weights(sp["g"], sp["w_hat"])
-        del sp["w_hat"]
 
     def step(st):
         for sp in specs:
