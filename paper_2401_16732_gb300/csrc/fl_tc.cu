@@ -7,9 +7,13 @@
 //
 // For limb l and slot u the contraction is a small matrix product mod q_l:
 //   Y[i][col] = sum_g W[i][g] * X[g][col]   (mod q),  col = (image, band, component).
-// Balanced base-256 digits.  A residue v < 2^31 is v = sum_a d_a(v) 256^a with
-// d_a(v) = byte_a(v + 0x80808080) - 128 in [-128, 127]; every digit is exact in
-// fp16.  With X'_a = 256^a X mod q (a = 0..3):
+// Balanced base-256 digits.  A value v < 0x7F7F7F80 (so that v + 0x80808080
+// does not wrap) is v = sum_a d_a(v) 256^a with d_a(v) = byte_a(v +
+// 0x80808080) - 128 in [-128, 127]; every digit is exact in fp16.  The
+// weights and inputs are residues below q < 2^30; X'_a = 256^a X mod q
+// (a = 0..3) is a Shoup product of X < q, which lies below 1.25 q (the
+// quotient estimate is one short only when the remainder is below X / 2^32
+// of q), so every value split here is in range.
 //   W X = sum_a d_a(W) 256^a X = sum_a d_a(W) X'_a  (mod q)
 //       = sum_e 256^e P_e,   P_e = sum_(g, a) d_a(W[g]) d_e(X'_a[g]).
 // So per slot one matrix product with K = (g, a) (4G) and N = (col, e) (4 per
@@ -20,8 +24,8 @@
 // pattern minus 0x4B400000 is then P_e itself.
 // Recombination mod q on the CUDA cores: Y = sum_e 256^e P_e (|Y| < 2^46.1)
 // is known exactly mod 2^32 from the bit patterns; its quotient k =
-// round(Y / q) comes from an fp32 estimate of Y (error below 2^24.4, and
-// every prime of a context lies above 2^29, so k is within 0.55 of Y / q),
+// round(Y / q) comes from an fp32 estimate of Y (error below 2^23.6, and
+// every prime of a context lies above 2^29, so k is within 0.53 of Y / q),
 // and Y - k q + q lies in [0, 2q), the input range of the inverse NTT,
 // computed exactly in 32-bit arithmetic.
 //
@@ -226,22 +230,20 @@ __device__ __forceinline__ uint2 digits4(uint32_t v) {
 
 // Y - k q + q in [0, 2q) for Y = sum_e 256^e P_e, from the accumulator bit
 // patterns b[e] = bits(3 * 2^22 + P_e), b[e] in [2^23, 2^24].  The fp32
-// estimate of Y sums the biased accumulators by three fmas, which round by
-// at most 2^8, 2^16 and 2^24 (the last sum may reach 2^48 + 2^40), and
-// subtracts the biases' sum 3 * 2^22 * 0x01010101, itself rounded by 2^22
-// (the subtraction is exact: both operands are multiples of 2^24 and the
-// difference is below 2^47).  So the estimate is within 2^24.4 of Y, i.e.
-// within 0.042 q for q > 2^29, and with the final rounding to an integer
-// (0.5) and the rounding of 1/q (below 0.005 at |Y / q| < 2^16.1), k is
-// within 0.55 of Y / q.
-// nq = -q mod 2^32; c = FP_BIAS * q + q - FP_BIAS * 0x01010101 mod 2^32 (the
-// biases of k and of the four P_e).
+// estimate of Y leaves out 256^0 P_0 (|P_0| <= 2^22) and takes the biases of
+// e = 1..3 out first: b[3] 2^24 - 3 * 2^22 (2^8 + 2^16 + 2^24) is exact (the
+// constant has 18 significant bits, the difference is a multiple of 2^24
+// below 2^46.1), and the two fmas that add b[2] 2^16 and b[1] 2^8 round by at
+// most 2^22 each.  So the estimate is within 2^23.6 of Y, i.e. within
+// 0.021 q for q > 2^29, and with the final rounding to an integer (0.5) and
+// the rounding of 1/q (below 0.005 at |Y / q| < 2^16.1), k is within 0.53 of
+// Y / q.
 __device__ __forceinline__ uint32_t recombine(const uint32_t* b, float qinv, uint32_t nq, uint32_t c) {
-  constexpr float kBiasSum = (float)(12582912.0 * 16843009.0);  // the exact integer, rounded once
-  const float y = fmaf(__uint_as_float(b[3]), 16777216.f,
-                       fmaf(__uint_as_float(b[2]), 65536.f, fmaf(__uint_as_float(b[1]), 256.f, __uint_as_float(b[0]))));
-  const uint32_t kb = __float_as_uint(fmaf(y - kBiasSum, qinv, 12582912.f));  // FP_BIAS + round(Y / q)
-  const uint32_t lo = b[0] + (b[1] << 8) + (b[2] << 16) + (b[3] << 24);     // Y + FP_BIAS * 0x01010101 mod 2^32
+  constexpr float kBias123 = (float)(12582912.0 * 16843008.0);  // exact
+  const float y = fmaf(__uint_as_float(b[1]), 256.f,
+                       fmaf(__uint_as_float(b[2]), 65536.f, fmaf(__uint_as_float(b[3]), 16777216.f, -kBias123)));
+  const uint32_t kb = __float_as_uint(fmaf(y, qinv, 12582912.f));  // FP_BIAS + round(Y / q)
+  const uint32_t lo = b[0] + (b[1] << 8) + (b[2] << 16) + (b[3] << 24);  // Y + FP_BIAS * 0x01010101 mod 2^32
   return kb * nq + lo + c;
 }
 }  // namespace
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t x = *reinterpret_cast<const uint32_t*>(tsm + OFF_RAWB + r * RAWB_STEP + b_off);
       // (the copies filled zeros beyond G, and the digits of 0 are zeros)
       const uint32_t y0 = x + 0x80808080u;
-      const uint32_t y1 = shoup_mul(x, 256u, w1s, q) + 0x80808080u;  // X'_a in [0, 2q), congruent to 256^a X
+      const uint32_t y1 = shoup_mul(x, 256u, w1s, q) + 0x80808080u;  // X'_a < 1.25 q, congruent to 256^a X
       const uint32_t y2 = shoup_mul(x, 65536u, w2s, q) + 0x80808080u;
       const uint32_t y3 = shoup_mul(x, 16777216u, w3s, q) + 0x80808080u;
       uint2 dd[4];
@@ -454,8 +456,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t ta = tbase + ((uint32_t)(32 * qd) << 16);
     // Groups come in pairs (8 slots, one 32-byte sector of every output row):
     // the even group's results wait in shared memory for the odd one's.
-    constexpr int HS = 32 * TC_EPI_WARPS;  // hold[local column][slot][epilogue thread]
-    uint32_t* hold = reinterpret_cast<uint32_t*>(tsm + OFF_HOLD) + (tid - 32 * TC_PROD_WARPS);
+    constexpr int HS = 32 * TC_EPI_WARPS;  // hold[local column][epilogue thread], the 4 slots of a group
+    uint4* hold = reinterpret_cast<uint4*>(tsm + OFF_HOLD) + (tid - 32 * TC_PROD_WARPS);
+    const size_t row_off = (size_t)(i0 + rrow) * rowstride;  // this lane's output channel, column offsets apart
     // Every accumulator of a buffer starts at 3 * 2^22: this warp writes the
     // bias into its lanes and columns (column chunk p of every slot) once it
     // has read them, and hands the buffer back to the MMA warp.
@@ -498,14 +501,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int s = 0; s < TC_U; ++s) o[s] = recombine(&v[s][4 * cc2], qinv, nq, cfix);
           if (ab == 0) {
-#pragma unroll
-            for (int s = 0; s < TC_U; ++s) hold[(cl * TC_U + s) * HS] = o[s];
+            hold[cl * HS] = make_uint4(o[0], o[1], o[2], o[3]);
           } else {
             const long long co = colout[c];
             if (row_ok && co >= 0) {
-              uint4* dst = reinterpret_cast<uint4*>(y_hat + co + (size_t)(i0 + rrow) * rowstride + u0 - TC_U);
-              __stcs(dst, make_uint4(hold[(cl * TC_U) * HS], hold[(cl * TC_U + 1) * HS], hold[(cl * TC_U + 2) * HS],
-                                     hold[(cl * TC_U + 3) * HS]));
+              uint4* dst = reinterpret_cast<uint4*>(y_hat + (size_t)co + row_off + u0 - TC_U);
+              __stcs(dst, hold[cl * HS]);
               __stcs(dst + 1, make_uint4(o[0], o[1], o[2], o[3]));
             }
           }
