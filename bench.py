@@ -460,7 +460,7 @@ def share_tc_workspace(ctx, layers, B):
     given layers: they run one after another on one stream, and a workspace
     larger than a layer needs is valid for it."""
     if layers:
-        ws = ctx.tc_workspace(max((lay["g"] for lay in layers), key=lambda g: g.n_in), B)
+        ws = ctx.tc_workspace(max((lay["g"] for lay in layers), key=lambda g: ctx.tc_workspace_bytes(g, B)), B)
         for lay in layers:
             lay["ws"] = ws
 
@@ -572,9 +572,9 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
                 ev[0].record(stream)
                 ctx.he_conv2d_ntt_inputs(lay["g"], lay["ct"], lay["ws"], stream=stream)
                 ev[1].record(stream)
-                ctx.he_conv2d_tc_from_ntt(lay["g"], B, lay["w_tc"], lay["ws"], o, stream=stream)
+                ctx.he_conv2d_tc_from_ntt(lay["g"], B, lay["w_tc"], lay["ws"], stream=stream)
                 ev[2].record(stream)
-                ctx.intt_mask_outputs(lay["g"], o, r=lay["r"], stream=stream)
+                ctx.intt_mask_outputs(lay["g"], lay["ws"], o, r=lay["r"], stream=stream)
                 ev[3].record(stream)
             return
         if events is not None and args.form != "tc":
@@ -589,9 +589,10 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
                 events[2].record(stream)
             return
         if args.form == "tc":
-            # per layer: input NTT, tensor-core contraction into the output
-            # buffer (NTT domain), in-place inverse NTT + mask of every output
-            # row; with `events`, each stage of each layer is bracketed
+            # per layer: input NTT, tensor-core contraction into the
+            # workspace's scratch (NTT domain, slot-tiled), inverse NTT + mask
+            # of every output row into the outputs; with `events`, each stage
+            # of each layer is bracketed
             # (events[k] = 4 events per layer) and the stages are separate calls
             for k, (lay, o) in enumerate(zip(layers, outs)):
                 if events is None:
@@ -602,9 +603,9 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
                 ev[0].record(stream)
                 ctx.he_conv2d_ntt_inputs(lay["g"], lay["ct"], lay["ws"], stream=stream)
                 ev[1].record(stream)
-                ctx.he_conv2d_tc_from_ntt(lay["g"], B, lay["w_hat"], lay["ws"], o, stream=stream)
+                ctx.he_conv2d_tc_from_ntt(lay["g"], B, lay["w_hat"], lay["ws"], stream=stream)
                 ev[2].record(stream)
-                ctx.intt_mask_outputs(lay["g"], o, r=lay["r"], stream=stream)
+                ctx.intt_mask_outputs(lay["g"], lay["ws"], o, r=lay["r"], stream=stream)
                 ev[3].record(stream)
             return
         if args.form == "otf":
@@ -863,7 +864,7 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
         kname = roof["kernel"]
     if tuned["kernel"] == "tc":
         # two kernels per layer after the input NTT: the tensor-core
-        # contraction (NTT-domain outputs to HBM) and the in-place inverse NTT +
+        # contraction (NTT-domain outputs to the scratch in HBM) and the inverse NTT +
         # mask of every output row; each is timed with its own events
         tpk, tpk_src = tensor_peak()
         digit_flops = 2 * 16 * macs  # 16 fp16 digit products per modular multiply-add
@@ -884,7 +885,7 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
                     "frac": intt_bytes / intt_s / 1e9 / hbm, "peak_source": peak_kind}
         intt_alu = dict(alu_line, achieved=bfly / intt_s / 1e12, frac=bfly / intt_s / ALU_BFLY_PEAK)
         i_main, i_other = (intt_hbm, intt_alu) if intt_bytes / (hbm * 1e9) >= bfly / ALU_BFLY_PEAK else (intt_alu, intt_hbm)
-        intt_line = dict(i_main, kernel="k_intt_mask_rows (in-place inverse NTT + mask of every output row)",
+        intt_line = dict(i_main, kernel="k_intt_mask_rows (inverse NTT + mask of every output row, gathered from the scratch)",
                          kernel_ms_per_step=kern["intt"], algorithmic_bytes_per_step=intt_bytes,
                          algorithmic_butterflies_per_step=bfly, other_roofline=i_other,
                          traffic=traffic_of(args.config, "intt_rows"),
@@ -929,21 +930,26 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
         return line
     if world == 1 and args.config == "resnet18" and args.form == "ntt" and not args.no_batched:
         del layers, graph, arr, ws
-        line["batched"] = run_batched(args, local_rank)
+        line["batched"] = run_batched(args, local_rank, {args.config: line["value"]})
     print(json.dumps(line), flush=True)
     return 0
 
 
-BATCHED = (("resnet18-b64", "ntt"), ("resnet18-b64", "tc"), ("resnet18-b64", "auto"),
+# (the default workload's tensor-core form too, beside the line's plain form)
+BATCHED = (("resnet18", "tc"),
+           ("resnet18-b64", "ntt"), ("resnet18-b64", "tc"), ("resnet18-b64", "auto"),
            ("resnet50-b8", "ntt"), ("resnet50-b8", "tc"), ("resnet50-b8", "auto"))
 
 
-def run_batched(args, local_rank):
+def run_batched(args, local_rank, plain_values=None):
     """The batched stacks (ResNet-18 CIFAR B=64, ResNet-50 ImageNet B=8) in the
-    plain form, the tensor-core form and the autotuned per-layer mix, each
+    plain form, the tensor-core form and the autotuned per-layer mix, and the
+    default workload (ResNet-18 CIFAR B=1) in the tensor-core form, each
     measured as the default line is (one CUDA graph per step, device-side
     events, clocks during the timed region), at up to 5 timed steps, without
-    the end-to-end and CPU legs.  Returns {config: {form: summary}}."""
+    the end-to-end and CPU legs; plain_values gives the plain form's value of
+    a config measured elsewhere (the default line's own workload).  Returns
+    {config: {form: summary}}."""
     import argparse as _ap
     import gc
 
@@ -981,10 +987,11 @@ def run_batched(args, local_rank):
         del ln
     torch.cuda.empty_cache()
     for cfg, forms in out.items():
-        if "ntt" in forms and "value" in forms["ntt"]:
+        plain = forms["ntt"].get("value") if "ntt" in forms else (plain_values or {}).get(cfg)
+        if plain:
             for f, summ in forms.items():
                 if f != "ntt" and "value" in summ:
-                    summ["speedup_over_plain"] = summ["value"] / forms["ntt"]["value"]
+                    summ["speedup_over_plain"] = summ["value"] / plain
     return out
 
 

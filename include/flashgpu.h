@@ -253,15 +253,21 @@ int fl_he_conv2d_direct(fl_ctx *ctx, const fl_conv_geom *geom, int B, const int8
  *   the fly.
  * - Unlike the plain form it is not fused with the inverse NTT: a tile spans
  *   128 output channels of 8 slots, while the inverse NTT needs every slot of
- *   one output.  So the NTT-domain outputs go through ct_out_dev, and a
- *   second kernel transforms every output row in place and adds the mask.
+ *   one output.  So the NTT-domain outputs go through the workspace, in an
+ *   order where each tile's results are contiguous runs, and a second kernel
+ *   gathers every output row from there, transforms it, adds the mask and
+ *   writes ct_out_dev.
  * - Every internal wait is bounded (2 s); a wait that runs out sets the
  *   context's tensor-core error word (fl_tc_error).
  * G > FL_TC_MAX_G: FL_ERR_SHAPE. */
 #define FL_TC_MAX_G 64
 /* Workspace of fl_he_conv2d_tc: the NTT images of the inputs (as for
  * fl_he_conv2d), then their copy in slot groups of 4 ([L][N/4][B][n_in][2][4])
- * that the contraction reads: 2 * B*n_in*2*L*N*4 bytes. */
+ * that the contraction reads, then the NTT-domain outputs in slot-tiled
+ * order ([L][N/8][R][8], R = column * Cout + output channel, column =
+ * (image, band, component)) that the inverse NTT gathers:
+ * 2 * B*n_in*2*L*N*4 + B*n_out*2*L*N*4 bytes.  The output ciphertexts must
+ * not overlap it. */
 size_t fl_he_conv2d_tc_workspace_bytes(const fl_ctx *ctx, const fl_conv_geom *geom, int B);
 /* Bytes of the tensor-core weight tiles of one layer (fl_tc_weights):
  * L * ceil(Cout/128) * (N/4) * ceil(G/4) * 16384; 0 when G > FL_TC_MAX_G
@@ -288,17 +294,18 @@ int fl_he_conv2d_tc(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint16_t
 
 /* The stages of fl_he_conv2d_tc after the input NTT, as separate calls
  * (same results).  fl_he_conv2d_tc_from_ntt: the tensor-core contraction
- * from a workspace (fl_he_conv2d_tc_workspace_bytes) whose first half
+ * from a workspace (fl_he_conv2d_tc_workspace_bytes) whose first part
  * fl_he_conv2d_ntt_inputs filled; it writes the slot-tiled copy of the
- * inputs into the second half, and ct_out_dev receives
- * the NTT-domain outputs (values in [0, 2 q_l)).  fl_intt_mask_outputs: the
- * in-place inverse NTT of B * n_out such NTT-domain output ciphertexts
- * (whose weights carried N^-1) plus Delta * r on c0 when r_dev is not NULL;
- * the result is fl_he_conv2d_mask's. */
+ * inputs into the second part and the NTT-domain outputs (values in
+ * [0, 2 q_l), slot-tiled) into the third.  fl_intt_mask_outputs: the inverse
+ * NTT of those B * n_out output ciphertexts (whose weights carried N^-1),
+ * gathered from the workspace, plus Delta * r on c0 when r_dev is not NULL,
+ * into ct_out_dev (not overlapping the workspace); the result is
+ * fl_he_conv2d_mask's. */
 int fl_he_conv2d_tc_from_ntt(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint16_t *w_tc_dev,
-                             void *workspace_dev, size_t workspace_bytes, uint32_t *ct_out_dev, void *stream);
-int fl_intt_mask_outputs(fl_ctx *ctx, const fl_conv_geom *geom, int B, const uint32_t *r_dev, uint32_t *ct_out_dev,
-                         void *stream);
+                             void *workspace_dev, size_t workspace_bytes, void *stream);
+int fl_intt_mask_outputs(fl_ctx *ctx, const fl_conv_geom *geom, int B, const void *workspace_dev,
+                         size_t workspace_bytes, const uint32_t *r_dev, uint32_t *ct_out_dev, void *stream);
 
 /* Synchronise `stream`, read the tensor-core form's error word into
  * *error_host and clear it.  FL_OK when it is 0; FL_ERR_TIMEOUT when a

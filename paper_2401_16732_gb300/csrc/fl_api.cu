@@ -689,11 +689,15 @@ int fl_he_conv2d_otf(fl_ctx* ctx, const fl_conv_geom* geom, int B, const int8_t*
 }
 
 size_t fl_he_conv2d_tc_workspace_bytes(const fl_ctx* ctx, const fl_conv_geom* geom, int B) {
-  return 2 * fl_he_conv2d_workspace_bytes(ctx, geom, B);
+  if (!ctx || !geom || B < 0) return 0;
+  return 2 * fl_he_conv2d_workspace_bytes(ctx, geom, B) +
+         4 * fl::tc_scratch_words(B, fl::ConvDims{geom->Cout, geom->G, geom->n_in, geom->n_out, geom->bands}, ctx->L,
+                                  ctx->N);
 }
 
 // Checks shared by the tensor-core entry points; the workspace holds the NTT
-// images of the inputs, then their slot-tiled copy.
+// images of the inputs, their slot-tiled copy, then the NTT-domain outputs
+// in slot-tiled order (the scratch).
 static int tc_checks(fl_ctx* ctx, const fl_conv_geom* geom, int B, size_t workspace_bytes) {
   int rc;
   if ((rc = conv_checks(ctx, geom, B, workspace_bytes))) return rc;
@@ -705,20 +709,42 @@ static int tc_checks(fl_ctx* ctx, const fl_conv_geom* geom, int B, size_t worksp
   return FL_OK;
 }
 
-// slot-tiled copy of the NTT images (second half of the workspace), then the
-// tensor-core contraction; `pdl`: the contraction follows the copy as a
-// programmatic dependent launch
+static uint32_t* tc_scratch(fl_ctx* ctx, const fl_conv_geom* geom, int B, const void* ws) {
+  return (uint32_t*)ws + 2 * (fl_he_conv2d_workspace_bytes(ctx, geom, B) / 4);
+}
+
+// slot-tiled copy of the NTT images (the workspace's second part), then the
+// tensor-core contraction into the scratch (its third part); the
+// contraction follows the copy as a programmatic dependent launch
 static int stage_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint16_t* w_tc_dev, const void* ws,
-                    uint32_t* ct_out_dev, cudaStream_t st) {
+                    cudaStream_t st) {
   const uint32_t* c_hat = (const uint32_t*)ws;
   uint32_t* c_tc = (uint32_t*)ws + fl_he_conv2d_workspace_bytes(ctx, geom, B) / 4;
   int rc;
   if ((rc = launched(fl::launch_tc_inputs(c_hat, c_tc, B, geom->n_in, ctx->L, ctx->N, st), "tensor-core input layout")))
     return rc;
   return launched(fl::launch_conv_tc(B, fl::ConvDims{geom->Cout, geom->G, geom->n_in, geom->n_out, geom->bands},
-                                     w_tc_dev, c_tc, ct_out_dev, ctx->N, ctx->cc, ctx->tc_err, st, true,
-                                     ctx->tc_tile),
+                                     w_tc_dev, c_tc, tc_scratch(ctx, geom, B, ws), ctx->N, ctx->cc, ctx->tc_err, st,
+                                     true, ctx->tc_tile),
                   "tensor-core contraction");
+}
+
+// the inverse NTT + mask of every scratch row into the output ciphertexts,
+// which must not overlap the workspace they are read from
+static int stage_intt_rows(fl_ctx* ctx, const fl_conv_geom* geom, int B, const void* ws, const uint32_t* r_dev,
+                           uint32_t* ct_out_dev, cudaStream_t st, bool pdl) {
+  if ((long long)2 * B * geom->bands * geom->Cout > 0x7fffffffLL)
+    return fail(FL_ERR_ARG, "B=%d: too many output rows for one launch", B);
+  const char* a = (const char*)ws;
+  const char* b = (const char*)ct_out_dev;
+  const size_t ws_bytes = fl_he_conv2d_tc_workspace_bytes(ctx, geom, B),
+               out_bytes = (size_t)B * geom->n_out * 2 * ctx->L * ctx->N * 4;
+  if (a < b + out_bytes && b < a + ws_bytes) return fail(FL_ERR_ARG, "output ciphertexts overlap the workspace");
+  return launched(fl::launch_intt_mask_rows(ctx->logN, B,
+                                            fl::ConvDims{geom->Cout, geom->G, geom->n_in, geom->n_out, geom->bands},
+                                            tc_scratch(ctx, geom, B, ws), ct_out_dev, r_dev, ctx->tw, ctx->cc, st, pdl,
+                                            ctx->ntt_plan),
+                  "output inverse ntt");
 }
 
 int fl_he_conv2d_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint16_t* w_tc_dev, const uint32_t* ct_in_dev,
@@ -731,34 +757,27 @@ int fl_he_conv2d_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint16_t
   if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = stage_ntt(ctx, geom, B, ct_in_dev, workspace_dev, st))) return rc;
-  if ((rc = stage_tc(ctx, geom, B, w_tc_dev, workspace_dev, ct_out_dev, st))) return rc;
-  return launched(fl::launch_intt_mask_rows(ctx->logN, (long long)B * geom->n_out * 2 * ctx->L, ct_out_dev, r_dev,
-                                            ctx->tw, ctx->cc, st, true, ctx->ntt_plan),
-                  "output inverse ntt");
+  if ((rc = stage_tc(ctx, geom, B, w_tc_dev, workspace_dev, st))) return rc;
+  return stage_intt_rows(ctx, geom, B, workspace_dev, r_dev, ct_out_dev, st, true);
 }
 
 int fl_he_conv2d_tc_from_ntt(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint16_t* w_tc_dev,
-                             void* workspace_dev, size_t workspace_bytes, uint32_t* ct_out_dev, void* stream) {
+                             void* workspace_dev, size_t workspace_bytes, void* stream) {
   int rc;
   if ((rc = tc_checks(ctx, geom, B, workspace_bytes))) return rc;
   if (B == 0) return FL_OK;
-  if ((rc = check_ptrs({w_tc_dev, workspace_dev, ct_out_dev}))) return rc;
-  return stage_tc(ctx, geom, B, w_tc_dev, workspace_dev, ct_out_dev, (cudaStream_t)stream);
+  if ((rc = check_ptrs({w_tc_dev, workspace_dev}))) return rc;
+  return stage_tc(ctx, geom, B, w_tc_dev, workspace_dev, (cudaStream_t)stream);
 }
 
-int fl_intt_mask_outputs(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint32_t* r_dev, uint32_t* ct_out_dev,
-                         void* stream) {
+int fl_intt_mask_outputs(fl_ctx* ctx, const fl_conv_geom* geom, int B, const void* workspace_dev,
+                         size_t workspace_bytes, const uint32_t* r_dev, uint32_t* ct_out_dev, void* stream) {
   int rc;
-  if ((rc = check_ctx(ctx)) || (rc = check_geom(ctx, geom))) return rc;
-  if (B < 0) return fail(FL_ERR_ARG, "B=%d", B);
+  if ((rc = tc_checks(ctx, geom, B, workspace_bytes))) return rc;
   if (B == 0) return FL_OK;
-  if ((rc = check_ptrs({ct_out_dev}))) return rc;
+  if ((rc = check_ptrs({workspace_dev, ct_out_dev}))) return rc;
   if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
-  if ((long long)B * geom->n_out * 2 * ctx->L > 0x7fffffffLL)
-    return fail(FL_ERR_ARG, "B=%d: too many output rows for one launch", B);
-  return launched(fl::launch_intt_mask_rows(ctx->logN, (long long)B * geom->n_out * 2 * ctx->L, ct_out_dev, r_dev,
-                                            ctx->tw, ctx->cc, (cudaStream_t)stream, false, ctx->ntt_plan),
-                  "output inverse ntt");
+  return stage_intt_rows(ctx, geom, B, workspace_dev, r_dev, ct_out_dev, (cudaStream_t)stream, false);
 }
 
 size_t fl_tc_weights_bytes(const fl_ctx* ctx, const fl_conv_geom* geom) {

@@ -410,13 +410,14 @@ __device__ __forceinline__ void ntt_forward_to_smem(uint32_t* s, const uint32_t*
 // part (several polynomials may be transformed side by side by disjoint
 // thread groups sharing one barrier).
 // gsrc: when not null, the first pass reads the thread's 32 coefficients
-// straight from this global row (natural order) instead of from `s`; every
-// such read happens before the first barrier, so the epilogue may write the
-// result over gsrc in place.
+// straight from global memory instead of from `s`: the row's coefficients
+// 8k .. 8k + 7 (natural order) are the 8 words at gsrc + k * gchunk (gchunk
+// = 8 for a contiguous row).  Every such read happens before the first
+// barrier, so the epilogue may write the result over gsrc in place.
 template <int LOGN, class Epi, class Bar, bool SCALE = true, int R1 = Plan<LOGN>::R1>
 __device__ __forceinline__ void intt_from_smem_bar(uint32_t* s, const uint32_t* __restrict__ tw_l,
                                                    const LimbConst& lc, int tid, Epi epi, Bar bar,
-                                                   const uint32_t* gsrc = nullptr) {
+                                                   const uint32_t* gsrc = nullptr, size_t gchunk = 8) {
   constexpr int N = 1 << LOGN, T = N / 32, R2 = LOGN - 5 - R1;
   static_assert(plan_ok(LOGN, R1), "pass plan");
   const uint2* f = reinterpret_cast<const uint2*>(tw_l) + TW_INV * N;
@@ -426,9 +427,11 @@ __device__ __forceinline__ void intt_from_smem_bar(uint32_t* s, const uint32_t* 
     uint32_t* p = s + tid * ROW;
     if (gsrc) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const uint4 x = reinterpret_cast<const uint4*>(gsrc + 32 * tid)[j];
-        v[4 * j] = x.x, v[4 * j + 1] = x.y, v[4 * j + 2] = x.z, v[4 * j + 3] = x.w;
+      for (int k = 0; k < 4; ++k) {
+        const uint4* src = reinterpret_cast<const uint4*>(gsrc + (size_t)(4 * tid + k) * gchunk);
+        const uint4 x0 = src[0], x1 = src[1];
+        v[8 * k] = x0.x, v[8 * k + 1] = x0.y, v[8 * k + 2] = x0.z, v[8 * k + 3] = x0.w;
+        v[8 * k + 4] = x1.x, v[8 * k + 5] = x1.y, v[8 * k + 6] = x1.z, v[8 * k + 7] = x1.w;
       }
     } else {
       lds_row(p, v);
@@ -453,9 +456,9 @@ __device__ __forceinline__ void intt_from_smem(uint32_t* s, const uint32_t* __re
 template <int LOGN, class Epi, int R1 = Plan<LOGN>::R1>
 __device__ __forceinline__ void intt_from_smem_unscaled(uint32_t* s, const uint32_t* __restrict__ tw_l,
                                                         const LimbConst& lc, int tid, Epi epi,
-                                                        const uint32_t* gsrc = nullptr) {
+                                                        const uint32_t* gsrc = nullptr, size_t gchunk = 8) {
   auto bar = [] { __syncthreads(); };
-  intt_from_smem_bar<LOGN, Epi, decltype(bar), false, R1>(s, tw_l, lc, tid, epi, bar, gsrc);
+  intt_from_smem_bar<LOGN, Epi, decltype(bar), false, R1>(s, tw_l, lc, tid, epi, bar, gsrc, gchunk);
 }
 
 }  // namespace fl

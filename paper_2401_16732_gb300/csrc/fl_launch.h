@@ -171,10 +171,15 @@ size_t conv_tc_smem_bytes();
 size_t tc_weights_bytes(int L, int Cout, int G, int N);
 cudaError_t launch_tc_weights(const uint32_t* w_hat, uint16_t* w_tc, int L, int Cout, int G, int N, cudaStream_t st);
 cudaError_t launch_tc_inputs(const uint32_t* c_hat, uint32_t* c_tc, int B, int n_in, int L, int N, cudaStream_t st);
-cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint16_t* w_tc, const uint32_t* c_hat, uint32_t* y_hat,
+// the contraction into the scratch y_sc[l][u / 8][column * Cout + i][u % 8]
+// (tc_scratch_words words), then the inverse NTT + mask of every scratch row
+// into the output ciphertexts y
+size_t tc_scratch_words(int B, const ConvDims& cd, int L, int N);
+cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint16_t* w_tc, const uint32_t* c_hat, uint32_t* y_sc,
                            int N, const CtxConst& cc, unsigned long long* err, cudaStream_t st, bool pdl, int gpc = 0);
-cudaError_t launch_intt_mask_rows(int logn, long long rows, uint32_t* y, const uint32_t* r, const uint32_t* tw,
-                                  const CtxConst& cc, cudaStream_t st, bool pdl, int r1 = 0);
+cudaError_t launch_intt_mask_rows(int logn, int B, const ConvDims& cd, const uint32_t* y_sc, uint32_t* y,
+                                  const uint32_t* r, const uint32_t* tw, const CtxConst& cc, cudaStream_t st, bool pdl,
+                                  int r1 = 0);
 // direct form (fl_direct.cu)
 cudaError_t launch_direct_setup(int logn);
 cudaError_t launch_direct(int logn, int B, const GeomDims& g, const int8_t* w, const uint32_t* ct, uint32_t* out,

@@ -41,12 +41,22 @@
 //                  MMA warp issues 4 MMAs M128 N64 K16 per K step, one per
 //                  slot, into one of two tensor-memory accumulator buffers;
 //                  8 epilogue warps load the accumulators, recombine, store
-//                  the NTT-domain outputs in [0, 2q) in 32-byte runs and
-//                  reset the buffer to the bias; every hand-off an mbarrier
-//                  with a bounded wait
-//   k_intt_mask_rows   in-place inverse NTT of every output row, + Delta*r on
-//                  component 0 (the encoded weights carry N^-1, so the
+//                  the NTT-domain outputs in [0, 2q) into a scratch buffer
+//                  in slot-tiled order and reset the buffer to the bias;
+//                  every hand-off an mbarrier with a bounded wait
+//   k_intt_mask_rows   inverse NTT of every output row, gathered from the
+//                  scratch, + Delta*r on component 0, written to the output
+//                  ciphertexts (the encoded weights carry N^-1, so the
 //                  transform is the unscaled one)
+//
+// The scratch order, y_sc[l][u / 8][R][u % 8] with R = column * Cout + i for
+// output channel i and column (image, band, component): a CTA's group pair
+// (8 slots) of 128 channels x 16 columns lands as 16 runs of 4 KB.  Written
+// straight into the output rows ([b][oct][c][l][u]) the same results are
+// 32-byte pieces of 2048 rows 256-512 KB apart, and those scattered writes
+// bounded the kernel at small G (no stores at all: 1.8x faster there).  The
+// price is on the inverse NTT's side: each thread gathers its 32
+// coefficients as four 32-byte pieces.
 #include <cuda_runtime.h>
 
 #include "fl_device.cuh"
@@ -266,20 +276,20 @@ __device__ __forceinline__ uint32_t recombine(const uint32_t* b, float qinv, uin
 //                        back into the buffer -> arrive acc_empty
 template <int GPC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_conv_tc(const uint16_t* __restrict__ w_tc, const uint32_t* __restrict__ c_hat, uint32_t* __restrict__ y_hat,
+    k_conv_tc(const uint16_t* __restrict__ w_tc, const uint32_t* __restrict__ c_hat, uint32_t* __restrict__ y_sc,
               ConvDims cd, int B, int N, CtxConst cc, unsigned long long* err) {
   extern __shared__ __align__(1024) uint8_t tsm[];
   __shared__ uint64_t a_full[TC_NS], tile_full[TC_NS], tile_empty[TC_NS], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
-  __shared__ long long colout[TC_CW];  // output word offset of each column, output channel 0; -1 outside
+  __shared__ long long colrow[TC_CW];  // scratch row R of each column at output channel 0; -1 outside
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cols = 2 * B * cd.bands, mtiles = (cd.Cout + TC_M - 1) / TC_M;
   const int mt = blockIdx.x % mtiles, i0 = mt * TC_M, col0 = (blockIdx.x / mtiles) * TC_CW;
   static_assert(GPC % 2 == 0, "the epilogue stores groups in pairs");
   const int l = blockIdx.z, grp0 = blockIdx.y * GPC, L = cc.L, G = cd.G;
   const LimbConst lc = cc.limb[l];
-  const size_t NL = (size_t)L * N, rowstride = (size_t)cd.bands * 2 * NL;
+  const size_t R_total = (size_t)cols * cd.Cout;  // scratch rows
   const int nch = (G + TC_GS - 1) / TC_GS, T = GPC * nch;
   const uint32_t sb = su32(tsm);
 
@@ -298,8 +308,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < TC_CW) {
-    const int colg = col0 + tid, bb = colg >> 1, b = bb / cd.bands, band = bb - b * cd.bands;
-    colout[tid] = colg < cols ? (long long)((((size_t)b * cd.n_out + band) * 2 + (colg & 1)) * NL + (size_t)l * N) : -1;
+    const int colg = col0 + tid;
+    colrow[tid] = colg < cols ? (long long)colg * cd.Cout : -1;
   }
   pdl_wait();  // the inputs come from the preceding forward NTT
   tc_fence_before();
@@ -458,7 +468,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // the even group's results wait in shared memory for the odd one's.
     constexpr int HS = 32 * TC_EPI_WARPS;  // hold[local column][epilogue thread], the 4 slots of a group
     uint4* hold = reinterpret_cast<uint4*>(tsm + OFF_HOLD) + (tid - 32 * TC_PROD_WARPS);
-    const size_t row_off = (size_t)(i0 + rrow) * rowstride;  // this lane's output channel, column offsets apart
+    // this lane's output channel; a group pair's 8 slots are 8 words of row R
+    uint32_t* scr = y_sc + (size_t)l * (N / 8) * R_total * 8 + (size_t)(i0 + rrow) * 8;
     // Every accumulator of a buffer starts at 3 * 2^22: this warp writes the
     // bias into its lanes and columns (column chunk p of every slot) once it
     // has read them, and hands the buffer back to the MMA warp.
@@ -480,7 +491,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 #pragma unroll 1
     for (int grp = 0; grp < GPC; ++grp) {
-      const int ab = grp & 1, u0 = 4 * (grp0 + grp);
+      const int ab = grp & 1;
+      const size_t u8 = (size_t)(grp0 + grp) >> 1;  // the group pair's 8 slots
       // the decision to stop is the warp's: the tensor-memory loads below are
       // warp-collective
       if (__any_sync(0xffffffffu, !mbar_wait_bounded(&acc_full[ab], (grp >> 1) & 1))) {
@@ -503,9 +515,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (ab == 0) {
             hold[cl * HS] = make_uint4(o[0], o[1], o[2], o[3]);
           } else {
-            const long long co = colout[c];
-            if (row_ok && co >= 0) {
-              uint4* dst = reinterpret_cast<uint4*>(y_hat + (size_t)co + row_off + u0 - TC_U);
+            const long long cr = colrow[c];
+            if (row_ok && cr >= 0) {
+              uint4* dst = reinterpret_cast<uint4*>(scr + (u8 * R_total + (size_t)cr) * 8);
               __stcs(dst, hold[cl * HS]);
               __stcs(dst + 1, make_uint4(o[0], o[1], o[2], o[3]));
             }
@@ -525,27 +537,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
-// Row r = (oct * 2 + c) * L + l of y (NTT domain, values in [0, 2q)) becomes
-// N times its inverse transform, + Delta_l * r[oct] when c == 0 and r is set.
-// Launched after the contraction as a programmatic dependent: it waits for
-// the contraction before its first read.
-template <int LOGN, int R1 = Plan<LOGN>::R1>
-__global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
-    k_intt_mask_rows(uint32_t* __restrict__ y, const uint32_t* __restrict__ r, const uint32_t* __restrict__ tw,
-                     CtxConst cc) {
+// Scratch row R = column * Cout + i (column = (image, band, component)) of
+// limb l = blockIdx.y, NTT domain with values in [0, 2q), in the order
+// y_sc[l][u / 8][R][u % 8], becomes N times its inverse transform, + Delta_l
+// * r[oct] when the component is 0 and r is set, in the output row
+// (b, oct = i * bands + band, component, l) of y.  Grid (R_total, L): the
+// CTAs that run together read neighbouring rows, so each 8-slot piece they
+// gather is part of a contiguous run.
+template <int LOGN, int R1>
+__global__ void __launch_bounds__((1 << LOGN) / 32)
+    k_intt_mask_rows(const uint32_t* __restrict__ y_sc, uint32_t* __restrict__ y, const uint32_t* __restrict__ r,
+                     const uint32_t* __restrict__ tw, int Cout, int bands, int n_out, CtxConst cc) {
   constexpr int N = 1 << LOGN;
   extern __shared__ uint32_t sm[];
-  const int L = cc.L;
-  const size_t row = blockIdx.x;
-  const int l = (int)(row % L), c = (int)((row / L) % 2);
-  const size_t oct = row / (2 * (size_t)L);
+  const int L = cc.L, l = blockIdx.y;
+  const size_t R = blockIdx.x, R_total = gridDim.x;
+  const int colg = (int)(R / Cout), i = (int)(R - (size_t)colg * Cout);
+  const int c = colg & 1, bb = colg >> 1, b = bb / bands, band = bb - b * bands;
+  const size_t oct = (size_t)b * n_out + (size_t)i * bands + band;  // output ciphertext, image-major
   const LimbConst lc = cc.limb[l];
-  uint32_t* p = y + row * N;
+  uint32_t* p = y + ((oct * 2 + c) * L + l) * N;
   pdl_wait();
-  // the first (radix-32) pass reads its coefficients from the row itself;
-  // every read precedes the first barrier, so the result may overwrite it
+  // the first (radix-32) pass gathers its coefficients from the scratch
   intt_from_smem_unscaled<LOGN, MaskStore, R1>(sm, tw + (size_t)l * TwLayout<LOGN>::LIMB_WORDS, lc, threadIdx.x,
-                                               MaskStore{p, (r && c == 0) ? r + oct * N : nullptr, lc}, p);
+                                               MaskStore{p, (r && c == 0) ? r + oct * N : nullptr, lc},
+                                               y_sc + ((size_t)l * (N / 8) * R_total + R) * 8, R_total * 8);
 }
 
 // The encoded weights as k_conv_tc's weight tiles: for every limb l,
@@ -585,6 +601,8 @@ __global__ void k_tc_weights(const uint32_t* __restrict__ w_hat, uint16_t* __res
   for (int s = 0; s < TC_U; ++s)
     dst[s * (TILEA_SLOT / 16) + c] = make_uint4(d[0][s].x, d[0][s].y, d[1][s].x, d[1][s].y);
 }
+
+size_t tc_scratch_words(int B, const ConvDims& cd, int L, int N) { return (size_t)2 * B * cd.bands * cd.Cout * L * N; }
 
 size_t tc_weights_bytes(int L, int Cout, int G, int N) {
   return (size_t)L * ((Cout + TC_M - 1) / TC_M) * (N / 4) * ((G + TC_GS - 1) / TC_GS) * TILEA_STEP;
@@ -650,7 +668,7 @@ static cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, size_t smem, cudaStr
 
 // pdl: the previous operation in `st` is the forward NTT of these inputs.
 // gpc: slot groups per CTA (4, 8 or 16; 0 = the default).
-cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint16_t* w_tc, const uint32_t* c_hat, uint32_t* y_hat,
+cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint16_t* w_tc, const uint32_t* c_hat, uint32_t* y_sc,
                            int N, const CtxConst& cc, unsigned long long* err, cudaStream_t st, bool pdl, int gpc) {
   if (B == 0 || cd.Cout == 0) return cudaSuccess;
   if (cd.G < 1 || cd.G > kTcMaxG) return cudaErrorInvalidValue;
@@ -662,9 +680,9 @@ cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint16_t* w_tc, cons
   cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)(mtiles * nchunks), N / (4 * gpc), cc.L), dim3(TC_THREADS),
                                       TC_SMEM, st, at, pdl);
   switch (gpc) {
-    case 4: return cudaLaunchKernelEx(&cfg, k_conv_tc<4>, w_tc, c_hat, y_hat, cd, B, N, cc, err);
-    case 8: return cudaLaunchKernelEx(&cfg, k_conv_tc<8>, w_tc, c_hat, y_hat, cd, B, N, cc, err);
-    default: return cudaLaunchKernelEx(&cfg, k_conv_tc<16>, w_tc, c_hat, y_hat, cd, B, N, cc, err);
+    case 4: return cudaLaunchKernelEx(&cfg, k_conv_tc<4>, w_tc, c_hat, y_sc, cd, B, N, cc, err);
+    case 8: return cudaLaunchKernelEx(&cfg, k_conv_tc<8>, w_tc, c_hat, y_sc, cd, B, N, cc, err);
+    default: return cudaLaunchKernelEx(&cfg, k_conv_tc<16>, w_tc, c_hat, y_sc, cd, B, N, cc, err);
   }
 }
 
@@ -697,16 +715,18 @@ cudaError_t launch_tc_setup(int logn) {
 }
 
 // pdl: the previous operation in `st` is the contraction that wrote y.
-cudaError_t launch_intt_mask_rows(int logn, long long rows, uint32_t* y, const uint32_t* r, const uint32_t* tw,
-                                  const CtxConst& cc, cudaStream_t st, bool pdl, int r1) {
+cudaError_t launch_intt_mask_rows(int logn, int B, const ConvDims& cd, const uint32_t* y_sc, uint32_t* y,
+                                  const uint32_t* r, const uint32_t* tw, const CtxConst& cc, cudaStream_t st, bool pdl,
+                                  int r1) {
+  const long long rows = 2LL * B * cd.bands * cd.Cout;  // scratch rows per limb
   if (rows == 0) return cudaSuccess;
   if (rows > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   cudaLaunchAttribute at[1];
   cudaError_t e = cudaSuccess;
   FL_PLAN_DISPATCH(logn, r1, {
-    cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)rows), dim3((1 << LG) / 32),
+    cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)rows, cc.L), dim3((1 << LG) / 32),
                                         (size_t)padded_words(1 << LG) * 4, st, at, pdl);
-    e = cudaLaunchKernelEx(&cfg, k_intt_mask_rows<LG, R1>, y, r, tw, cc);
+    e = cudaLaunchKernelEx(&cfg, k_intt_mask_rows<LG, R1>, y_sc, y, r, tw, cd.Cout, cd.bands, cd.n_out, cc);
   });
   return e;
 }

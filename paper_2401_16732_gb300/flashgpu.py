@@ -79,8 +79,8 @@ _SIGS = {
     "fl_tc_weights_bytes": ([_vp, _gp], _sz),
     "fl_tc_weights": ([_vp, _gp, _vp, _vp, _vp], _i),
     "fl_he_conv2d_tc_workspace_bytes": ([_vp, _gp, _i], _sz),
-    "fl_he_conv2d_tc_from_ntt": ([_vp, _gp, _i, _vp, _vp, _sz, _vp, _vp], _i),
-    "fl_intt_mask_outputs": ([_vp, _gp, _i, _vp, _vp, _vp], _i),
+    "fl_he_conv2d_tc_from_ntt": ([_vp, _gp, _i, _vp, _vp, _sz, _vp], _i),
+    "fl_intt_mask_outputs": ([_vp, _gp, _i, _vp, _sz, _vp, _vp, _vp], _i),
     "fl_mod_switch": ([_vp, _i, _vp, _i, _vp, _vp], _i),
     "fl_he_conv2d_otf": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "fl_he_conv2d_mask": ([_vp, _gp, _i, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _i),
@@ -394,10 +394,13 @@ class Context:
                                         _stream(stream)))
         return out
 
+    def tc_workspace_bytes(self, g, B: int) -> int:
+        return _lib.fl_he_conv2d_tc_workspace_bytes(self.h, ctypes.byref(g), B)
+
     def tc_workspace(self, g, B: int) -> torch.Tensor:
-        """Workspace of he_conv2d_tc: the inputs' NTT images and their
-        slot-tiled copy."""
-        nbytes = _lib.fl_he_conv2d_tc_workspace_bytes(self.h, ctypes.byref(g), B)
+        """Workspace of he_conv2d_tc: the inputs' NTT images, their
+        slot-tiled copy and the slot-tiled NTT-domain outputs."""
+        nbytes = self.tc_workspace_bytes(g, B)
         return torch.empty(max(nbytes, 16) // 4, dtype=torch.int32, device=f"cuda:{self.device}")
 
     def tc_weight_shape(self, g):
@@ -438,21 +441,25 @@ class Context:
                                     _stream(stream)))
         return out
 
-    def he_conv2d_tc_from_ntt(self, g, B, w_tc, workspace, out, stream=None):
+    def he_conv2d_tc_from_ntt(self, g, B, w_tc, workspace, stream=None):
         """Stage of he_conv2d_tc: the tensor-core contraction from a workspace
-        filled by he_conv2d_ntt_inputs; out gets NTT-domain values in [0, 2q)."""
+        filled by he_conv2d_ntt_inputs; the NTT-domain outputs (values in
+        [0, 2q), slot-tiled) stay in the workspace for intt_mask_outputs."""
         _dev_i16(w_tc, self.tc_weight_shape(g), "w_tc")
         _check(_lib.fl_he_conv2d_tc_from_ntt(self.h, ctypes.byref(g), B, _ptr(w_tc), _ptr(workspace),
-                                             workspace.numel() * workspace.element_size(), _ptr(out),
-                                             _stream(stream)))
-        return out
+                                             workspace.numel() * workspace.element_size(), _stream(stream)))
 
-    def intt_mask_outputs(self, g, out, r=None, stream=None):
-        """Stage of he_conv2d_tc: in-place inverse NTT of NTT-domain outputs,
-        plus the mask when r is given."""
+    def intt_mask_outputs(self, g, workspace, out, r=None, stream=None):
+        """Stage of he_conv2d_tc: the inverse NTT of the NTT-domain outputs
+        he_conv2d_tc_from_ntt left in the workspace, plus the mask when r is
+        given, into out."""
         B = out.shape[0]
         _dev_u32(out, (B, g.n_out, 2, self.L, self.N), "out")
-        _check(_lib.fl_intt_mask_outputs(self.h, ctypes.byref(g), B, _ptr(r), _ptr(out), _stream(stream)))
+        if r is not None:
+            _dev_u32(r, (B, g.n_out, self.N), "r")
+        _check(_lib.fl_intt_mask_outputs(self.h, ctypes.byref(g), B, _ptr(workspace),
+                                         workspace.numel() * workspace.element_size(), _ptr(r), _ptr(out),
+                                         _stream(stream)))
         return out
 
     def noise_inf(self, sk, ct, m, stream=None) -> float:

@@ -213,8 +213,8 @@ def test_tc_form_stages_equal_the_one_call_form(fg):
     ws = c.tc_workspace(g, B)
     out = torch.full_like(want, -1)
     c.he_conv2d_ntt_inputs(g, ct, ws)
-    c.he_conv2d_tc_from_ntt(g, B, wt, ws, out)
-    c.intt_mask_outputs(g, out, r=r)
+    c.he_conv2d_tc_from_ntt(g, B, wt, ws)
+    c.intt_mask_outputs(g, ws, out, r=r)
     assert torch.equal(out, want)
     assert c.tc_error() == 0
 

@@ -114,7 +114,7 @@ def test_tc_form_full_stack_in_the_bench_configuration(fg, oracle, config):
     c = fg.Context(wl.N, wl.L)
     specs, filters = _bench_layers(c, wl, 7, tc=True)
     assert max(sp["g"].G for sp in specs) == (52 if config == "resnet50-b8" else 10)
-    ws = c.tc_workspace(max((sp["g"] for sp in specs), key=lambda g: g.n_in), wl.B)  # shared, as bench.py does
+    ws = c.tc_workspace(max((sp["g"] for sp in specs), key=lambda g: c.tc_workspace_bytes(g, wl.B)), wl.B)  # shared
     for sp in specs:
         sp["ws"] = ws
 
