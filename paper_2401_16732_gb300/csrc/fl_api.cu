@@ -729,10 +729,9 @@ static int stage_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint16_t
                   "tensor-core contraction");
 }
 
-// the inverse NTT + mask of every scratch row into the output ciphertexts,
-// which must not overlap the workspace they are read from
-static int stage_intt_rows(fl_ctx* ctx, const fl_conv_geom* geom, int B, const void* ws, const uint32_t* r_dev,
-                           uint32_t* ct_out_dev, cudaStream_t st, bool pdl) {
+// the output ciphertexts are gathered from the workspace: they may not
+// overlap it, and their rows must fit one launch
+static int tc_out_checks(fl_ctx* ctx, const fl_conv_geom* geom, int B, const void* ws, const uint32_t* ct_out_dev) {
   if ((long long)2 * B * geom->bands * geom->Cout > 0x7fffffffLL)
     return fail(FL_ERR_ARG, "B=%d: too many output rows for one launch", B);
   const char* a = (const char*)ws;
@@ -740,6 +739,13 @@ static int stage_intt_rows(fl_ctx* ctx, const fl_conv_geom* geom, int B, const v
   const size_t ws_bytes = fl_he_conv2d_tc_workspace_bytes(ctx, geom, B),
                out_bytes = (size_t)B * geom->n_out * 2 * ctx->L * ctx->N * 4;
   if (a < b + out_bytes && b < a + ws_bytes) return fail(FL_ERR_ARG, "output ciphertexts overlap the workspace");
+  return FL_OK;
+}
+
+// the inverse NTT + mask of every scratch row into the output ciphertexts
+// (after tc_out_checks)
+static int stage_intt_rows(fl_ctx* ctx, const fl_conv_geom* geom, int B, const void* ws, const uint32_t* r_dev,
+                           uint32_t* ct_out_dev, cudaStream_t st, bool pdl) {
   return launched(fl::launch_intt_mask_rows(ctx->logN, B,
                                             fl::ConvDims{geom->Cout, geom->G, geom->n_in, geom->n_out, geom->bands},
                                             tc_scratch(ctx, geom, B, ws), ct_out_dev, r_dev, ctx->tw, ctx->cc, st, pdl,
@@ -755,6 +761,7 @@ int fl_he_conv2d_tc(fl_ctx* ctx, const fl_conv_geom* geom, int B, const uint16_t
   if (B == 0) return FL_OK;
   if ((rc = check_ptrs({w_tc_dev, ct_in_dev, ct_out_dev, workspace_dev}))) return rc;
   if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
+  if ((rc = tc_out_checks(ctx, geom, B, workspace_dev, ct_out_dev))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = stage_ntt(ctx, geom, B, ct_in_dev, workspace_dev, st))) return rc;
   if ((rc = stage_tc(ctx, geom, B, w_tc_dev, workspace_dev, st))) return rc;
@@ -777,6 +784,7 @@ int fl_intt_mask_outputs(fl_ctx* ctx, const fl_conv_geom* geom, int B, const voi
   if (B == 0) return FL_OK;
   if ((rc = check_ptrs({workspace_dev, ct_out_dev}))) return rc;
   if (r_dev && (rc = check_ptrs({r_dev}))) return rc;
+  if ((rc = tc_out_checks(ctx, geom, B, workspace_dev, ct_out_dev))) return rc;
   return stage_intt_rows(ctx, geom, B, workspace_dev, r_dev, ct_out_dev, (cudaStream_t)stream, false);
 }
 

@@ -217,6 +217,14 @@ def test_tc_form_stages_equal_the_one_call_form(fg):
     c.intt_mask_outputs(g, ws, out, r=r)
     assert torch.equal(out, want)
     assert c.tc_error() == 0
+    # the outputs are gathered from the workspace: an output buffer inside it
+    # is refused before any launch, by the staged call and the one-call form
+    inside = ws[ws.numel() - out.numel():].view(out.shape)
+    with pytest.raises(fg.FlashError, match="overlap"):
+        c.intt_mask_outputs(g, ws, inside, r=r)
+    with pytest.raises(fg.FlashError, match="overlap"):
+        c.he_conv2d_tc(g, wt, ct, out=inside, workspace=ws, r=r)
+    assert torch.equal(c.he_conv2d_tc(g, wt, ct, workspace=ws, r=r), want)
 
 
 def decode_tc_weights(wt, L, Cout, G, N):
