@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // CTAs that run together read neighbouring rows, so each 8-slot piece they
 // gather is part of a contiguous run.
 template <int LOGN, int R1>
-__global__ void __launch_bounds__((1 << LOGN) / 32)
+__global__ void __launch_bounds__((1 << LOGN) / 32, minb_one_poly<LOGN>())
     k_intt_mask_rows(const uint32_t* __restrict__ y_sc, uint32_t* __restrict__ y, const uint32_t* __restrict__ r,
                      const uint32_t* __restrict__ tw, int Cout, int bands, int n_out, CtxConst cc) {
   constexpr int N = 1 << LOGN;
