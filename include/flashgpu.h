@@ -387,8 +387,8 @@ int fl_ctx_get_stack_kernel(const fl_ctx *ctx);
  *   3 at N = 2048; 3, 4 at 4096; 3, 4, 5 at 8192; 4, 5 at 16384; 0 selects
  *   the default (3, 4, 4, 5 for the four ring degrees).  FL_ERR_ARG for any
  *   other value.  The getter returns the r1 in use.
- * - Tensor-core tile: slot groups of 4 per CTA of fl_he_conv2d_tc (4, 8 or
- *   16; 0 selects the default 16).  FL_ERR_ARG otherwise. */
+ * - Tensor-core tile: slot groups of 4 per CTA of fl_he_conv2d_tc (4, 8, 16,
+ *   32 or 64; 0 selects the default 32).  FL_ERR_ARG otherwise. */
 int fl_ctx_set_ntt_plan(fl_ctx *ctx, int r1);
 int fl_ctx_get_ntt_plan(const fl_ctx *ctx);
 int fl_ctx_set_tc_tile(fl_ctx *ctx, int groups);

@@ -980,13 +980,13 @@ int fl_ctx_get_ntt_plan(const fl_ctx* ctx) { return ctx ? (ctx->ntt_plan ? ctx->
 int fl_ctx_set_tc_tile(fl_ctx* ctx, int groups) {
   int rc;
   if ((rc = check_ctx(ctx))) return rc;
-  if (groups != 0 && groups != 4 && groups != 8 && groups != 16)
-    return fail(FL_ERR_ARG, "tensor-core tile of %d slot groups (4, 8 or 16)", groups);
+  if (groups != 0 && groups != 4 && groups != 8 && groups != 16 && groups != 32 && groups != 64)
+    return fail(FL_ERR_ARG, "tensor-core tile of %d slot groups (4, 8, 16, 32 or 64)", groups);
   ctx->tc_tile = groups;
   return FL_OK;
 }
 
-int fl_ctx_get_tc_tile(const fl_ctx* ctx) { return ctx ? (ctx->tc_tile ? ctx->tc_tile : 16) : 0; }
+int fl_ctx_get_tc_tile(const fl_ctx* ctx) { return ctx ? (ctx->tc_tile ? ctx->tc_tile : 32) : 0; }
 
 int fl_he_conv2d_stack(fl_ctx* ctx, const fl_stack_layer* layers, int n_layers, void* workspace_dev,
                        size_t workspace_bytes, void* stream) {

@@ -77,10 +77,10 @@ constexpr int TC_LOAD_WARP = TC_MMA_WARP + 1;              // one the bulk copie
 constexpr int TC_THREADS = 32 * (TC_LOAD_WARP + 1);        // 576
 constexpr int TC_RING = 6;            // raw-input ring depth, in K steps
 constexpr int TC_NS = 6;              // operand stages (weight tile + input tile)
-// slot groups per CTA (the tile's length along the slots): 4, 8 or 16, a
+// slot groups per CTA (the tile's length along the slots): 4, 8, 16, 32 or 64, a
 // template parameter of k_conv_tc chosen per workload (even: the epilogue
 // stores groups in pairs)
-constexpr int TC_GPC_DEFAULT = 16;
+constexpr int TC_GPC_DEFAULT = 32;
 constexpr int TC_TMEM_COLS = 2 * TC_U * TC_NN;  // 512: two accumulator buffers
 // shared-memory layout (bytes)
 constexpr int RAWB_STEP = TC_CW * TC_GS * 16;      // [image/band][g][component][4 slots]
@@ -667,13 +667,13 @@ static cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, size_t smem, cudaStr
 }
 
 // pdl: the previous operation in `st` is the forward NTT of these inputs.
-// gpc: slot groups per CTA (4, 8 or 16; 0 = the default).
+// gpc: slot groups per CTA (4, 8, 16, 32 or 64; 0 = the default).
 cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint16_t* w_tc, const uint32_t* c_hat, uint32_t* y_sc,
                            int N, const CtxConst& cc, unsigned long long* err, cudaStream_t st, bool pdl, int gpc) {
   if (B == 0 || cd.Cout == 0) return cudaSuccess;
   if (cd.G < 1 || cd.G > kTcMaxG) return cudaErrorInvalidValue;
   if (gpc == 0) gpc = TC_GPC_DEFAULT;
-  if (gpc != 4 && gpc != 8 && gpc != 16) return cudaErrorInvalidValue;
+  if (gpc != 4 && gpc != 8 && gpc != 16 && gpc != 32 && gpc != 64) return cudaErrorInvalidValue;
   const long long mtiles = (cd.Cout + TC_M - 1) / TC_M, nchunks = (2LL * B * cd.bands + TC_CW - 1) / TC_CW;
   if (mtiles * nchunks > 0x7fffffffLL || N % (4 * gpc) != 0) return cudaErrorInvalidConfiguration;
   cudaLaunchAttribute at[1];
@@ -682,6 +682,8 @@ cudaError_t launch_conv_tc(int B, const ConvDims& cd, const uint16_t* w_tc, cons
   switch (gpc) {
     case 4: return cudaLaunchKernelEx(&cfg, k_conv_tc<4>, w_tc, c_hat, y_sc, cd, B, N, cc, err);
     case 8: return cudaLaunchKernelEx(&cfg, k_conv_tc<8>, w_tc, c_hat, y_sc, cd, B, N, cc, err);
+    case 32: return cudaLaunchKernelEx(&cfg, k_conv_tc<32>, w_tc, c_hat, y_sc, cd, B, N, cc, err);
+    case 64: return cudaLaunchKernelEx(&cfg, k_conv_tc<64>, w_tc, c_hat, y_sc, cd, B, N, cc, err);
     default: return cudaLaunchKernelEx(&cfg, k_conv_tc<16>, w_tc, c_hat, y_sc, cd, B, N, cc, err);
   }
 }
@@ -703,7 +705,9 @@ cudaError_t launch_tc_setup(int logn) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_conv_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)) ||
       (e = cudaFuncSetAttribute(k_conv_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)) ||
-      (e = cudaFuncSetAttribute(k_conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)))
+      (e = cudaFuncSetAttribute(k_conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)) ||
+      (e = cudaFuncSetAttribute(k_conv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)) ||
+      (e = cudaFuncSetAttribute(k_conv_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)))
     return e;
   switch (logn) {
     case 11: return intt_rows_setup<11>();

@@ -29,7 +29,7 @@ FL_STACK_PER_LAYER, FL_STACK_PERSISTENT, FL_STACK_QUEUE = 0, 1, 2
 FL_NOALLOC_SCRATCH_BYTES = 16 << 20
 FL_TC_MAX_G = 64
 NTT_PLANS = {11: (3,), 12: (3, 4), 13: (3, 4, 5), 14: (4, 5)}  # available first-pass radix exponents
-TC_TILES = (4, 8, 16)
+TC_TILES = (4, 8, 16, 32, 64)
 FL_STACK_MAX_LAYERS = 64
 
 
