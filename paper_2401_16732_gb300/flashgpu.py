@@ -146,20 +146,32 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dev_u32(t: torch.Tensor, shape, name):
-    if t.dtype not in (torch.int32, torch.uint32) or not t.is_cuda or not t.is_contiguous():
-        raise FlashError(f"{name}: expected a contiguous 32-bit CUDA tensor")
-    if tuple(t.shape) != tuple(shape):
+_KINDS = {"u32": ((torch.int32, torch.uint32), "32-bit"), "i16": ((torch.int16, torch.uint16), "16-bit"),
+          "i8": ((torch.int8,), "int8"), "any": (None, "")}
+
+
+def _dev(t, kind, shape, name, device=None):
+    """The C entry points take raw device pointers and cannot check what they
+    point to: every tensor handed to one is checked here first -- a CUDA
+    tensor (on `device` when given), contiguous, of the element kind and (when
+    `shape` is not None) the shape the call reads or writes."""
+    dtypes, what = _KINDS[kind]
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous() or \
+            (dtypes is not None and t.dtype not in dtypes):
+        raise FlashError(f"{name}: expected a contiguous {what + ' ' if what else ''}CUDA tensor")
+    if device is not None and t.device.index != device:
+        raise FlashError(f"{name}: on cuda:{t.device.index}, the context is on cuda:{device}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
         raise FlashError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
     return t
 
 
-def _dev_i16(t: torch.Tensor, shape, name):
-    if t.dtype not in (torch.int16, torch.uint16) or not t.is_cuda or not t.is_contiguous():
-        raise FlashError(f"{name}: expected a contiguous 16-bit CUDA tensor")
-    if tuple(t.shape) != tuple(shape):
-        raise FlashError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
-    return t
+def _dev_u32(t: torch.Tensor, shape, name, device=None):
+    return _dev(t, "u32", shape, name, device)
+
+
+def _dev_i16(t: torch.Tensor, shape, name, device=None):
+    return _dev(t, "i16", shape, name, device)
 
 
 def selftest_wait_timeout(stream=None) -> tuple[int, int]:
@@ -176,6 +188,7 @@ def repack_outputs(prev: ConvGeom, nxt: ConvGeom, src, out=None, stream=None) ->
     _dev_u32(src, (B, prev.n_out, prev.N), "src")
     if out is None:
         out = torch.empty((B, nxt.n_in, nxt.N), dtype=src.dtype, device=src.device)
+    _dev_u32(out, (B, nxt.n_in, nxt.N), "out", src.device.index)
     _check(_lib.fl_repack_outputs(ctypes.byref(prev), ctypes.byref(nxt), B, _ptr(src), _ptr(out), _stream(stream)))
     return out
 
@@ -205,31 +218,55 @@ class Context:
     def _new(self, *shape):
         return torch.empty(shape, dtype=torch.int32, device=f"cuda:{self.device}")
 
+    def _u32(self, t, shape, name):
+        return _dev(t, "u32", shape, name, self.device)
+
+    def _ct(self, t, name):
+        """Ciphertexts [..., 2, L, N]; returns how many."""
+        _dev(t, "u32", None, name, self.device)
+        if t.dim() < 3 or tuple(t.shape[-3:]) != (2, self.L, self.N):
+            raise FlashError(f"{name}: expected [..., 2, {self.L}, {self.N}], got {tuple(t.shape)}")
+        return t.numel() // (2 * self.L * self.N)
+
+    def _ws(self, t, name="workspace"):
+        """A workspace: any contiguous tensor on the context's device; the
+        library checks its size in bytes."""
+        return _dev(t, "any", None, name, self.device)
+
+    def _out(self, out, shape, name="out"):
+        return self._new(*shape) if out is None else self._u32(out, shape, name)
+
     # -- client side -----------------------------------------------------
     def keygen(self, s: torch.Tensor, stream=None) -> torch.Tensor:
+        _dev(s, "i8", (self.N,), "s", self.device)
         sk = self._new(self.L, self.N)
         _check(_lib.fl_keygen(self.h, _ptr(s), _ptr(sk), _stream(stream)))
         return sk
 
     def encrypt(self, sk, g: ConvGeom, x, a, e, out=None, stream=None) -> torch.Tensor:
         B = x.shape[0]
-        _dev_u32(a, (B, g.n_in, self.L, self.N), "a")
-        out = self._new(B, g.n_in, 2, self.L, self.N) if out is None else out
+        self._u32(sk, (self.L, self.N), "sk")
+        self._u32(x, (B, g.Cin, g.H, g.W), "x")
+        self._u32(a, (B, g.n_in, self.L, self.N), "a")
+        self._u32(e, (B, g.n_in, self.N), "e")
+        out = self._out(out, (B, g.n_in, 2, self.L, self.N))
         _check(_lib.fl_encrypt(self.h, _ptr(sk), ctypes.byref(g), B, _ptr(x), _ptr(a), _ptr(e), _ptr(out),
                                _stream(stream)))
         return out
 
     def encrypt_online(self, g: ConvGeom, x, enc0, out=None, stream=None) -> torch.Tensor:
         B = x.shape[0]
-        _dev_u32(enc0, (B, g.n_in, 2, self.L, self.N), "enc0")
-        out = torch.empty_like(enc0) if out is None else out
+        self._u32(x, (B, g.Cin, g.H, g.W), "x")
+        self._u32(enc0, (B, g.n_in, 2, self.L, self.N), "enc0")
+        out = torch.empty_like(enc0) if out is None else self._u32(out, tuple(enc0.shape), "out")
         _check(_lib.fl_encrypt_online(self.h, ctypes.byref(g), B, _ptr(x), _ptr(enc0), _ptr(out), _stream(stream)))
         return out
 
     def decrypt(self, sk, ct, stream=None) -> torch.Tensor:
         """ct [..., 2, L, N] -> m [..., N] (values in [0, t))."""
+        self._u32(sk, (self.L, self.N), "sk")
+        n = self._ct(ct, "ct")
         lead = ct.shape[:-3]
-        n = int(torch.tensor(lead).prod()) if len(lead) else 1
         ws = torch.empty(_lib.fl_decrypt_workspace_bytes(self.h, n) // 4 + 4, dtype=torch.int32, device=ct.device)
         m = self._new(*lead, self.N)
         _check(_lib.fl_decrypt(self.h, _ptr(sk), n, _ptr(ct), _ptr(m), _ptr(ws), ws.numel() * 4, _stream(stream)))
@@ -237,6 +274,7 @@ class Context:
 
     def extract_outputs(self, g: ConvGeom, m, stream=None) -> torch.Tensor:
         B = m.shape[0]
+        self._u32(m, (B, g.n_out, self.N), "m")
         y = self._new(B, g.Cout, g.Ho, g.Wo)
         _check(_lib.fl_extract_outputs(ctypes.byref(g), B, _ptr(m), _ptr(y), _stream(stream)))
         return y
@@ -246,7 +284,8 @@ class Context:
         return _lib.fl_weights_bytes(self.h, ctypes.byref(g))
 
     def encode_weights(self, g: ConvGeom, w, out=None, stream=None) -> torch.Tensor:
-        out = self._new(self.L, g.Cout, g.G, self.N) if out is None else out
+        _dev(w, "i8", (g.Cout, g.Cin, g.k, g.k), "w", self.device)
+        out = self._out(out, (self.L, g.Cout, g.G, self.N))
         _check(_lib.fl_encode_weights(self.h, ctypes.byref(g), _ptr(w), _ptr(out), _stream(stream)))
         return out
 
@@ -261,25 +300,33 @@ class Context:
         """Homomorphic convolution of ct_in [B][n_in][2][L][N]; with r
         ([B][n_out][N]) the mask addition is fused (fl_he_conv2d_mask)."""
         B = ct_in.shape[0]
-        _dev_u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
-        out = self._new(B, g.n_out, 2, self.L, self.N) if out is None else out
-        ws = self.workspace(g, B) if workspace is None else workspace
+        self._u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
+        self._u32(w_hat, (self.L, g.Cout, g.G, self.N), "w_hat")
+        out = self._out(out, (B, g.n_out, 2, self.L, self.N))
+        ws = self.workspace(g, B) if workspace is None else self._ws(workspace)
         if r is None:
             _check(_lib.fl_he_conv2d(self.h, ctypes.byref(g), B, _ptr(w_hat), _ptr(ct_in), _ptr(out), _ptr(ws),
                                      ws.numel() * ws.element_size(), _stream(stream)))
         else:
-            _dev_u32(r, (B, g.n_out, self.N), "r")
+            self._u32(r, (B, g.n_out, self.N), "r")
             _check(_lib.fl_he_conv2d_mask(self.h, ctypes.byref(g), B, _ptr(w_hat), _ptr(ct_in), _ptr(r), _ptr(out),
                                           _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
         return out
 
     def he_conv2d_ntt_inputs(self, g, ct_in, workspace, stream=None):
         """Stage a3 of he_conv2d: forward NTT of ct_in into the workspace."""
+        self._u32(ct_in, (ct_in.shape[0], g.n_in, 2, self.L, self.N), "ct_in")
+        self._ws(workspace)
         _check(_lib.fl_he_conv2d_ntt_inputs(self.h, ctypes.byref(g), ct_in.shape[0], _ptr(ct_in), _ptr(workspace),
                                             workspace.numel() * workspace.element_size(), _stream(stream)))
 
     def he_conv2d_from_ntt(self, g, B, w_hat, workspace, out, r=None, stream=None):
         """Stages a4-a6 of he_conv2d from a workspace filled by he_conv2d_ntt_inputs."""
+        self._u32(w_hat, (self.L, g.Cout, g.G, self.N), "w_hat")
+        self._ws(workspace)
+        self._u32(out, (B, g.n_out, 2, self.L, self.N), "out")
+        if r is not None:
+            self._u32(r, (B, g.n_out, self.N), "r")
         _check(_lib.fl_he_conv2d_from_ntt(self.h, ctypes.byref(g), B, _ptr(w_hat), _ptr(workspace),
                                           workspace.numel() * workspace.element_size(), _ptr(r), _ptr(out),
                                           _stream(stream)))
@@ -296,6 +343,12 @@ class Context:
         keep = []
         for k, sp in enumerate(specs):
             g = sp["g"]
+            B = sp["ct_in"].shape[0]
+            self._u32(sp["w_hat"], (self.L, g.Cout, g.G, self.N), f"layer {k}: w_hat")
+            self._u32(sp["ct_in"], (B, g.n_in, 2, self.L, self.N), f"layer {k}: ct_in")
+            self._u32(sp["out"], (B, g.n_out, 2, self.L, self.N), f"layer {k}: out")
+            if sp.get("r") is not None:
+                self._u32(sp["r"], (B, g.n_out, self.N), f"layer {k}: r")
             keep.extend([g, sp["w_hat"], sp["ct_in"], sp["out"], sp.get("r")])
             arr[k].geom = ctypes.pointer(g)
             arr[k].B = sp["ct_in"].shape[0]
@@ -313,6 +366,7 @@ class Context:
     def he_conv2d_stack(self, arr, workspace, stream=None, stage="all"):
         fn = {"all": _lib.fl_he_conv2d_stack, "ntt": _lib.fl_he_conv2d_stack_ntt,
               "run": _lib.fl_he_conv2d_stack_run}[stage]
+        self._ws(workspace)
         _check(fn(self.h, arr, len(arr), _ptr(workspace), workspace.numel() * workspace.element_size(),
                   _stream(stream)))
 
@@ -344,6 +398,7 @@ class Context:
         _check(_lib.fl_ctx_set_tc_tile(self.h, groups))
 
     def stack_error(self, workspace, stream=None) -> int:
+        self._ws(workspace)
         v = ctypes.c_uint64()
         rc = _lib.fl_stack_error(_ptr(workspace), _stream(stream), ctypes.byref(v))
         if rc not in (FL_OK, FL_ERR_TIMEOUT):
@@ -357,10 +412,10 @@ class Context:
         caller's [B][n_out][2][L][N] buffer.  Every buffer's dtype, device,
         contiguity and shape is checked before the call."""
         B = ct_in.shape[0]
-        _dev_u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
-        _dev_u32(w_hat, (self.L, g.Cout, g.G, self.N), "w_hat")
-        _dev_u32(r, (B, g.n_out, self.N), "r")
-        _dev_u32(out, (B, g.n_out, 2, self.L, self.N), "out")
+        self._u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
+        self._u32(w_hat, (self.L, g.Cout, g.G, self.N), "w_hat")
+        self._u32(r, (B, g.n_out, self.N), "r")
+        self._u32(out, (B, g.n_out, 2, self.L, self.N), "out")
         _check(_lib.fl_he_conv2d_mask_noalloc(self.h, ctypes.byref(g), ct_in.shape[0], _ptr(w_hat), _ptr(ct_in),
                                               _ptr(r), _ptr(out), _stream(stream)))
         return out
@@ -370,12 +425,12 @@ class Context:
         when r is given) from int8 filters w [Cout][Cin][k][k], with no
         encoded weights."""
         B = ct_in.shape[0]
-        if w.dtype != torch.int8 or not w.is_cuda or not w.is_contiguous() or \
-                tuple(w.shape) != (g.Cout, g.Cin, g.k, g.k):
-            raise FlashError("w: expected a contiguous int8 CUDA tensor [Cout][Cin][k][k]")
-        _dev_u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
-        out = self._new(B, g.n_out, 2, self.L, self.N) if out is None else out
-        workspace = self.workspace(g, B) if workspace is None else workspace
+        _dev(w, "i8", (g.Cout, g.Cin, g.k, g.k), "w", self.device)
+        self._u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
+        if r is not None:
+            self._u32(r, (B, g.n_out, self.N), "r")
+        out = self._out(out, (B, g.n_out, 2, self.L, self.N))
+        workspace = self.workspace(g, B) if workspace is None else self._ws(workspace)
         _check(_lib.fl_he_conv2d_otf(self.h, ctypes.byref(g), B, _ptr(w), _ptr(ct_in), _ptr(r), _ptr(out),
                                      _ptr(workspace), workspace.numel() * workspace.element_size(),
                                      _stream(stream)))
@@ -385,11 +440,11 @@ class Context:
         """Direct form (DRot + CMult, no NTT) from int8 filters w [Cout][Cin][k][k];
         the same ciphertexts as he_conv2d (plus the mask when r is given)."""
         B = ct_in.shape[0]
-        if w.dtype != torch.int8 or not w.is_cuda or not w.is_contiguous() or \
-                tuple(w.shape) != (g.Cout, g.Cin, g.k, g.k):
-            raise FlashError("w: expected a contiguous int8 CUDA tensor [Cout][Cin][k][k]")
-        _dev_u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
-        out = self._new(B, g.n_out, 2, self.L, self.N) if out is None else out
+        _dev(w, "i8", (g.Cout, g.Cin, g.k, g.k), "w", self.device)
+        self._u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
+        if r is not None:
+            self._u32(r, (B, g.n_out, self.N), "r")
+        out = self._out(out, (B, g.n_out, 2, self.L, self.N))
         _check(_lib.fl_he_conv2d_direct(self.h, ctypes.byref(g), B, _ptr(w), _ptr(ct_in), _ptr(r), _ptr(out),
                                         _stream(stream)))
         return out
@@ -413,14 +468,14 @@ class Context:
         """The encoded weights [L][Cout][G][N] as he_conv2d_tc's weight tiles:
         balanced base-256 digits in fp16, in the MMA's shared-memory layout
         (int16 tensor of tc_weight_shape(g); see fl_tc_weights)."""
-        _dev_u32(w_hat, (self.L, g.Cout, g.G, self.N), "w_hat")
+        self._u32(w_hat, (self.L, g.Cout, g.G, self.N), "w_hat")
         if g.G > FL_TC_MAX_G:
             raise FlashError(f"G={g.G} above {FL_TC_MAX_G}: the tensor-core form is not exact")
         shape = self.tc_weight_shape(g)
         if 2 * math.prod(shape) != _lib.fl_tc_weights_bytes(self.h, ctypes.byref(g)):
             raise FlashError("tensor-core weight tiles: the library's size differs from the binding's shape")
         out = torch.empty(shape, dtype=torch.int16, device=w_hat.device) if out is None else out
-        _dev_i16(out, shape, "out")
+        _dev_i16(out, shape, "out", self.device)
         _check(_lib.fl_tc_weights(self.h, ctypes.byref(g), _ptr(w_hat), _ptr(out), _stream(stream)))
         return out
 
@@ -429,13 +484,13 @@ class Context:
         same ciphertexts as he_conv2d (plus the mask when r is given) from
         the weight tiles of tc_weights.  G <= FL_TC_MAX_G."""
         B = ct_in.shape[0]
-        _dev_u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
-        _dev_i16(w_tc, self.tc_weight_shape(g), "w_tc")
+        self._u32(ct_in, (B, g.n_in, 2, self.L, self.N), "ct_in")
+        _dev_i16(w_tc, self.tc_weight_shape(g), "w_tc", self.device)
         if r is not None:
-            _dev_u32(r, (B, g.n_out, self.N), "r")
+            self._u32(r, (B, g.n_out, self.N), "r")
         out = self._new(B, g.n_out, 2, self.L, self.N) if out is None else out
-        _dev_u32(out, (B, g.n_out, 2, self.L, self.N), "out")
-        workspace = self.tc_workspace(g, B) if workspace is None else workspace
+        self._u32(out, (B, g.n_out, 2, self.L, self.N), "out")
+        workspace = self.tc_workspace(g, B) if workspace is None else self._ws(workspace)
         _check(_lib.fl_he_conv2d_tc(self.h, ctypes.byref(g), B, _ptr(w_tc), _ptr(ct_in), _ptr(r), _ptr(out),
                                     _ptr(workspace), workspace.numel() * workspace.element_size(),
                                     _stream(stream)))
@@ -445,7 +500,8 @@ class Context:
         """Stage of he_conv2d_tc: the tensor-core contraction from a workspace
         filled by he_conv2d_ntt_inputs; the NTT-domain outputs (values in
         [0, 2q), slot-tiled) stay in the workspace for intt_mask_outputs."""
-        _dev_i16(w_tc, self.tc_weight_shape(g), "w_tc")
+        _dev_i16(w_tc, self.tc_weight_shape(g), "w_tc", self.device)
+        self._ws(workspace)
         _check(_lib.fl_he_conv2d_tc_from_ntt(self.h, ctypes.byref(g), B, _ptr(w_tc), _ptr(workspace),
                                              workspace.numel() * workspace.element_size(), _stream(stream)))
 
@@ -454,9 +510,10 @@ class Context:
         he_conv2d_tc_from_ntt left in the workspace, plus the mask when r is
         given, into out."""
         B = out.shape[0]
-        _dev_u32(out, (B, g.n_out, 2, self.L, self.N), "out")
+        self._u32(out, (B, g.n_out, 2, self.L, self.N), "out")
         if r is not None:
-            _dev_u32(r, (B, g.n_out, self.N), "r")
+            self._u32(r, (B, g.n_out, self.N), "r")
+        self._ws(workspace)
         _check(_lib.fl_intt_mask_outputs(self.h, ctypes.byref(g), B, _ptr(workspace),
                                          workspace.numel() * workspace.element_size(), _ptr(r), _ptr(out),
                                          _stream(stream)))
@@ -465,8 +522,9 @@ class Context:
     def noise_inf(self, sk, ct, m, stream=None) -> float:
         """Largest |v| of the decryption noise (Appendix A) of ct [..., 2, L, N]
         against the expected messages m [..., N] (values in [0, t))."""
-        n = ct.numel() // (2 * self.L * self.N)
-        _dev_u32(ct, (n, 2, self.L, self.N) if ct.dim() == 4 else tuple(ct.shape), "ct")
+        self._u32(sk, (self.L, self.N), "sk")
+        n = self._ct(ct, "ct")
+        _dev(m, "u32", None, "m", self.device)
         if m.numel() != n * self.N:
             raise FlashError(f"m: {m.numel()} values for {n} ciphertexts of {self.N} coefficients")
         ws = torch.empty(max(_lib.fl_noise_workspace_bytes(self.h, n), 16) // 4, dtype=torch.int32, device=ct.device)
@@ -478,16 +536,20 @@ class Context:
     def copy_to_device(self, host, dev, stream=None):
         """Copy the host tensor's 32-bit words into the device tensor through
         the library (fl_copy_to_device); asynchronous for pinned host memory."""
-        if host.is_cuda or not dev.is_cuda or host.numel() != dev.numel() or host.element_size() != 4:
-            raise FlashError("copy_to_device: a 32-bit host tensor and a device tensor of the same size")
+        if not isinstance(host, torch.Tensor) or host.is_cuda or not host.is_contiguous() or \
+                host.numel() != dev.numel() or host.element_size() != 4:
+            raise FlashError("copy_to_device: a contiguous 32-bit host tensor and a device tensor of the same size")
+        self._u32(dev, dev.shape, "dev")
         _check(_lib.fl_copy_to_device(self.h, _ptr(host), _ptr(dev), host.numel(), _stream(stream)))
         return dev
 
     def copy_to_host(self, dev, host, stream=None):
         """Copy the device tensor's 32-bit words into the host tensor through
         the library (fl_copy_to_host); asynchronous for pinned host memory."""
-        if host.is_cuda or not dev.is_cuda or host.numel() != dev.numel() or dev.element_size() != 4:
-            raise FlashError("copy_to_host: a device tensor and a 32-bit host tensor of the same size")
+        self._u32(dev, dev.shape, "dev")
+        if not isinstance(host, torch.Tensor) or host.is_cuda or not host.is_contiguous() or \
+                host.numel() != dev.numel() or host.element_size() != 4:
+            raise FlashError("copy_to_host: a device tensor and a contiguous 32-bit host tensor of the same size")
         _check(_lib.fl_copy_to_host(self.h, _ptr(dev), _ptr(host), dev.numel(), _stream(stream)))
         return host
 
@@ -502,17 +564,18 @@ class Context:
 
     def mod_switch(self, ct, L_out: int, out=None, stream=None) -> torch.Tensor:
         """Ciphertexts [..., 2, L, N] -> [..., 2, L_out, N] under the first L_out primes."""
-        if ct.shape[-3:] != (2, self.L, self.N):
-            raise FlashError(f"ct: expected [..., 2, {self.L}, {self.N}], got {tuple(ct.shape)}")
-        n = ct.numel() // (2 * self.L * self.N)
+        n = self._ct(ct, "ct")
+        shape = tuple(ct.shape[:-2]) + (L_out, self.N)
         if out is None:
-            out = torch.empty(tuple(ct.shape[:-2]) + (L_out, self.N), dtype=ct.dtype, device=ct.device)
+            out = torch.empty(shape, dtype=ct.dtype, device=ct.device)
+        self._u32(out, shape, "out")
         _check(_lib.fl_mod_switch(self.h, n, _ptr(ct), L_out, _ptr(out), _stream(stream)))
         return out
 
     def mask_to_share(self, ct, r, stream=None) -> torch.Tensor:
         """In place: c0 += Delta*r for ct [..., 2, L, N], r [..., N]."""
-        n = ct.numel() // (2 * self.L * self.N)
+        n = self._ct(ct, "ct")
+        self._u32(r, tuple(ct.shape[:-3]) + (self.N,), "r")
         _check(_lib.fl_mask_to_share(self.h, n, _ptr(ct), _ptr(r), _stream(stream)))
         return ct
 
@@ -520,51 +583,62 @@ class Context:
     def _n_vec(self, t, name):
         if t.numel() % self.N:
             raise FlashError(f"{name}: size {t.numel()} is not a multiple of N={self.N}")
-        return _dev_u32(t, t.shape, name).numel() // self.N
+        return self._u32(t, t.shape, name).numel() // self.N
 
     def batch_encode(self, slots, out=None, stream=None) -> torch.Tensor:
         """slots [..., N] -> plaintext polynomials [..., N] in [0, t)."""
         n = self._n_vec(slots, "slots")
-        out = torch.empty_like(slots) if out is None else out
+        out = torch.empty_like(slots) if out is None else self._u32(out, tuple(slots.shape), "out")
         _check(_lib.fl_batch_encode(self.h, n, _ptr(slots), _ptr(out), _stream(stream)))
         return out
 
     def batch_decode(self, m, out=None, stream=None) -> torch.Tensor:
         """plaintext polynomials [..., N] (values in [0, t)) -> slots [..., N]."""
         n = self._n_vec(m, "m")
-        out = torch.empty_like(m) if out is None else out
+        out = torch.empty_like(m) if out is None else self._u32(out, tuple(m.shape), "out")
         _check(_lib.fl_batch_decode(self.h, n, _ptr(m), _ptr(out), _stream(stream)))
         return out
 
     def x2x_prepare(self, r, v, out=None, stream=None) -> torch.Tensor:
         """Offline step: masks r, v [..., N] -> prep [n][L+2][N]."""
         n = self._n_vec(r, "r")
-        _dev_u32(v, r.shape, "v")
-        out = self._new(n, self.L + 2, self.N) if out is None else _dev_u32(out, (n, self.L + 2, self.N), "prep")
+        self._u32(v, r.shape, "v")
+        out = self._out(out, (n, self.L + 2, self.N), "prep")
         _check(_lib.fl_x2x_prepare(self.h, n, _ptr(r), _ptr(v), _ptr(out), _stream(stream)))
         return out
 
     def x2x_round1(self, prep, ct_z, out=None, stream=None) -> torch.Tensor:
         """<2rz + v> (batch encoded) from <z> (batch encoded) [n][2][L][N]."""
         n = prep.shape[0]
-        _dev_u32(ct_z, (n, 2, self.L, self.N), "ct_z")
-        out = self._new(n, 2, self.L, self.N) if out is None else out
+        self._u32(prep, (n, self.L + 2, self.N), "prep")
+        self._u32(ct_z, (n, 2, self.L, self.N), "ct_z")
+        out = self._out(out, (n, 2, self.L, self.N))
         _check(_lib.fl_x2x_round1(self.h, n, _ptr(prep), _ptr(ct_z), _ptr(out), _stream(stream)))
         return out
 
     def x2x_round2(self, prep, ct_x, ct_y, out=None, stream=None) -> torch.Tensor:
         """<a^2 + a> = <X> - <Y> + (r^2 - r + v), direct encoded [n][2][L][N]."""
         n = prep.shape[0]
-        _dev_u32(ct_x, (n, 2, self.L, self.N), "ct_x")
-        _dev_u32(ct_y, (n, 2, self.L, self.N), "ct_y")
-        out = self._new(n, 2, self.L, self.N) if out is None else out
+        self._u32(prep, (n, self.L + 2, self.N), "prep")
+        self._u32(ct_x, (n, 2, self.L, self.N), "ct_x")
+        self._u32(ct_y, (n, 2, self.L, self.N), "ct_y")
+        out = self._out(out, (n, 2, self.L, self.N))
         _check(_lib.fl_x2x_round2(self.h, n, _ptr(prep), _ptr(ct_x), _ptr(ct_y), _ptr(out), _stream(stream)))
         return out
 
+    def _polys(self, data, name="data"):
+        """Polynomials [..., L, N] in place; returns how many L-limb groups."""
+        self._u32(data, data.shape, name)
+        if data.dim() < 2 or tuple(data.shape[-2:]) != (self.L, self.N):
+            raise FlashError(f"{name}: expected [..., {self.L}, {self.N}], got {tuple(data.shape)}")
+        return data.numel() // (self.L * self.N)
+
     def ntt_forward(self, data, stream=None):
+        self._polys(data)
         _check(_lib.fl_ntt_forward(self.h, data.numel() // (self.L * self.N), _ptr(data), _stream(stream)))
         return data
 
     def ntt_inverse(self, data, stream=None):
+        self._polys(data)
         _check(_lib.fl_ntt_inverse(self.h, data.numel() // (self.L * self.N), _ptr(data), _stream(stream)))
         return data
