@@ -6,8 +6,9 @@ it runs on the queue kernel, at B = 64 on per-layer launches, the kernels the
 autotuner keeps for these workloads; the ResNet-50 ImageNet stack (53
 layers, N = 16384, L = 4, B = 8) runs on per-layer launches too.  The
 tensor-core form runs the batched stacks per layer as bench.py --form tc
-does.  Sampled outputs, two output channels of every layer for the last
-image, are compared bit for bit with the oracle's Algorithm 1 plus the
+does, and the ResNet-50 stack runs once more with both forms mixed the way
+bench.py --form auto runs it.  Sampled outputs, two output channels of every
+layer for the last image, are compared bit for bit with the oracle's Algorithm 1 plus the
 mask.  The x^2 + x server rounds run over the 1808
 activation ciphertexts of bench.py's x2x workload."""
 import numpy as np
@@ -132,6 +133,56 @@ def test_tc_form_full_stack_in_the_bench_configuration(fg, oracle, config):
     stream.synchronize()
     _check_sampled(oracle, c, wl, specs, filters, _two_channels)
     del graph, specs
+
+
+def test_mixed_forms_full_stack_as_the_autotuned_step(fg, oracle):
+    """ResNet-50 B=8 as bench.py --form auto runs it: the plain layers as one
+    stack call on the queue kernel, then the tensor-core layers one by one
+    with a shared workspace, all in one CUDA graph.  The forms follow the
+    layers' shapes the way the autotuner measures them to fall (tensor
+    cores where G >= 7 and Cout >= 128), so that both forms cover many layers
+    and the queue kernel runs over a full-size N = 16384 stack with gaps
+    between its layers.  Two output channels of every layer against the
+    oracle."""
+    wl = WORKLOADS["resnet50-b8"]
+    torch.cuda.empty_cache()
+    c = fg.Context(wl.N, wl.L)
+    c.stack_kernel = fg.FL_STACK_QUEUE
+    N, L, B = wl.N, wl.L, wl.B
+    specs, filters = [], []
+    for li, shape in enumerate(wl.layers):
+        g = c.geom(*shape)
+        w = synth.weights(9, (g.Cout, g.Cin, g.k, g.k), li)
+        w_hat = c.encode_weights(g, torch.from_numpy(w).to(torch.int8).cuda())
+        tc = g.G >= 7 and g.Cout >= 128
+        wk = {"w_tc": c.tc_weights(g, w_hat)} if tc else {"w_hat": w_hat}
+        del w_hat
+        specs.append({"g": g, "tc": tc, **wk,
+                      "ct_in": synth.device_uniform_residues(9, c.primes, (B, g.n_in, 2, L, N), li),
+                      "r": synth.device_masks(9, (B, g.n_out, N), T, li),
+                      "out": torch.empty((B, g.n_out, 2, L, N), dtype=torch.int32, device="cuda")})
+        filters.append((shape, w))
+    tc_specs = [sp for sp in specs if sp["tc"]]
+    assert 10 <= len(tc_specs) <= len(specs) - 10
+    arr = c.stack_layers([{k: sp[k] for k in ("g", "w_hat", "ct_in", "r", "out")} for sp in specs if not sp["tc"]])
+    ws = c.stack_workspace(arr)
+    wst = c.tc_workspace(max((sp["g"] for sp in tc_specs), key=lambda g: c.tc_workspace_bytes(g, B)), B)
+
+    def step(st):
+        c.he_conv2d_stack(arr, ws, stream=st)
+        for sp in tc_specs:
+            c.he_conv2d_tc(sp["g"], sp["w_tc"], sp["ct_in"], out=sp["out"], workspace=wst, r=sp["r"], stream=st)
+
+    stream, graph = _replay_once(step)
+    for sp in specs:
+        sp["out"].fill_(-1)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        graph.replay()
+    stream.synchronize()
+    assert c.stack_error(ws) == 0 and c.tc_error() == 0
+    _check_sampled(oracle, c, wl, specs, filters, _two_channels)
+    del arr, ws, wst, graph, specs
 
 
 def test_x2x_rounds_at_the_bench_size(fg, oracle):
