@@ -540,6 +540,13 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
                             "queue": flashgpu.FL_STACK_QUEUE}[args.stack_kernel]
         tuned = {"kernel": args.stack_kernel, "ms": None}
 
+    def set_tile(lay):
+        # the tensor-core tile the autotuner chose for this layer (else the
+        # context's): the call reads it when it launches, and a graph
+        # captured from the step keeps each layer's
+        if "tc_tile" in lay:
+            ctx.tc_tile = lay["tc_tile"]
+
     def step(events=None, outs=None, arr_=None):
         # forward NTT of every layer's inputs (one launch), then the
         # contraction + inverse NTT + mask kernel(s) over all layers; `outs`
@@ -563,6 +570,7 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
             for lay, o in zip(layers, outs):
                 if lay["form"] != "tc":
                     continue
+                set_tile(lay)
                 if events is None:
                     ctx.he_conv2d_tc(lay["g"], lay["w_tc"], lay["ct"], out=o, workspace=lay["ws"], r=lay["r"],
                                      stream=stream)
@@ -595,6 +603,7 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
             # of each layer is bracketed
             # (events[k] = 4 events per layer) and the stages are separate calls
             for k, (lay, o) in enumerate(zip(layers, outs)):
+                set_tile(lay)
                 if events is None:
                     ctx.he_conv2d_tc(lay["g"], lay["w_hat"], lay["ct"], out=o, workspace=lay["ws"], r=lay["r"],
                                      stream=stream)
@@ -632,10 +641,14 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
     if args.form in ("ntt", "tc", "auto") and not args.no_tune:
         # pass plan of the input NTTs (and of the tensor-core form's
         # inverse-NTT rows), tensor-core tile: each timed on the whole step
-        from paper_2401_16732_gb300.autotune import tune_ntt_plan, tune_tc_tile
+        from paper_2401_16732_gb300.autotune import tune_ntt_plan, tune_tc_tiles
         tuning["ntt_plan"] = tune_ntt_plan(ctx, lambda st: step(), stream=stream)
-        if tc_layers:
-            tuning["tc_tile"] = tune_tc_tile(ctx, lambda st: step(), stream=stream)
+        if args.form == "tc":  # per layer (the auto form chose its layers' tiles with their forms)
+            tile0 = str(ctx.tc_tile)  # the context's (default) tile
+            tiles = tune_tc_tiles(ctx, layers, w_key="w_hat", stream=stream)
+            tuning["tc_tile"] = {"per_layer": [t["choice"] for t in tiles],
+                                 "ms_saved_vs_context_tile": round(sum(t["ms"][tile0] - t["ms"][str(t["choice"])]
+                                                                       for t in tiles), 4)}
 
     # capture one step in a CUDA graph (40 launches for ResNet-18)
     with torch.cuda.stream(stream):
@@ -914,7 +927,9 @@ def run_gpu(args, wl, rank, world, local_rank, emit=True):
                    "l2": f"no flush: {step_bytes / 1e9:.2f} GB of algorithmic traffic per step > {L2_BYTES / 1e6:.0f} MB L2",
                    "graph": "one CUDA graph per step: input NTT of all layers + the contraction/INTT/mask kernel(s)",
                    "stack_kernel": tuned["kernel"], "autotune_ms": tuned["ms"], "form": args.form,
-                   "ntt_plan": ctx.ntt_plan, "tc_tile": ctx.tc_tile, "tuning": tuning},
+                   "ntt_plan": ctx.ntt_plan,
+                   "tc_tile": [lay["tc_tile"] for lay in tc_layers if "tc_tile" in lay] or ctx.tc_tile,
+                   "tuning": tuning},
         "slot_mac_per_s": world * macs * args.steps / (ms * 1e-3),
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,

@@ -164,15 +164,56 @@ def tune_tc_tile(ctx: flashgpu.Context, fn, stream=None, reps: int = 3, graph: b
     return _choose(ctx, "tc_tile", flashgpu.TC_TILES, fn, stream, reps, graph)
 
 
+def _time_tc_tiles(ctx, g, w_tc, lay, workspace, stream, reps, graph, tiles=None):
+    """Milliseconds of one layer's he_conv2d_tc under every tensor-core tile
+    (the context's tile is restored afterwards): ({tile: ms}, fastest tile)."""
+    saved = ctx.tc_tile
+    ms = {}
+    try:
+        for tile in tiles or flashgpu.TC_TILES:
+            ctx.tc_tile = tile
+            ms[str(tile)] = time_call(lambda st: ctx.he_conv2d_tc(g, w_tc, lay["ct_in"], out=lay["out"],
+                                                                  workspace=workspace, r=lay["r"], stream=st),
+                                      stream, reps, graph)
+    finally:
+        ctx.tc_tile = saved
+    return ms, int(min(ms, key=ms.get))
+
+
+def tune_tc_tiles(ctx: flashgpu.Context, layers, w_key: str = "w_tc", stream=None, reps: int = 3,
+                  graph: bool = True):
+    """Per tensor-core layer, time he_conv2d_tc under every tile and record
+    the fastest as the layer's "tc_tile" (a caller sets ctx.tc_tile to it
+    before that layer's call).  The best tile depends on the layer: a long
+    tile halves the per-CTA set-up, but leaves few CTAs (a partial last wave)
+    on layers with few output-channel and column tiles.  `layers` holds dicts
+    with g, ct_in, r, out, the weight tiles under `w_key` and optionally
+    "ws" (a tensor-core workspace).  Returns [{"choice", "ms"}] per layer."""
+    stream = stream or torch.cuda.current_stream()
+    out = []
+    for lay in layers:
+        g, B = lay["g"], int(lay["ct_in"].shape[0])
+        wst = lay.get("ws")
+        if wst is None:
+            wst = ctx.tc_workspace(g, B)
+        ms, best = _time_tc_tiles(ctx, g, lay[w_key], lay, wst, stream, reps, graph)
+        lay["tc_tile"] = best
+        out.append({"choice": best, "ms": ms})
+        del wst
+    return out
+
+
 def tune_forms(ctx: flashgpu.Context, layers, stream=None, reps: int = 3, graph: bool = True,
                cache: str | None = DEFAULT_CACHE):
     """Per layer, time the plain fused form (he_conv2d with the mask) against
-    the tensor-core form (he_conv2d_tc) and keep the faster.  `layers` holds
-    dicts with g, w_hat, ct_in, r, out; the tensor-core weights are built for
-    the timing and kept (as "w_tc") only for layers that choose that form, and
-    "w_hat" is dropped from those, so at most one extra weight copy is live at
-    a time.  Layers with G above FL_TC_MAX_G stay plain.  Returns the list of
-    {"form", "ms": {"plain", "tc"}} per layer; each layer dict gets "form"."""
+    the tensor-core form (he_conv2d_tc, under every tensor-core tile) and keep
+    the faster.  `layers` holds dicts with g, w_hat, ct_in, r, out; the
+    tensor-core weights are built for the timing and kept (as "w_tc") only for
+    layers that choose that form, and "w_hat" is dropped from those, so at most
+    one extra weight copy is live at a time.  Layers with G above FL_TC_MAX_G
+    stay plain.  Returns the list of {"form", "ms": {"plain", "tc"}, "tc_tile"}
+    per layer; each layer dict gets "form", and a tensor-core layer its fastest
+    tile as "tc_tile"."""
     stream = stream or torch.cuda.current_stream()
     table = {}
     if cache and os.path.exists(cache):
@@ -185,28 +226,29 @@ def tune_forms(ctx: flashgpu.Context, layers, stream=None, reps: int = 3, graph:
     out = []
     for lay in layers:
         g, B = lay["g"], int(lay["ct_in"].shape[0])
-        key = hashlib.sha256(json.dumps([dev, "form", ctx.N, ctx.L, ctx.ntt_plan, ctx.tc_tile, B,
+        key = hashlib.sha256(json.dumps([dev, "form, tile per layer", ctx.N, ctx.L, ctx.ntt_plan, B,
                                          (g.Cin, g.Cout, g.H, g.W, g.k, g.stride, g.pad)]).encode()).hexdigest()[:24]
         if g.G > flashgpu.FL_TC_MAX_G:
-            res = {"form": "plain", "ms": {"plain": None, "tc": None}}
+            res = {"form": "plain", "ms": {"plain": None, "tc": None}, "tc_tile": None}
         elif key in table:
             res = dict(table[key], cached=True)
         else:
             ws = ctx.workspace(g, B)
             wst = ctx.tc_workspace(g, B)
             w_tc = ctx.tc_weights(g, lay["w_hat"])
+            tile_ms, tile = _time_tc_tiles(ctx, g, w_tc, lay, wst, stream, reps, graph)
             ms = {"plain": time_call(lambda st: ctx.he_conv2d(g, lay["w_hat"], lay["ct_in"], out=lay["out"],
                                                               workspace=ws, r=lay["r"], stream=st),
                                      stream, reps, graph),
-                  "tc": time_call(lambda st: ctx.he_conv2d_tc(g, w_tc, lay["ct_in"], out=lay["out"], workspace=wst,
-                                                              r=lay["r"], stream=st),
-                                  stream, reps, graph)}
-            res = {"form": min(ms, key=ms.get), "ms": ms}
+                  "tc": tile_ms[str(tile)]}
+            res = {"form": min(ms, key=ms.get), "ms": ms, "tc_tile": tile}
             table[key] = res
             del ws, wst, w_tc
         lay["form"] = res["form"]
         if res["form"] == "tc":
             lay["w_tc"] = ctx.tc_weights(g, lay["w_hat"])
+            if res.get("tc_tile"):
+                lay["tc_tile"] = res["tc_tile"]
             del lay["w_hat"]
         out.append(res)
     if cache:

@@ -95,10 +95,11 @@ def test_every_plan_and_tile_is_bit_exact_against_the_oracle(fg, oracle, N, L, s
 
 
 def test_autotuner_choices_stay_bit_exact(fg, oracle):
-    """The autotuner times every pass plan, tile and per-layer form, leaves
-    valid choices set, and the two-layer workload it tuned still gives the
-    plain form's ciphertexts (and the oracle's on a sampled channel)."""
-    from paper_2401_16732_gb300.autotune import tune_forms, tune_ntt_plan, tune_tc_tile
+    """The autotuner times every pass plan, tile (for the whole step and per
+    layer) and per-layer form, leaves valid choices set, and the two-layer
+    workload it tuned still gives the plain form's ciphertexts (and the
+    oracle's on a sampled channel)."""
+    from paper_2401_16732_gb300.autotune import tune_forms, tune_ntt_plan, tune_tc_tile, tune_tc_tiles
     N, L, B = 4096, 2, 2
     c = fg.Context(N, L)
     shapes = [(16, 16, 16, 16, 3, 1, 1), (64, 130, 8, 8, 3, 1, 1)]
@@ -125,11 +126,17 @@ def test_autotuner_choices_stay_bit_exact(fg, oracle):
     tile = tune_tc_tile(c, lambda st: c.he_conv2d_tc(lay1["g"], wt, lay1["ct_in"], out=lay1["out"], r=lay1["r"],
                                                       stream=st), reps=1)
     assert tile["choice"] in fg.TC_TILES and c.tc_tile == tile["choice"]
+    per_layer = tune_tc_tiles(c, [dict(lay, w_tc=c.tc_weights(lay["g"], lay["w_hat"])) for lay in layers], reps=1)
+    assert all(t["choice"] in fg.TC_TILES and set(t["ms"]) == {str(x) for x in fg.TC_TILES} for t in per_layer)
+    assert c.tc_tile == tile["choice"]  # the per-layer timing leaves the context's tile as it was
     forms = tune_forms(c, layers, reps=1, cache=None)
     assert [f["form"] for f in forms] == [lay["form"] for lay in layers]
     for lay, wnt, f in zip(layers, want, forms):
         assert f["form"] in ("plain", "tc") and all(v > 0 for v in f["ms"].values())
+        assert f["tc_tile"] in fg.TC_TILES
         if lay["form"] == "tc":
+            assert lay["tc_tile"] == f["tc_tile"]
+            c.tc_tile = lay["tc_tile"]
             got = c.he_conv2d_tc(lay["g"], lay["w_tc"], lay["ct_in"], r=lay["r"])
         else:
             got = c.he_conv2d(lay["g"], lay["w_hat"], lay["ct_in"], r=lay["r"])
