@@ -39,7 +39,7 @@ def test_noalloc_equals_workspace_entry_point_on_two_calls(N, L, shape, B):
         out = torch.full_like(want, -1)
         torch.cuda.synchronize()
         before = torch.cuda.memory_allocated()
-        free_before, _ = torch.cuda.mem_get_info()  # the driver's count: sees a cudaMalloc inside the library too
+        free_before, _ = torch.cuda.mem_get_info()  # the CUDA driver's count of free memory: it sees a cudaMalloc inside the library too
         c.he_conv2d_mask_noalloc(g, wh, ct, r, out)
         torch.cuda.synchronize()
         assert torch.cuda.memory_allocated() == before
