@@ -997,7 +997,11 @@ def run_batched(args, local_rank, plain_values=None):
         if "forms" in tun:
             summ["forms"] = [f["form"] for f in tun["forms"]]
             summ["form_ms"] = [f["ms"] for f in tun["forms"]]
-        summ["tuning_ms"] = {k: v["ms"] for k, v in tun.items() if k != "forms"}
+        if "forms" in tun:
+            summ["form_tiles"] = [f.get("tc_tile") for f in tun["forms"]]
+        # whole-step choices carry their timings under "ms"; the per-layer
+        # tile choice of the tensor-core form is summarised as it is
+        summ["tuning_ms"] = {k: v.get("ms", v) for k, v in tun.items() if k != "forms"}
         out.setdefault(cfg, {})[form] = summ
         del ln
     torch.cuda.empty_cache()
