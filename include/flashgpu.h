@@ -388,7 +388,11 @@ int fl_ctx_get_stack_kernel(const fl_ctx *ctx);
  *   the default (3, 4, 4, 5 for the four ring degrees).  FL_ERR_ARG for any
  *   other value.  The getter returns the r1 in use.
  * - Tensor-core tile: slot groups of 4 per CTA of fl_he_conv2d_tc (4, 8, 16,
- *   32 or 64; 0 selects the default 32).  FL_ERR_ARG otherwise. */
+ *   32 or 64; 0 selects the default 32).  FL_ERR_ARG otherwise.  Each call
+ *   reads the setting when it launches, so a caller may set it before every
+ *   layer's call (the autotuner picks it per layer).
+ * The settings are plain fields of the context: set them from one host
+ * thread, between calls. */
 int fl_ctx_set_ntt_plan(fl_ctx *ctx, int r1);
 int fl_ctx_get_ntt_plan(const fl_ctx *ctx);
 int fl_ctx_set_tc_tile(fl_ctx *ctx, int groups);
